@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark of the tau = 1 lattice Boltzmann step on GB300.
+
+Workload (default): the 2-D shock tube on the square lattice, 4096 x 512
+nodes, x-only Sod jump at mid-length, transmissive x ends, reflecting y walls,
+run toward t = 0.2 (820 steps), synthetic initial state (Section V.C).
+
+One benchmark step = one tau = 1 step of the whole grid (one fused kernel
+launch: equilibrium, migration, summation, reach, FP64 totals).  The state
+(67 MB in FP32) fits the 129 MB L2, so L2 is flushed by a 256 MB write
+between timed steps and every step is timed alone with CUDA events on the
+solver's stream.
+
+  value      node-updates/s of the FP32 path (device-resident state)
+  fp64       the same for the FP64 path (bit-exact with the oracle)
+  e2e        node-updates/s of whole solves through the C ABI from pinned
+             host buffers: set moments (H2D), 820 steps, moments (D2H)
+  roofline   step kernel: algorithmic bytes (4 fields read + 4 written per
+             node) / mean kernel time, against the measured HBM copy rate
+  cpu_baseline  the FP64 oracle on this host's cores, bounded sample
+
+--impl reference times the oracle alone (the CPU reference arm).
+Multi-GPU (torchrun): independent replicas, one per rank (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY = 4096, 512
+T_END = 0.2
+WORKLOAD = "sod_2d_4096x512_transmissive_x_reflecting_y"
+# profiling case: the periodic cylinder box, state larger than L2
+WORKLOADS = {
+    "sod2d": dict(nx=4096, ny=512, name=WORKLOAD),
+    "cylinder2d": dict(nx=8192, ny=8192, name="cylinder_2d_8192x8192_periodic"),
+}
+METRIC = "node-updates/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def steps_and_lambda(t_end, dx):
+    n = max(1, int(math.ceil(t_end / dx - 1e-9)))
+    return n, t_end / (n * dx)
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class Clocks:
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+    from paper_1602_02675_gb300 import lbm as L
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    wl = WORKLOADS[args.workload]
+    nx, ny = wl["nx"], wl["ny"]
+    dx = 1.0 / nx
+    nsolve, lam = steps_and_lambda(T_END, dx)
+    if args.workload == "cylinder2d":
+        lam = 1.0
+    N = nx * ny
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def make(prec, cons_every=1):
+        if args.workload == "cylinder2d":
+            cfg = L.make_config(2, nx, ny, dt=lam * dx, precision=prec,
+                                bc_x=L.PERIODIC, bc_y=L.PERIODIC, kahan=1,
+                                cons_every=cons_every, stream=stream.cuda_stream)
+            s = L.Solver(cfg)
+            s.init_riemann((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1),
+                           L.CIRCLE, 0.5, 0.5, 0.4)
+            return s
+        cfg = L.make_config(2, nx, ny, dt=lam * dx, precision=prec,
+                            bc_x=L.TRANSMISSIVE, bc_y=L.REFLECTING, kahan=1,
+                            cons_every=cons_every, stream=stream.cuda_stream)
+        s = L.Solver(cfg)
+        s.init_riemann((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), L.PLANAR_X, 0.5)
+        return s
+
+    def timed_steps(s, K, W):
+        with torch.cuda.stream(stream):
+            s.step(W)
+            stream.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True),
+                   torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for a, b in ev:
+                flush.fill_(1.0)          # evict the state from L2
+                a.record(stream)
+                s.step(1)
+                b.record(stream)
+            stream.synchronize()
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        ms = [a.elapsed_time(b) for a, b in ev]
+        s.synchronize()
+        return ms, wall
+
+    # FP32 (headline)
+    s32 = make(L.F32)
+    clocks = Clocks(dev)
+    ms32, wall32 = timed_steps(s32, args.steps, args.warmup)
+    clk = clocks.stop()
+    s32.close()
+    # FP64 (oracle-exact path)
+    k64 = max(3, args.steps // 4)
+    ms64 = [float("nan")]
+    if args.precision == "both":
+        s64 = make(L.F64)
+        ms64, _ = timed_steps(s64, k64, max(3, args.warmup))
+        s64.close()
+
+    t32 = sum(ms32) / 1e3
+    t64 = sum(ms64) / 1e3
+    if world > 1:
+        t = torch.tensor([t32, t64], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t32, t64 = float(t[0]), float(t[1])
+    value = world * N * args.steps / t32
+    v64 = world * N * k64 / t64
+
+    # e2e: whole solves through the C ABI from pinned host memory
+    e2e = (run_e2e(args, L, torch, stream, lam, nsolve, world)
+           if args.e2e_solves > 0 and args.workload == "sod2d" else None)
+
+    peak, peak_kind = load_peaks()
+    mean_ms = t32 / args.steps * 1e3
+    bytes_per_launch = 8 * 4 * N            # 4 fields read + 4 written, FP32
+    achieved = bytes_per_launch / (mean_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": args.traffic, "peak_kind": peak_kind,
+            "kernel": "step_kernel<float,2,true>",
+            "bytes_per_launch": bytes_per_launch}
+    mean64 = t64 / k64 * 1e3
+    line = {
+        "metric": METRIC, "value": value, "unit": "node-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(mean_ms, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (Sod initial state, Section V.C)",
+        "config": {"workload": wl["name"], "nx": nx, "ny": ny, "nodes": N,
+                   "lambda": lam, "steps_to_t0.2": nsolve,
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "fp64": {"value": v64, "unit": "node-updates/s", "steps": k64,
+                 "ms_per_step": round(mean64, 5),
+                 "hbm_frac": round((16 * 4 * N) / (mean64 / 1e3) / 1e9 / peak, 4),
+                 "parity": "bit-exact with the FP64 oracle (tests)"},
+        "e2e": e2e,
+        "roofline": roof,
+        "clocks": clk,
+        "gpu_launches": args.steps,
+        "wall_s_timed_fp32": round(wall32, 4),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0 and not args.no_l1:
+        line["l1_vs_oracle"] = l1_vs_oracle(L)
+    return line
+
+
+def run_e2e(args, L, torch, stream, lam, nsolve, world):
+    """Whole solves: H2D of the initial moments from pinned host memory,
+    nsolve steps, D2H of the final moments and pressure."""
+    import numpy as np
+    N = NX * NY
+    dx = 1.0 / NX
+    # the initial state, as a user would hold it on the host (physical units)
+    x = (np.arange(NX) + 0.5) * dx
+    left = np.tile(x < 0.5, NY)
+    pin = lambda: torch.empty(N, dtype=torch.float64, pin_memory=True).numpy()
+    rho, mx, my, rhoE = pin(), pin(), pin(), pin()
+    rho[:] = np.where(left, 1.0, 0.125)
+    mx[:] = 0.0
+    my[:] = 0.0
+    rhoE[:] = np.where(left, 1.0, 0.1) / 0.4
+    outs = {k: pin() for k in ("rho", "mx", "my", "rhoE", "p")}
+    cfg = L.make_config(2, NX, NY, dt=lam * dx, precision=L.F32,
+                        bc_x=L.TRANSMISSIVE, bc_y=L.REFLECTING, kahan=1,
+                        stream=stream.cuda_stream)
+    times = []
+    with L.Solver(cfg) as s:
+        for rep in range(1 + args.e2e_solves):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.set_moments(rho, mx, my, rhoE)
+            s.step(nsolve)
+            s.moments(outs)
+            dt = time.perf_counter() - t0
+            if rep > 0:
+                times.append(dt)
+    t = statistics.median(times)
+    return {"value": world * N * nsolve / t, "unit": "node-updates/s",
+            "h2d_bytes_per_step": 4 * 8 * N, "d2h_bytes_per_step": 5 * 8 * N,
+            "step": f"one solve to t=0.2 ({nsolve} lattice steps)",
+            "solve_ms_p50": round(1e3 * t, 3),
+            "solves": len(times)}
+
+
+# --------------------------------------------------------------------------
+# the oracle on the host: CPU baseline and reference arm
+# --------------------------------------------------------------------------
+def _oracle_sod_steps(nsteps, ny=NY):
+    from oracle import oracle as O
+    dx = 1.0 / NX
+    _, lam = steps_and_lambda(T_END, dx)
+    P = O.Params(dim=2, nx=NX, ny=ny, bc_x=O.TRANSMISSIVE, bc_y=O.REFLECTING)
+    s = O.riemann_planar(P, 0.0, 1.0, 0.5, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1),
+                         lam)
+    t0 = time.perf_counter()
+    O.run(P, s, nsteps)
+    return time.perf_counter() - t0, NX * ny * nsteps
+
+
+def cpu_baseline(seconds: float) -> dict:
+    # calibrate on one step of a 4096 x 8 strip, then size the sample
+    t, nu = _oracle_sod_steps(1, ny=8)
+    rate = nu / t
+    rows = max(8, min(NY, int(seconds * rate / NX)))
+    t, nu = _oracle_sod_steps(1, ny=rows)
+    return {"value": nu / t, "unit": "node-updates/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"1 step of a 4096 x {rows} strip of the 4096 x 512 Sod "
+                      f"lattice (FP64, single thread), {t:.1f} s"}
+
+
+def l1_vs_oracle(L) -> dict:
+    """FP32 path against the FP64 oracle: mean |error| / field range on the
+    1-D Sod tube (1000 nodes, 200 steps to t = 0.2)."""
+    import numpy as np
+    from oracle import oracle as O
+    n = 1000
+    P = O.Params(dim=1, nx=n, bc_x=O.TRANSMISSIVE)
+    st, _ = O.run(P, O.riemann_planar(P, 0, 1, 0.5, (1.0, 0.0, 1.0),
+                                      (0.125, 0.0, 0.1), 1.0), 200)
+    o = O.lattice_to_physical(1.4, 1.0, st)
+    out = {}
+    for prec, name in ((L.F32, "f32"), (L.F64, "f64")):
+        with L.Solver(L.make_config(1, n, precision=prec)) as s:
+            s.init_riemann((1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
+            s.step(200)
+            g = s.moments()
+        out[name] = {f: float(np.mean(np.abs(g[f] - o[f])) /
+                              (o[f].max() - o[f].min()))
+                     for f in ("rho", "mx", "rhoE")}
+    out["case"] = "sod_1d_1000, 200 steps"
+    return out
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle as it stands: K bounded samples of the workload."""
+    if rank != 0:
+        return None
+    times, nus = [], []
+    rows = args.ref_rows
+    for _ in range(args.warmup):
+        _oracle_sod_steps(1, ny=rows)
+    for _ in range(args.steps):
+        t, nu = _oracle_sod_steps(1, ny=rows)
+        times.append(t)
+        nus.append(nu)
+    value = sum(nus) / sum(times)
+    return {
+        "metric": METRIC, "value": value, "unit": "node-updates/s",
+        "impl": "reference", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1e3 * sum(times) / len(times), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (Sod initial state, Section V.C)",
+        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY,
+                   "sample_rows": rows},
+        "cpu_baseline": {"value": value, "unit": "node-updates/s",
+                         "cores": 1, "kind": "oracle",
+                         "sample": f"each step: 1 lattice step of a 4096 x {rows} "
+                                   "strip of the Sod lattice (FP64, 1 thread)"},
+        "e2e": {"value": value, "unit": "node-updates/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-solves", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-rows", type=int, default=16)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per step-kernel launch, if measured")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-l1", action="store_true")
+    ap.add_argument("--workload", default="sod2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="both", choices=["both", "f32"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line))
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * lbm.h - C ABI of the GB300 tau = 1 semi-discrete lattice Boltzmann solver.
+ *
+ * The method (Komeili, Mirzaei, Shabouei, "Performance of 1-D and 2-D Lattice
+ * Boltzmann (LB) in Solution of the Shock Tube Problem"): with relaxation time
+ * tau = 1 the BGK update reduces to f(x + r dt, t + dt) = f_eq(x, t)
+ * (Section III.A, eqs 9-10), so a node's state is its moments
+ * Y = (rho, rho V, rho E) alone (eq 7).  One step expands every node's moments
+ * into its equilibrium packets over the triple-level (1-D) or dual-level
+ * square (2-D) velocity set (Section III.B, eqs 11-26; Section IV), migrates
+ * each packet to x + (V + c') dt with linear (eq 28) or bilinear (eq 29)
+ * splitting, and sums the arrivals into the new moments (eqs 6, 22; Section
+ * V.A).  The shock-tube problem of Section V.C is the initial state.
+ *
+ * Conventions shared by every entry point:
+ *  - Plain C types only.  Host arrays are caller-owned, hold n = nx*ny
+ *    doubles with x fastest, and are not retained after the call returns.
+ *  - All device memory (the two moment buffers and a few scratch words) is
+ *    owned by the handle and allocated in lbm_create.
+ *  - Work is issued on the stream given in lbm_config.stream (a
+ *    cudaStream_t, or NULL for the default stream), in call order.
+ *    lbm_step returns before the GPU finishes; lbm_moments, lbm_conservation,
+ *    lbm_reach, lbm_diagnostics and lbm_synchronize wait for it.
+ *  - Every call returns an lbm_status; nothing throws across the ABI.
+ *    lbm_last_error gives a message for the last failure on a handle.
+ *    LBM_EINVAL leaves the handle usable; after any other error the handle
+ *    may only be destroyed.
+ *  - A handle is not thread-safe; separate handles are independent.
+ *  - Physical units at the ABI: positions in [x0, x1] along x, square cells
+ *    dx = (x1 - x0)/nx, time step dt.  Internally the lattice velocity is
+ *    V = u*lambda with lambda = dt/dx and energies per unit mass scale with
+ *    lambda^2.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_handle lbm_handle;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,   /* bad argument or configuration */
+  LBM_ENOMEM = 2,   /* device or host allocation failed */
+  LBM_ECUDA = 3,    /* a CUDA call failed (message in lbm_last_error) */
+  LBM_ESTATE = 4,   /* a node reached rho < 0 or a non-finite moment */
+  LBM_EREACH = 5,   /* migration reach exceeded the configured max_reach */
+  LBM_ETIMEOUT = 6, /* a bounded device-side wait gave up */
+  LBM_EBUDGET = 7   /* request does not fit the memory budget */
+} lbm_status;
+
+typedef enum { LBM_F32 = 0, LBM_F64 = 1 } lbm_precision;
+
+/* Boundary rule per axis (Section V.B).  Beyond the edge a source node
+   ("additional point") holds the state of: the nearest edge node
+   (TRANSMISSIVE, zero gradient); the mirror image about the wall half a cell
+   beyond the edge node, normal momentum negated (REFLECTING); the node one
+   period away (PERIODIC).  Packets landing outside the domain are dropped. */
+typedef enum {
+  LBM_TRANSMISSIVE = 0,
+  LBM_REFLECTING = 1,
+  LBM_PERIODIC = 2
+} lbm_bc;
+
+typedef enum { LBM_PLANAR_X = 0, LBM_CIRCLE = 1 } lbm_geom;
+
+typedef struct {
+  int32_t dim;        /* 1 or 2 (Section IV.A / IV.B) */
+  int32_t precision;  /* lbm_precision of the stored moments and the step */
+  int32_t bc_x, bc_y; /* lbm_bc; bc_y ignored in 1-D */
+  int64_t nx, ny;     /* nodes; ny must be 1 in 1-D */
+  double x0, x1;      /* physical extent along x; dx = (x1 - x0)/nx */
+  double y0;          /* lower edge along y (2-D); cells are square */
+  double gamma;       /* ratio of specific heats, > 1 (eqs 15, 24-27) */
+  double theta;       /* 1-D rest share d0 = theta*rho (Section III.B,
+                         0.4..0.55); must be 0 in 2-D where d0 = 0 */
+  double dt;          /* physical time step; lambda = dt/dx */
+  int32_t max_reach;  /* largest migration reach R (lattice cells) a step
+                         may meet; 0 picks the default (1-D 64, 2-D 6).
+                         Shared memory per block grows with it.  A step
+                         that meets a larger R leaves the state untouched
+                         and reports LBM_EREACH at the next waiting call. */
+  int32_t kahan;      /* F32 only: 1 = compensated (Kahan) summation of
+                         the gathered arrivals, 0 = plain summation */
+  int32_t cons_every; /* also sum total mass/momentum/energy in FP64 every
+                         this many steps inside the step kernel (0 = never;
+                         lbm_conservation computes them on request) */
+  int32_t reserved_;
+  void* stream;       /* cudaStream_t; NULL = legacy default stream */
+} lbm_config;
+
+/* Primitive state (physical units): density, velocity, pressure. */
+typedef struct {
+  double rho, u, v, p;
+} lbm_prim;
+
+/* ABI revision of this header. */
+int32_t lbm_abi_version(void);
+
+/* Validate cfg, allocate the handle and its device buffers.  *out is set
+   only on LBM_OK.  Errors: LBM_EINVAL (cfg), LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out);
+
+/* Riemann initial state of Section V.C (Sod: left (1, 0, 1), right
+   (0.125, 0, 0.1)).  Nodes sit at cell centres x_i = x0 + (i + 1/2) dx.
+   geom = LBM_PLANAR_X: nodes with x < a0 take *inner, the rest *outer.
+   geom = LBM_CIRCLE: nodes with (x - a0)^2 + (y - a1)^2 < radius^2 take
+   *inner, the rest *outer.  Moments: m = rho u lambda,
+   rhoE = p lambda^2/(gamma - 1) + rho |u lambda|^2 / 2.  Also sets the
+   migration reach for the first step.  Stream-ordered, does not wait. */
+lbm_status lbm_init_riemann(lbm_handle* h, const lbm_prim* inner,
+                            const lbm_prim* outer, int32_t geom, double a0,
+                            double a1, double radius);
+
+/* Set every node from host primitive arrays (rho, u, v, p; v may be NULL in
+   1-D), converted to moments on the device as in lbm_init_riemann.  Waits
+   for the copy to finish before returning. */
+lbm_status lbm_set_primitives(lbm_handle* h, const double* rho,
+                              const double* u, const double* v,
+                              const double* p, int64_t n);
+
+/* Set every node from host conserved arrays in physical units (rho,
+   rho*u, rho*v, rho*E with E = e + |u|^2/2); my may be NULL in 1-D.  With
+   lbm_moments this is checkpoint / restart: the tau = 1 state is the moments
+   alone (eq 10).  Waits for the copy to finish before returning. */
+lbm_status lbm_set_moments(lbm_handle* h, const double* rho, const double* mx,
+                           const double* my, const double* rhoE, int64_t n);
+
+/* Advance nsteps tau = 1 steps (eq 10), one fused kernel launch each:
+   equilibrium (eqs 13-15, 24-26), packets (eqs 11-14, 21), split (eqs 23,
+   28, 29), migration and summation (eqs 6, 22), boundaries (Section V.B);
+   the same launch reduces the next step's migration reach.  Returns after
+   queueing the work (stream-ordered, does not wait).  Errors found on the
+   device (LBM_ESTATE, LBM_EREACH) are reported by the next waiting call. */
+lbm_status lbm_step(lbm_handle* h, int64_t nsteps);
+
+/* Copy the current state to host arrays in physical units: rho, rho*u,
+   rho*v (NULL allowed; ignored in 1-D), rho*E and, if p is not NULL, the
+   pressure P = (gamma - 1) rho e (eq 27), recovered in FP64 on the device.
+   Waits for all queued work. */
+lbm_status lbm_moments(lbm_handle* h, double* rho, double* mx, double* my,
+                       double* rhoE, double* p, int64_t n);
+
+/* FP64 totals over all nodes, physical units, in a fixed reduction order:
+   out[0] = sum rho, out[1] = sum rho*u, out[2] = sum rho*v, out[3] =
+   sum rho*E.  Conserved exactly by the step on periodic and closed domains
+   (eq 22 with eqs 16-18).  Waits for all queued work. */
+lbm_status lbm_conservation(lbm_handle* h, double out[4]);
+
+/* Migration reach R the next step will use (lattice cells): the maximum over
+   nodes of floor(|V_a|) + 1 + c2 (eq 26), computed conservatively.  Waits. */
+lbm_status lbm_reach(lbm_handle* h, int32_t* reach);
+
+/* Counters: steps taken since the last state set, number of nodes whose
+   internal energy came out below zero from round-off and was clamped to 0,
+   and the device error flags (bit 0: LBM_ESTATE, bit 1: LBM_EREACH).
+   Any pointer may be NULL.  Waits. */
+lbm_status lbm_diagnostics(lbm_handle* h, int64_t* steps, int64_t* eclamps,
+                           uint32_t* flags);
+
+/* Wait for queued work and report device-side errors. */
+lbm_status lbm_synchronize(lbm_handle* h);
+
+/* Lattice velocity scale lambda = dt/dx of a handle (0 for NULL). */
+double lbm_lambda(const lbm_handle* h);
+
+/* Message for the last failure on h (empty string if none; static text for
+   h == NULL).  Owned by the handle. */
+const char* lbm_last_error(const lbm_handle* h);
+
+/* Free the handle and its device memory.  NULL-safe.  Waits for queued
+   work first. */
+void lbm_destroy(lbm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,86 @@
+// Internal declarations shared by the kernels and the C-ABI layer.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+// Device error flags (Scratch::flags).
+enum : unsigned { kFlagState = 1u, kFlagReach = 2u };
+
+// Small device-resident block of per-handle scratch words.
+struct Scratch {
+  int reach;               // migration reach the next step uses
+  int reach_next;          // max-reduced by the running step
+  unsigned flags;          // kFlag*
+  unsigned ticket;         // blocks finished in the running launch
+  unsigned long long eclamps;  // nodes whose e < 0 was clamped to 0
+  double cons[4];          // FP64 totals (lattice units) of the last sum
+};
+
+// Constants of the equilibrium (Section III.B) for one lattice and gas.
+struct EqConst {
+  double theta;  // 1-D: d0 = theta*rho; 2-D: 0
+  double kq;     // D (gamma - 1)
+  double kphi;   // 1 - D/2 (gamma - 1)     (eq 15)
+  double b1;     // directions per level: 2 (1-D), 4 (square lattice)
+  double kreach; // D (gamma - 1) / (1 - b0 theta): X = kreach * e
+};
+
+struct StepArgs {
+  const void* in[4];  // rho, m_x, m_y, rhoE (m_y unused in 1-D)
+  void* out[4];
+  int nx, ny;
+  int bc_x, bc_y;
+  int r_cap;          // largest reach the launch's shared memory holds
+  int kahan;          // F32: compensated summation of row-pair sums
+  int do_cons;        // this launch also sums FP64 totals
+  int nblocks;
+  EqConst k;
+  Scratch* scr;
+  double* part;       // [nblocks * 4] FP64 partial sums
+};
+
+// Launch helpers (step kernels).
+size_t step_smem_bytes(int dim, bool f64, int r_cap);
+cudaError_t step_prepare(int dim, bool f64, size_t smem);
+int step_blocks(int dim, int nx, int ny);
+cudaError_t launch_step(int dim, bool f64, const StepArgs& a, size_t smem,
+                        cudaStream_t s);
+
+// Auxiliary kernels (init, conversion, reductions).
+struct InitArgs {
+  void* f[4];
+  int nx, ny, dim;
+  double x0, y0, dx, lambda, gamma;
+  int geom;                 // 0 planar (x < a0 -> inner), 1 circle
+  double a0, a1, radius;
+  double in_[4], out_[4];   // rho, u, v, p of the inner / outer state
+};
+cudaError_t launch_init(bool f64, const InitArgs& a, cudaStream_t s);
+
+// staging holds n doubles per field; kind 0 = primitives (rho, u, v, p),
+// kind 1 = physical conserved (rho, rho u, rho v, rho E).
+cudaError_t launch_from_host_layout(bool f64, int kind, int dim,
+                                    const double* staging, void* const f[4],
+                                    int64_t n, double lambda, double gamma,
+                                    cudaStream_t s);
+
+// Lattice state -> physical (rho, m_x, m_y, rhoE, p) in staging.
+cudaError_t launch_to_host_layout(bool f64, int dim, const void* const f[4],
+                                  double* staging, int64_t n, double lambda,
+                                  double gamma, cudaStream_t s);
+
+// Reach of the current state into scr->reach (conservative, see kernels).
+cudaError_t launch_reach(bool f64, int dim, const void* const f[4], int64_t n,
+                         const EqConst& k, Scratch* scr, cudaStream_t s);
+
+// FP64 totals of the current state into scr->cons (fixed order).
+cudaError_t launch_totals(bool f64, int dim, const void* const f[4], int64_t n,
+                          double* part, int nblocks_cap, Scratch* scr,
+                          cudaStream_t s);
+int totals_blocks(int64_t n);
+
+}  // namespace lbm

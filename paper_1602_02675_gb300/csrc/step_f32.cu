@@ -1,0 +1,46 @@
+// FP32 step kernels (compensated or plain summation of the row-pair sums).
+#include "step_kernel.cuh"
+
+namespace lbm {
+
+cudaError_t launch_step_f32(int dim, const StepArgs& a, size_t smem,
+                            cudaStream_t s) {
+  if (dim == 1) {
+    dim3 grid((a.nx + TileShape<1>::TX - 1) / TileShape<1>::TX, 1);
+    if (a.kahan)
+      step_kernel<float, 1, true><<<grid, 256, smem, s>>>(a);
+    else
+      step_kernel<float, 1, false><<<grid, 256, smem, s>>>(a);
+  } else {
+    dim3 grid((a.nx + TileShape<2>::TX - 1) / TileShape<2>::TX,
+              (a.ny + TileShape<2>::TY - 1) / TileShape<2>::TY);
+    if (a.kahan)
+      step_kernel<float, 2, true><<<grid, 256, smem, s>>>(a);
+    else
+      step_kernel<float, 2, false><<<grid, 256, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+size_t step_smem_f32(int dim, int r_cap) {
+  return dim == 1 ? step_smem_bytes_t<float, 1>(r_cap)
+                  : step_smem_bytes_t<float, 2>(r_cap);
+}
+
+cudaError_t step_prepare_f32(int dim, size_t smem) {
+  cudaError_t e;
+  if (dim == 1) {
+    e = cudaFuncSetAttribute(step_kernel<float, 1, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(step_kernel<float, 1, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  e = cudaFuncSetAttribute(step_kernel<float, 2, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(step_kernel<float, 2, false>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace lbm

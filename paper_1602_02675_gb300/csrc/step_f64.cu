@@ -1,0 +1,36 @@
+// FP64 step kernels.  This unit is compiled with -fmad=false: every product
+// and sum rounds on its own, in the same order the arithmetic is written, so
+// the FP64 step reproduces a plain evaluation of the same formulas.
+#include "step_kernel.cuh"
+
+namespace lbm {
+
+cudaError_t launch_step_f64(int dim, const StepArgs& a, size_t smem,
+                            cudaStream_t s) {
+  if (dim == 1) {
+    dim3 grid((a.nx + TileShape<1>::TX - 1) / TileShape<1>::TX, 1);
+    step_kernel<double, 1, false><<<grid, 256, smem, s>>>(a);
+  } else {
+    dim3 grid((a.nx + TileShape<2>::TX - 1) / TileShape<2>::TX,
+              (a.ny + TileShape<2>::TY - 1) / TileShape<2>::TY);
+    step_kernel<double, 2, false><<<grid, 256, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+size_t step_smem_f64(int dim, int r_cap) {
+  return dim == 1 ? step_smem_bytes_t<double, 1>(r_cap)
+                  : step_smem_bytes_t<double, 2>(r_cap);
+}
+
+cudaError_t step_prepare_f64(int dim, size_t smem) {
+  if (dim == 1)
+    return cudaFuncSetAttribute(step_kernel<double, 1, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+  return cudaFuncSetAttribute(step_kernel<double, 2, false>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+}
+
+}  // namespace lbm

@@ -1,0 +1,506 @@
+// Fused tau = 1 step: equilibrium + migration + summation + reach, one launch.
+//
+// One block owns a tile of destination nodes (1-D: 256 x 1, 2-D: 32 x 8,
+// one destination per thread).  It
+//  1. computes the equilibrium packets of every source node within the
+//     migration reach R of the tile once (Section III.B eqs 13-15, 24-26;
+//     packets eqs 11-14, 21; split weights eq 23, 28, 29) and keeps them in
+//     shared memory; sources beyond the domain edge are the additional points
+//     of Section V.B (zero-gradient, periodic image or mirror image);
+//  2. lets each thread gather the arrivals at its destination (eqs 6, 10,
+//     22): source rows at distance j below and above the destination are
+//     summed row by row (ascending x, packet table order, corner order) and
+//     added as pairs, j = 0..R.  The order is the same relative to every
+//     destination and symmetric under y -> -y;
+//  3. writes the new moments, reduces a conservative reach for the next step
+//     and, when asked, FP64 totals; the last block to finish publishes them.
+// No floating-point atomics anywhere; every sum has a fixed order.
+#pragma once
+
+#include <cstdint>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+template <int DIM>
+struct TileShape;
+template <>
+struct TileShape<1> {
+  static constexpr int TX = 256, TY = 1, NP = 5, NK = 2, NLEV = 3;
+};
+template <>
+struct TileShape<2> {
+  static constexpr int TX = 32, TY = 8, NP = 8, NK = 4, NLEV = 2;
+};
+
+// Shared-memory layout of the source records, structure of arrays, sized
+// for r_cap.  Per source: packet fields Px, Py (2-D), PE per packet, the mass
+// per level, split fractions f, and packed integers (c1, n_x, n_y).
+template <typename T, int DIM>
+struct SrcLayout {
+  using S = TileShape<DIM>;
+  int cap;  // sources the buffers hold
+  T* Px;
+  T* Py;
+  T* PE;
+  T* mass;
+  T* f0;
+  T* f1;
+  short* c1;
+  short* n0;
+  short* n1;
+
+  __host__ __device__ static int capacity(int r_cap) {
+    return (S::TX + 2 * r_cap) * (DIM == 2 ? (S::TY + 2 * r_cap) : 1);
+  }
+  __host__ __device__ static size_t bytes(int r_cap) {
+    size_t c = (size_t)capacity(r_cap);
+    size_t nt = (size_t)S::NP * (DIM == 2 ? 3 : 2) + S::NLEV + (DIM == 2 ? 2 : 1);
+    size_t b = c * nt * sizeof(T) + c * 3 * sizeof(short);
+    return (b + 15) & ~size_t(15);
+  }
+  __device__ void bind(unsigned char* base, int r_cap) {
+    cap = capacity(r_cap);
+    T* p = reinterpret_cast<T*>(base);
+    Px = p;
+    p += S::NP * cap;
+    if (DIM == 2) {
+      Py = p;
+      p += S::NP * cap;
+    } else {
+      Py = nullptr;
+    }
+    PE = p;
+    p += S::NP * cap;
+    mass = p;
+    p += S::NLEV * cap;
+    f0 = p;
+    p += cap;
+    if (DIM == 2) {
+      f1 = p;
+      p += cap;
+    } else {
+      f1 = nullptr;
+    }
+    short* q = reinterpret_cast<short*>(p);
+    c1 = q;
+    n0 = q + cap;
+    n1 = q + 2 * cap;
+  }
+};
+
+// Interior node supplying the state of source coordinate L on one axis, and
+// the sign of the momentum component along that axis there (Section V.B).
+__device__ __forceinline__ int virtual_axis(int bc, int n, long long L,
+                                            bool* flip) {
+  *flip = false;
+  if (L >= 0 && L < n) return (int)L;
+  if (bc == 0) return L < 0 ? 0 : n - 1;  // transmissive: zero gradient
+  if (bc == 2) {                          // periodic
+    long long w = L % n;
+    return (int)(w < 0 ? w + n : w);
+  }
+  long long p2 = 2LL * n;                 // reflecting: mirror, period 2n
+  long long w = L % p2;
+  if (w < 0) w += p2;
+  if (w >= n) {
+    *flip = true;
+    return (int)(p2 - 1 - w);
+  }
+  return (int)w;
+}
+
+template <typename T>
+struct Equil {
+  bool emits, bad, clamp;
+  T V0, V1, e, d0, d1, d2, phi, f0, f1;
+  int c1, n0, n1;
+};
+
+__device__ __forceinline__ float dev_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double dev_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float dev_floor(float x) { return floorf(x); }
+__device__ __forceinline__ double dev_floor(double x) { return floor(x); }
+
+// Equilibrium of one node (Section III.B): V and e (eq 13, eq 15 text),
+// c1 = int(sqrt(D (gamma-1) e rho / (rho - b0 d0))), c2 = c1 + 1 (eq 26),
+// d1, d2 (eqs 24-25), phi (eq 15), floor/fraction of V (eqs 23, 28, 29).
+template <typename T, int DIM>
+__device__ __forceinline__ Equil<T> equilibrium(T rho, T mx, T my, T rhoE,
+                                                const EqConst& k) {
+  Equil<T> q;
+  q.emits = false;
+  q.bad = false;
+  q.clamp = false;
+  if (!isfinite(rho) || !isfinite(mx) || !isfinite(my) || !isfinite(rhoE) ||
+      rho < T(0)) {
+    q.bad = true;
+    return q;
+  }
+  if (rho == T(0)) return q;
+  q.V0 = mx / rho;
+  q.V1 = (DIM == 2) ? my / rho : T(0);
+  T E = rhoE / rho;
+  T e = E - T(0.5) * (q.V0 * q.V0 + q.V1 * q.V1);
+  if (e < T(0)) {
+    e = T(0);
+    q.clamp = true;
+  }
+  q.e = e;
+  T d0 = (DIM == 1) ? T(k.theta) * rho : T(0);
+  T rho_p = rho - T(1) * d0;
+  T Q = T(k.kq) * rho * e;
+  T X = Q / rho_p;
+  // X beyond 2^40 would mean c1 > 2^20: far past any supported reach
+  if (!isfinite(X) || !(X >= T(0)) || X > T(1099511627776.0)) {
+    q.bad = true;
+    return q;
+  }
+  // floor(sqrt(X)) of a correctly rounded sqrt is within one of the exact
+  // integer root, so one fix-up each way settles c1^2 <= X < (c1+1)^2
+  int c1 = (int)dev_floor(dev_sqrt(X));
+  if ((T)((long long)(c1 + 1) * (c1 + 1)) <= X) ++c1;
+  if (c1 > 0 && (T)((long long)c1 * c1) > X) --c1;
+  q.c1 = c1;
+  T c1sq = (T)(c1 * c1);
+  T c2sq = (T)((c1 + 1) * (c1 + 1));
+  T den = T(k.b1) * (c2sq - c1sq);
+  q.d0 = d0;
+  q.d1 = (c2sq * rho_p - Q) / den;
+  q.d2 = (Q - c1sq * rho_p) / den;
+  if (sizeof(T) == sizeof(float)) {
+    // eq 15 as e - (D/2)(gamma-1) e: the packets then carry exactly
+    // rho e = rho phi + Q/2 up to unbiased rounding; with the FP32-rounded
+    // constants kphi + kq/2 != 1 and every step would add a fixed bias
+    q.phi = e - T(0.5) * (T(k.kq) * e);
+  } else {
+    q.phi = T(k.kphi) * e;
+  }
+  T fl0 = dev_floor(q.V0);
+  q.n0 = (int)fl0;
+  q.f0 = q.V0 - fl0;
+  T fl1 = dev_floor(q.V1);
+  q.n1 = (int)fl1;
+  q.f1 = q.V1 - fl1;
+  q.emits = true;
+  return q;
+}
+
+// Packet p of the velocity set (Section IV): lattice offset and level.
+//   1-D: (0; d0), (+c1; d1), (-c1; d1), (+c2; d2), (-c2; d2)
+//   2-D: (+c1 ex), (-c1 ex), (+c1 ey), (-c1 ey) with d1, then the same with
+//        c2 and d2.
+template <int DIM>
+__device__ __forceinline__ void packet(int p, int c1, int* cx, int* cy,
+                                       int* lev) {
+  if (DIM == 1) {
+    int c = (p == 0) ? 0 : (p <= 2 ? c1 : c1 + 1);
+    *cx = (p == 2 || p == 4) ? -c : c;
+    *cy = 0;
+    *lev = (p == 0) ? 0 : (p <= 2 ? 1 : 2);
+  } else {
+    int lv = p >> 2;  // 0 -> level 1, 1 -> level 2
+    int c = c1 + lv;
+    int j = p & 3;
+    *cx = (j == 0) ? c : (j == 1 ? -c : 0);
+    *cy = (j == 2) ? c : (j == 3 ? -c : 0);
+    *lev = lv;  // index into the 2-D mass slots (d1, d2)
+  }
+}
+
+// Conservative migration reach of one node: >= floor(|V_a|) + 1 + c2 as the
+// step computes them, evaluated in FP32 with margins that cover its rounding
+// (an over-estimate only widens the source window).
+__device__ __forceinline__ int reach_bound(double rho, double mx, double my,
+                                           double rhoE, float kreach) {
+  if (!(rho > 0.0)) return 0;
+  float inv = 1.0f / (float)rho;
+  float v0 = fabsf((float)mx) * inv;
+  float v1 = fabsf((float)my) * inv;
+  float E = (float)rhoE * inv;
+  float kin = 0.5f * (v0 * v0 + v1 * v1);
+  float e = E - kin + 1e-5f * (fabsf(E) + kin);
+  e = fmaxf(e, 0.0f);
+  float X = kreach * e * 1.0001f;
+  float c1 = floorf(sqrtf(X));
+  float v = floorf(fmaxf(v0, v1) * 1.00001f);
+  float r = v + 1.0f + c1 + 1.0f;
+  return r > 1.0e8f ? 100000000 : (int)r;
+}
+
+template <typename T>
+__device__ __forceinline__ T ld(const void* p, long long i) {
+  return reinterpret_cast<const T*>(p)[i];
+}
+
+template <typename T, int DIM, bool KAHAN>
+__global__ void __launch_bounds__(256)
+    step_kernel(const StepArgs a) {
+  using S = TileShape<DIM>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red_sum[4][256 / 32];
+  __shared__ int red_reach[256 / 32];
+  __shared__ int is_last;
+
+  const int tid = threadIdx.x;
+  const int R = a.scr->reach;
+  if (R > a.r_cap) {
+    if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0)
+      atomicOr(&a.scr->flags, kFlagReach);
+    return;
+  }
+  const int Ry = (DIM == 2) ? R : 0;
+  const int x0 = blockIdx.x * S::TX;
+  const int y0 = blockIdx.y * S::TY;
+  const int W = S::TX + 2 * R;
+  const int H = (DIM == 2) ? S::TY + 2 * R : 1;
+  const int NS = W * H;
+
+  SrcLayout<T, DIM> L;
+  L.bind(smem_raw, a.r_cap);
+
+  // ---- 1. equilibrium packets of every source in reach of the tile ----
+  unsigned long long my_clamps = 0;
+  bool my_bad = false;
+  for (int i = tid; i < NS; i += 256) {
+    int ly = i / W;
+    int lx = i - ly * W;
+    long long sx = (long long)x0 - R + lx;
+    long long sy = (DIM == 2) ? (long long)y0 - R + ly : 0;
+    bool fx, fy = false;
+    int gx = virtual_axis(a.bc_x, a.nx, sx, &fx);
+    int gy = (DIM == 2) ? virtual_axis(a.bc_y, a.ny, sy, &fy) : 0;
+    long long g = (long long)gy * a.nx + gx;
+    T rho = ld<T>(a.in[0], g);
+    T mx = ld<T>(a.in[1], g);
+    T my = (DIM == 2) ? ld<T>(a.in[2], g) : T(0);
+    T rE = ld<T>(a.in[3], g);
+    if (fx) mx = -mx;
+    if (fy) my = -my;
+    Equil<T> q = equilibrium<T, DIM>(rho, mx, my, rE, a.k);
+    bool own = sx >= x0 && sx < x0 + S::TX && sx < a.nx &&
+               (DIM == 1 || (sy >= y0 && sy < y0 + S::TY && sy < a.ny));
+    if (own) {
+      my_clamps += q.clamp ? 1 : 0;
+      my_bad |= q.bad;
+    }
+    if (!q.emits) {
+      L.c1[i] = -1;
+      continue;
+    }
+    L.c1[i] = (short)q.c1;
+    L.n0[i] = (short)q.n0;
+    L.n1[i] = (short)q.n1;
+    L.f0[i] = q.f0;
+    if (DIM == 2) L.f1[i] = q.f1;
+    if (DIM == 1) {
+      L.mass[0 * L.cap + i] = q.d0;
+      L.mass[1 * L.cap + i] = q.d1;
+      L.mass[2 * L.cap + i] = q.d2;
+    } else {
+      L.mass[0 * L.cap + i] = q.d1;
+      L.mass[1 * L.cap + i] = q.d2;
+    }
+#pragma unroll
+    for (int p = 0; p < S::NP; ++p) {
+      int cx, cy, lev;
+      packet<DIM>(p, q.c1, &cx, &cy, &lev);
+      T d = L.mass[lev * L.cap + i];
+      T cbx = q.V0 + (T)cx;  // eq 12: V + c'
+      if (DIM == 1) {
+        L.Px[p * L.cap + i] = d * cbx;
+        L.PE[p * L.cap + i] = d * (T(0.5) * (cbx * cbx) + q.phi);
+      } else {
+        T cby = q.V1 + (T)cy;
+        L.Px[p * L.cap + i] = d * cbx;
+        L.Py[p * L.cap + i] = d * cby;
+        L.PE[p * L.cap + i] = d * (T(0.5) * (cbx * cbx + cby * cby) + q.phi);
+      }
+    }
+  }
+  if (my_clamps) atomicAdd(&a.scr->eclamps, my_clamps);
+  if (my_bad) atomicOr(&a.scr->flags, kFlagState);
+  __syncthreads();
+
+  // ---- 2. gather the arrivals at this thread's destination ----
+  const int tx = tid % S::TX;
+  const int ty = tid / S::TX;
+  const int dx = x0 + tx;
+  const int dy = y0 + ty;
+  const bool valid = dx < a.nx && dy < a.ny;
+  T tot[4] = {T(0), T(0), T(0), T(0)};
+  T comp[4] = {T(0), T(0), T(0), T(0)};
+  if (valid) {
+    for (int j = 0; j <= Ry; ++j) {
+      T pair[4];
+#pragma unroll 1
+      for (int side = 0; side < (j == 0 ? 1 : 2); ++side) {
+        const int sy = (side == 0) ? dy - j : dy + j;
+        const int ly = (DIM == 2) ? sy - (y0 - R) : 0;  // 1-D: one row
+        const int base = ly * W + tx;  // source dx - R sits at lx = tx
+        T r = T(0), x = T(0), y = T(0), e = T(0);
+        for (int i = 0; i <= 2 * R; ++i) {
+          const int s = base + i;
+          const int c1 = L.c1[s];
+          if (c1 < 0) continue;
+          const int c2 = c1 + 1;
+          const int ox = R - i - L.n0[s];
+          const int oy = (DIM == 2) ? (dy - sy) - L.n1[s] : 0;
+          bool near_x = ox >= -c2 && ox <= c2 + 1;
+          if (DIM == 1) {
+            if (!near_x) continue;
+          } else {
+            bool near_y = oy >= -c2 && oy <= c2 + 1;
+            bool xarm = (oy == 0 || oy == 1) && near_x;
+            bool yarm = (ox == 0 || ox == 1) && near_y;
+            if (!xarm && !yarm) continue;
+          }
+          const T fx0 = L.f0[s];
+          const T wx[2] = {T(1) - fx0, fx0};
+          T wy[2] = {T(1), T(0)};
+          if (DIM == 2) {
+            const T fy0 = L.f1[s];
+            wy[0] = T(1) - fy0;
+            wy[1] = fy0;
+          }
+#pragma unroll
+          for (int p = 0; p < S::NP; ++p) {
+            int cx, cy, lev;
+            packet<DIM>(p, c1, &cx, &cy, &lev);
+#pragma unroll
+            for (int kk = 0; kk < S::NK; ++kk) {
+              const int kx = kk & 1, ky = kk >> 1;
+              if (cx + kx != ox) continue;
+              if (DIM == 2 && cy + ky != oy) continue;
+              const T al = (DIM == 1) ? wx[kx] : wx[kx] * wy[ky];
+              r = r + al * L.mass[lev * L.cap + s];
+              x = x + al * L.Px[p * L.cap + s];
+              if (DIM == 2) y = y + al * L.Py[p * L.cap + s];
+              e = e + al * L.PE[p * L.cap + s];
+            }
+          }
+        }
+        if (side == 0) {
+          pair[0] = r;
+          pair[1] = x;
+          pair[2] = y;
+          pair[3] = e;
+        } else {
+          pair[0] = pair[0] + r;
+          pair[1] = pair[1] + x;
+          pair[2] = pair[2] + y;
+          pair[3] = pair[3] + e;
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        if (KAHAN) {  // compensated sum of the row-pair sums
+          T yk = pair[f] - comp[f];
+          T t = tot[f] + yk;
+          comp[f] = (t - tot[f]) - yk;
+          tot[f] = t;
+        } else {
+          tot[f] = tot[f] + pair[f];
+        }
+      }
+    }
+  }
+
+  // ---- 3. write, reach of the new state, FP64 totals ----
+  int my_reach = 0;
+  if (valid) {
+    const long long o = (long long)dy * a.nx + dx;
+    reinterpret_cast<T*>(a.out[0])[o] = tot[0];
+    reinterpret_cast<T*>(a.out[1])[o] = tot[1];
+    if (DIM == 2) reinterpret_cast<T*>(a.out[2])[o] = tot[2];
+    reinterpret_cast<T*>(a.out[3])[o] = tot[3];
+    my_reach = reach_bound((double)tot[0], (double)tot[1],
+                           DIM == 2 ? (double)tot[2] : 0.0, (double)tot[3],
+                           (float)a.k.kreach);
+  }
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+    my_reach = max(my_reach, __shfl_xor_sync(0xffffffffu, my_reach, off));
+  double ps[4] = {0.0, 0.0, 0.0, 0.0};
+  if (a.do_cons) {
+    if (valid) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) ps[f] = (double)tot[f];
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1)
+        ps[f] += __shfl_down_sync(0xffffffffu, ps[f], off);
+  }
+  if (lane == 0) {
+    red_reach[warp] = my_reach;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) red_sum[f][warp] = ps[f];
+  }
+  __syncthreads();
+  const int nblk = a.nblocks;
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  if (tid == 0) {
+    int rb = red_reach[0];
+    double bs[4] = {red_sum[0][0], red_sum[1][0], red_sum[2][0], red_sum[3][0]};
+    for (int w = 1; w < 256 / 32; ++w) {
+      rb = max(rb, red_reach[w]);
+#pragma unroll
+      for (int f = 0; f < 4; ++f) bs[f] += red_sum[f][w];
+    }
+    atomicMax(&a.scr->reach_next, rb);
+    if (a.do_cons) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) a.part[(long long)bid * 4 + f] = bs[f];
+    }
+    __threadfence();
+    unsigned done = atomicAdd(&a.scr->ticket, 1u);
+    is_last = (done == (unsigned)(nblk - 1));
+  }
+  __syncthreads();
+  if (!is_last) return;
+
+  // ---- last block: publish reach and totals (fixed order) ----
+  __threadfence();
+  if (a.do_cons) {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = tid; b < nblk; b += 256) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) s[f] += __ldcg(&a.part[(long long)b * 4 + f]);
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1)
+        s[f] += __shfl_down_sync(0xffffffffu, s[f], off);
+    if (lane == 0) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) red_sum[f][warp] = s[f];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int f = 0; f < 4; ++f) {
+        double t = red_sum[f][0];
+        for (int w = 1; w < 256 / 32; ++w) t += red_sum[f][w];
+        a.scr->cons[f] = t;
+      }
+    }
+  }
+  if (tid == 0) {
+    int rn = atomicAdd(&a.scr->reach_next, 0);
+    a.scr->reach = rn;
+    a.scr->reach_next = 0;
+    a.scr->ticket = 0u;
+    __threadfence();
+  }
+}
+
+template <typename T, int DIM>
+size_t step_smem_bytes_t(int r_cap) {
+  return SrcLayout<T, DIM>::bytes(r_cap);
+}
+
+}  // namespace lbm

@@ -1,0 +1,214 @@
+"""ctypes binding of the C ABI declared in include/lbm.h.
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  The functions keep the ABI's names; ``Solver`` bundles a handle
+with numpy-array helpers.  There is no fallback: if ``liblbm.so`` is missing
+or the GPU is absent, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, EREACH, ETIMEOUT, EBUDGET = range(8)
+STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA",
+                4: "LBM_ESTATE", 5: "LBM_EREACH", 6: "LBM_ETIMEOUT",
+                7: "LBM_EBUDGET"}
+F32, F64 = 0, 1
+TRANSMISSIVE, REFLECTING, PERIODIC = 0, 1, 2
+PLANAR_X, CIRCLE = 0, 1
+
+
+class lbm_config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
+                ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("theta", ctypes.c_double), ("dt", ctypes.c_double),
+                ("max_reach", ctypes.c_int32), ("kahan", ctypes.c_int32),
+                ("cons_every", ctypes.c_int32), ("reserved_", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class lbm_prim(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double), ("u", ctypes.c_double),
+                ("v", ctypes.c_double), ("p", ctypes.c_double)]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+_DP = ctypes.POINTER(ctypes.c_double)
+_H = ctypes.c_void_p
+
+
+def load() -> ctypes.CDLL:
+    """Load liblbm.so (built by __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "lbm_abi_version": ([], ctypes.c_int32),
+        "lbm_create": ([ctypes.POINTER(lbm_config), ctypes.POINTER(_H)], ctypes.c_int),
+        "lbm_init_riemann": ([_H, ctypes.POINTER(lbm_prim), ctypes.POINTER(lbm_prim),
+                              ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                              ctypes.c_double], ctypes.c_int),
+        "lbm_set_primitives": ([_H, _DP, _DP, _DP, _DP, ctypes.c_int64], ctypes.c_int),
+        "lbm_set_moments": ([_H, _DP, _DP, _DP, _DP, ctypes.c_int64], ctypes.c_int),
+        "lbm_step": ([_H, ctypes.c_int64], ctypes.c_int),
+        "lbm_moments": ([_H, _DP, _DP, _DP, _DP, _DP, ctypes.c_int64], ctypes.c_int),
+        "lbm_conservation": ([_H, _DP], ctypes.c_int),
+        "lbm_reach": ([_H, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "lbm_diagnostics": ([_H, ctypes.POINTER(ctypes.c_int64),
+                             ctypes.POINTER(ctypes.c_int64),
+                             ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+        "lbm_synchronize": ([_H], ctypes.c_int),
+        "lbm_lambda": ([_H], ctypes.c_double),
+        "lbm_last_error": ([_H], ctypes.c_char_p),
+        "lbm_destroy": ([_H], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _dp(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_DP)
+
+
+def _f64(a, n):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != n:
+        raise ValueError(f"array of {a.size} values, expected {n}")
+    return a
+
+
+def _check(h, st):
+    if st != OK:
+        msg = load().lbm_last_error(h)
+        raise LbmError(st, msg.decode() if msg else "")
+
+
+def make_config(dim, nx, ny=1, *, x0=0.0, x1=1.0, y0=0.0, gamma=1.4,
+                theta=None, dt=None, precision=F64, bc_x=TRANSMISSIVE,
+                bc_y=REFLECTING, max_reach=0, kahan=1, cons_every=0,
+                stream=None) -> lbm_config:
+    """lbm_config with the defaults of the Sod problem (Section V.C)."""
+    dx = (x1 - x0) / nx
+    if theta is None:
+        theta = 0.5 if dim == 1 else 0.0
+    return lbm_config(dim, precision, bc_x, bc_y, nx, ny if dim == 2 else 1,
+                      x0, x1, y0, gamma, theta, dx if dt is None else dt,
+                      max_reach, kahan, cons_every, 0, stream)
+
+
+class Solver:
+    """One handle of the C ABI."""
+
+    def __init__(self, cfg: lbm_config):
+        lib = load()
+        self.cfg = cfg
+        self.n = cfg.nx * cfg.ny
+        self.dim = cfg.dim
+        h = _H()
+        st = lib.lbm_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != OK:
+            raise LbmError(st, "lbm_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbm_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def lam(self) -> float:
+        return load().lbm_lambda(self.h)
+
+    def init_riemann(self, inner, outer, geom=PLANAR_X, a0=0.5, a1=0.5,
+                     radius=0.0):
+        """inner/outer: (rho, u, p) or (rho, u, v, p)."""
+        def prim(s):
+            s = tuple(float(v) for v in s)
+            return lbm_prim(*(s if len(s) == 4 else (s[0], s[1], 0.0, s[2])))
+        a, b = prim(inner), prim(outer)
+        _check(self.h, load().lbm_init_riemann(self.h, ctypes.byref(a),
+                                               ctypes.byref(b), geom, a0, a1,
+                                               radius))
+
+    def set_primitives(self, rho, u, v, p):
+        n = self.n
+        rho, u, v, p = (_f64(x, n) for x in (rho, u, v, p))
+        _check(self.h, load().lbm_set_primitives(self.h, _dp(rho), _dp(u),
+                                                 _dp(v), _dp(p), n))
+
+    def set_moments(self, rho, mx, my, rhoE):
+        n = self.n
+        rho, mx, my, rhoE = (_f64(x, n) for x in (rho, mx, my, rhoE))
+        _check(self.h, load().lbm_set_moments(self.h, _dp(rho), _dp(mx),
+                                              _dp(my), _dp(rhoE), n))
+
+    def step(self, nsteps=1):
+        _check(self.h, load().lbm_step(self.h, int(nsteps)))
+
+    def moments(self, out=None) -> dict:
+        """Physical rho, mx, my (2-D), rhoE, p as float64 arrays."""
+        n = self.n
+        if out is None:
+            out = {k: np.empty(n) for k in ("rho", "mx", "rhoE", "p")}
+            if self.dim == 2:
+                out["my"] = np.empty(n)
+        _check(self.h, load().lbm_moments(
+            self.h, _dp(out["rho"]), _dp(out["mx"]), _dp(out.get("my")),
+            _dp(out["rhoE"]), _dp(out.get("p")), n))
+        return out
+
+    def conservation(self) -> np.ndarray:
+        out = np.zeros(4)
+        _check(self.h, load().lbm_conservation(self.h, _dp(out)))
+        return out
+
+    def reach(self) -> int:
+        r = ctypes.c_int32(0)
+        _check(self.h, load().lbm_reach(self.h, ctypes.byref(r)))
+        return r.value
+
+    def diagnostics(self) -> dict:
+        s, e, f = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_uint32(0)
+        _check(self.h, load().lbm_diagnostics(self.h, ctypes.byref(s),
+                                              ctypes.byref(e), ctypes.byref(f)))
+        return {"steps": s.value, "eclamps": e.value, "flags": f.value}
+
+    def synchronize(self):
+        _check(self.h, load().lbm_synchronize(self.h))
