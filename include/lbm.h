@@ -34,6 +34,7 @@
 #ifndef LBM_H
 #define LBM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -175,6 +176,55 @@ const char* lbm_last_error(const lbm_handle* h);
 /* Free the handle and its device memory.  NULL-safe.  Waits for queued
    work first. */
 void lbm_destroy(lbm_handle* h);
+
+/* ---- allocation-free single step --------------------------------------
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc: code running under an allocator it does not
+ * own, services that must reserve all their memory up front, or real-time
+ * loops where an allocation could stall.  It performs one tau = 1 step, the
+ * same fused kernel as lbm_step, from caller-owned device arrays to
+ * caller-owned device arrays, and allocates nothing (no cudaMalloc, no
+ * cudaFree, no allocating library routine).
+ *
+ * Its scratch (migration reach, error flags, a block ticket and the FP64
+ * partial sums for the totals) is one static device array of
+ * LBM_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds
+ * until the process exits.  It bounds the grid: at most 32,760 tiles of the
+ * step kernel (1-D tiles are 256 nodes, 2-D tiles 32 x 8 nodes: about 8.3
+ * million nodes).  Larger grids are rejected with LBM_EINVAL and a message
+ * naming the limit; use lbm_create / lbm_step for them.
+ *
+ * Arrays are in lattice units (m = rho u lambda, rhoE scaled by lambda^2),
+ * element type float (LBM_F32) or double (LBM_F64), nx*ny nodes, x fastest,
+ * order {rho, m_x, m_y, rhoE}; m_y may be NULL in 1-D.  in and out must not
+ * overlap.  totals (4 doubles), reach (1 int32) and flags (1 uint32, bit 0
+ * LBM_ESTATE, bit 1 LBM_EREACH) are optional device pointers that receive
+ * the new state's FP64 totals, the reach of the new state and the device
+ * error flags.  The maximum reach is the lbm_create default (1-D 64, 2-D 6).
+ * Work is queued on stream (cudaStream_t, NULL = default stream); the call
+ * returns without waiting, so device-side errors arrive through flags.
+ * err (nullable, err_len bytes) receives a message on failure.
+ *
+ * Every call shares the one scratch array, which keeps the last call's
+ * contents; each call clears the part that must start at zero.  Calls that
+ * overlap on the GPU (different streams or threads at the same time) race
+ * on it and must be serialized by the caller.  The first call on a device
+ * looks up the array's device address (once per device, with that device
+ * current); make that first call before any stream capture.
+ */
+#define LBM_NOALLOC_SCRATCH_BYTES (1u << 20)
+
+typedef struct {
+  int32_t dim, precision, bc_x, bc_y;
+  int64_t nx, ny;
+  double gamma, theta;
+} lbm_noalloc_desc;
+
+lbm_status lbm_step_noalloc(const lbm_noalloc_desc* d, const void* const in[4],
+                            void* const out[4], double* totals, int32_t* reach,
+                            uint32_t* flags, void* stream, char* err,
+                            size_t err_len);
 
 #ifdef __cplusplus
 }

@@ -44,3 +44,27 @@ cudaError_t step_prepare_f32(int dim, size_t smem) {
 }
 
 }  // namespace lbm
+
+namespace lbm {
+
+// Raise (never lower) the dynamic shared-memory limit of the FP32 step
+// kernels so a launch needing smem bytes is allowed.
+cudaError_t step_raise_smem_f32(int dim, size_t smem) {
+  const void* fns[2] = {
+      dim == 1 ? (const void*)step_kernel<float, 1, true>
+               : (const void*)step_kernel<float, 2, true>,
+      dim == 1 ? (const void*)step_kernel<float, 1, false>
+               : (const void*)step_kernel<float, 2, false>};
+  for (const void* fn : fns) {
+    cudaFuncAttributes at;
+    cudaError_t e = cudaFuncGetAttributes(&at, fn);
+    if (e != cudaSuccess) return e;
+    if ((size_t)at.maxDynamicSharedSizeBytes >= smem) continue;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace lbm

@@ -34,3 +34,20 @@ cudaError_t step_prepare_f64(int dim, size_t smem) {
 }
 
 }  // namespace lbm
+
+namespace lbm {
+
+// Raise (never lower) the dynamic shared-memory limit of the FP64 step
+// kernel so a launch needing smem bytes is allowed.
+cudaError_t step_raise_smem_f64(int dim, size_t smem) {
+  cudaFuncAttributes at;
+  const void* fn = dim == 1 ? (const void*)step_kernel<double, 1, false>
+                            : (const void*)step_kernel<double, 2, false>;
+  cudaError_t e = cudaFuncGetAttributes(&at, fn);
+  if (e != cudaSuccess) return e;
+  if ((size_t)at.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+}
+
+}  // namespace lbm

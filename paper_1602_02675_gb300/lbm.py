@@ -41,6 +41,13 @@ class lbm_prim(ctypes.Structure):
                 ("v", ctypes.c_double), ("p", ctypes.c_double)]
 
 
+class lbm_noalloc_desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
+                ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("gamma", ctypes.c_double), ("theta", ctypes.c_double)]
+
+
 class LbmError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -82,6 +89,11 @@ def load() -> ctypes.CDLL:
         "lbm_lambda": ([_H], ctypes.c_double),
         "lbm_last_error": ([_H], ctypes.c_char_p),
         "lbm_destroy": ([_H], None),
+        "lbm_step_noalloc": ([ctypes.POINTER(lbm_noalloc_desc),
+                              ctypes.c_void_p * 4, ctypes.c_void_p * 4,
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t],
+                             ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -212,3 +224,19 @@ class Solver:
 
     def synchronize(self):
         _check(self.h, load().lbm_synchronize(self.h))
+
+
+def lbm_step_noalloc(desc: lbm_noalloc_desc, inputs, outputs, totals=0,
+                     reach=0, flags=0, stream=0) -> None:
+    """One step between caller-owned device arrays (integer device
+    addresses, order rho, m_x, m_y, rhoE; 0 for m_y in 1-D) without any
+    allocation by the library.  Raises LbmError with the library's message."""
+    lib = load()
+    ins = (ctypes.c_void_p * 4)(*[a or None for a in inputs])
+    outs = (ctypes.c_void_p * 4)(*[a or None for a in outputs])
+    err = ctypes.create_string_buffer(512)
+    st = lib.lbm_step_noalloc(ctypes.byref(desc), ins, outs, totals or None,
+                              reach or None, flags or None, stream or None,
+                              err, len(err))
+    if st != OK:
+        raise LbmError(st, err.value.decode())
