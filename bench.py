@@ -133,15 +133,17 @@ def run_ours(args, rank, world):
     def make(prec, cons_every=1):
         if args.workload == "cylinder2d":
             cfg = L.make_config(2, nx, ny, dt=lam * dx, precision=prec,
-                                bc_x=L.PERIODIC, bc_y=L.PERIODIC, kahan=1,
-                                cons_every=cons_every, stream=stream.cuda_stream)
+                                bc_x=L.PERIODIC, bc_y=L.PERIODIC,
+                                kahan=args.kahan, cons_every=cons_every,
+                                stream=stream.cuda_stream)
             s = L.Solver(cfg)
             s.init_riemann((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1),
                            L.CIRCLE, 0.5, 0.5, 0.4)
             return s
         cfg = L.make_config(2, nx, ny, dt=lam * dx, precision=prec,
-                            bc_x=L.TRANSMISSIVE, bc_y=L.REFLECTING, kahan=1,
-                            cons_every=cons_every, stream=stream.cuda_stream)
+                            bc_x=L.TRANSMISSIVE, bc_y=L.REFLECTING,
+                            kahan=args.kahan, cons_every=cons_every,
+                            stream=stream.cuda_stream)
         s = L.Solver(cfg)
         s.init_riemann((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), L.PLANAR_X, 0.5)
         return s
@@ -202,7 +204,8 @@ def run_ours(args, rank, world):
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
             "unit": "GB/s", "frac": round(achieved / peak, 4),
             "traffic": args.traffic, "peak_kind": peak_kind,
-            "kernel": "step_kernel<float,2,true>",
+            "kernel": ("lbm::fast::step2d_f32" if args.kahan == 0
+                       else "step_kernel<float,2,true>"),
             "bytes_per_launch": bytes_per_launch}
     mean64 = t64 / k64 * 1e3
     line = {
@@ -249,8 +252,8 @@ def run_e2e(args, L, torch, stream, lam, nsolve, world):
     rhoE[:] = np.where(left, 1.0, 0.1) / 0.4
     outs = {k: pin() for k in ("rho", "mx", "my", "rhoE", "p")}
     cfg = L.make_config(2, NX, NY, dt=lam * dx, precision=L.F32,
-                        bc_x=L.TRANSMISSIVE, bc_y=L.REFLECTING, kahan=1,
-                        stream=stream.cuda_stream)
+                        bc_x=L.TRANSMISSIVE, bc_y=L.REFLECTING,
+                        kahan=args.kahan, stream=stream.cuda_stream)
     times = []
     with L.Solver(cfg) as s:
         for rep in range(1 + args.e2e_solves):
@@ -366,6 +369,9 @@ def main():
     ap.add_argument("--no-l1", action="store_true")
     ap.add_argument("--workload", default="sod2d", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="both", choices=["both", "f32"])
+    ap.add_argument("--kahan", type=int, default=0, choices=[0, 1],
+                    help="FP32 kernel: 0 register kernel, 1 compensated "
+                         "exact-order kernel")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

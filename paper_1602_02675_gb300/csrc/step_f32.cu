@@ -1,4 +1,5 @@
 // FP32 step kernels (compensated or plain summation of the row-pair sums).
+#include "step_fast_f32.cuh"
 #include "step_kernel.cuh"
 
 namespace lbm {
@@ -11,20 +12,23 @@ cudaError_t launch_step_f32(int dim, const StepArgs& a, size_t smem,
       step_kernel<float, 1, true><<<grid, 256, smem, s>>>(a);
     else
       step_kernel<float, 1, false><<<grid, 256, smem, s>>>(a);
-  } else {
+  } else if (a.kahan || a.r_cap > fast::RMAX) {
     dim3 grid((a.nx + TileShape<2>::TX - 1) / TileShape<2>::TX,
               (a.ny + TileShape<2>::TY - 1) / TileShape<2>::TY);
-    if (a.kahan)
-      step_kernel<float, 2, true><<<grid, 256, smem, s>>>(a);
-    else
-      step_kernel<float, 2, false><<<grid, 256, smem, s>>>(a);
+    step_kernel<float, 2, true><<<grid, 256, smem, s>>>(a);
+  } else {
+    dim3 grid((a.nx + fast::TX - 1) / fast::TX, (a.ny + fast::TY - 1) / fast::TY);
+    StepArgs b = a;  // the last-block ticket counts this kernel's tiles
+    b.nblocks = (int)(grid.x * grid.y);
+    fast::step2d_f32<<<grid, fast::NTHR, smem, s>>>(b);
   }
   return cudaGetLastError();
 }
 
 size_t step_smem_f32(int dim, int r_cap) {
-  return dim == 1 ? step_smem_bytes_t<float, 1>(r_cap)
-                  : step_smem_bytes_t<float, 2>(r_cap);
+  if (dim == 1) return step_smem_bytes_t<float, 1>(r_cap);
+  size_t g = step_smem_bytes_t<float, 2>(r_cap), f = fast::smem_bytes();
+  return g > f ? g : f;
 }
 
 cudaError_t step_prepare_f32(int dim, size_t smem) {
@@ -39,7 +43,10 @@ cudaError_t step_prepare_f32(int dim, size_t smem) {
   e = cudaFuncSetAttribute(step_kernel<float, 2, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(step_kernel<float, 2, false>,
+  e = cudaFuncSetAttribute(step_kernel<float, 2, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fast::step2d_f32,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
@@ -50,11 +57,13 @@ namespace lbm {
 // Raise (never lower) the dynamic shared-memory limit of the FP32 step
 // kernels so a launch needing smem bytes is allowed.
 cudaError_t step_raise_smem_f32(int dim, size_t smem) {
-  const void* fns[2] = {
+  const void* fns[3] = {
       dim == 1 ? (const void*)step_kernel<float, 1, true>
                : (const void*)step_kernel<float, 2, true>,
       dim == 1 ? (const void*)step_kernel<float, 1, false>
-               : (const void*)step_kernel<float, 2, false>};
+               : (const void*)step_kernel<float, 2, false>,
+      dim == 1 ? (const void*)step_kernel<float, 1, false>
+               : (const void*)fast::step2d_f32};
   for (const void* fn : fns) {
     cudaFuncAttributes at;
     cudaError_t e = cudaFuncGetAttributes(&at, fn);

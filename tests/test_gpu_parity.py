@@ -148,13 +148,51 @@ def test_sod_1d_fp32_l1(kahan):
     _assert_l1(g, o, 1)
 
 
-@pytest.mark.parametrize("bcs", BC2[:2])
-def test_random_2d_fp32_l1(bcs):
-    nx, ny = 70, 21
+@pytest.mark.parametrize("kahan", [1, 0])
+@pytest.mark.parametrize("bcs", BC2)
+def test_random_2d_fp32_l1(bcs, kahan):
+    """kahan = 1: compensated exact-order kernel; kahan = 0: the register
+    kernel (uniform-type tiles on the fast path, mixed tiles on the general
+    path: this smooth field with a jump has both)."""
+    nx, ny = 70, 45
     prims = I.random_smooth_prims(2, nx, ny, seed=3000 + bcs[0])
-    g = _gpu(2, nx, ny, *bcs, prims=prims, steps=20, precision=L.F32)
+    g = _gpu(2, nx, ny, *bcs, prims=prims, steps=20, precision=L.F32,
+             kahan=kahan)
     o = _oracle(2, nx, ny, *bcs, prims=prims, steps=20)
     _assert_l1(g, o, 2)
+
+
+@pytest.mark.parametrize("kahan", [1, 0])
+def test_xonly_strong_jump_fp32_rows_identical(kahan):
+    """x-only data whose level c1 changes across the jump (c1 = 1 | 0: mixed
+    tiles on the general path) between reflecting walls: rows stay identical
+    bit for bit and m_y stays zero, and the rows match the oracle's x-only
+    run.  (Much stronger jumps make the square-lattice step chaotic even for
+    x-only data - a 1e-12 perturbation reaches O(1) - so no two
+    implementations can agree there.)"""
+    nx, ny = 300, 70
+    riem = ((1.0, 0.0, 1.0), (1.0, 0.0, 0.3), 0, 0.5, 0.5, 0.0)
+    g = _gpu(2, nx, ny, L.TRANSMISSIVE, L.REFLECTING, riemann=riem, steps=150,
+             precision=L.F32, kahan=kahan)
+    for f in FIELDS:
+        rows = g[f].reshape(ny, nx)
+        assert np.array_equal(rows, np.broadcast_to(rows[0], rows.shape)), f
+    assert np.all(g["my"] == 0.0)
+    o = _oracle(2, nx, 1, O.TRANSMISSIVE, O.REFLECTING, riemann=riem,
+                steps=150)
+    row = {f: g[f].reshape(ny, nx)[0] for f in FIELDS}
+    _assert_l1(row, o, 2)
+
+
+@pytest.mark.parametrize("kahan", [1, 0])
+def test_uniform_state_fp32_bitwise(kahan):
+    n = 96
+    prims = [np.full(n * n, 0.8), np.full(n * n, 0.37), np.full(n * n, -0.61),
+             np.full(n * n, 0.9)]
+    g = _gpu(2, n, n, L.PERIODIC, L.PERIODIC, prims=prims, steps=25,
+             precision=L.F32, kahan=kahan)
+    for f in FIELDS:
+        assert np.all(g[f] == g[f][0])
 
 
 def test_sod_2d_full_size_rows_match_oracle():
@@ -167,9 +205,9 @@ def test_sod_2d_full_size_rows_match_oracle():
     n, lam = O.steps_and_lambda(0.2, 1.0 / nx)
     o = _oracle(2, nx, 1, O.TRANSMISSIVE, O.REFLECTING, riemann=SOD, steps=n,
                 lam=lam)
-    for prec in (L.F64, L.F32):
+    for prec, kahan in ((L.F64, 1), (L.F32, 1), (L.F32, 0)):
         g = _gpu(2, nx, ny, L.TRANSMISSIVE, L.REFLECTING, riemann=SOD,
-                 steps=n, lam=lam, precision=prec)
+                 steps=n, lam=lam, precision=prec, kahan=kahan)
         for f in FIELDS:
             rows = g[f].reshape(ny, nx)
             assert np.array_equal(rows, np.broadcast_to(rows[0], rows.shape))
@@ -184,9 +222,10 @@ def test_sod_2d_full_size_rows_match_oracle():
 def test_conservation_periodic_gpu():
     nx, ny = 96, 40
     prims = I.random_smooth_prims(2, nx, ny, seed=44, jump=False)
-    for prec, tol in ((L.F64, 1e-13), (L.F32, 1e-6)):
+    for prec, tol, kahan in ((L.F64, 1e-13, 1), (L.F32, 1e-6, 1),
+                             (L.F32, 1e-6, 0)):
         cfg = L.make_config(2, nx, ny, precision=prec, bc_x=L.PERIODIC,
-                            bc_y=L.PERIODIC)
+                            bc_y=L.PERIODIC, kahan=kahan)
         with L.Solver(cfg) as s:
             s.set_primitives(*prims)
             t0 = s.conservation()
