@@ -323,6 +323,70 @@ def l1_vs_oracle(L) -> dict:
     return out
 
 
+def run_tubes(args):
+    """Batched 1-D tubes (4096 seeded tubes, 256..16384 nodes, pressure
+    ratio 2..100, density ratio 1..10, at rest, t = 0.2): solves/s of the
+    batched FP32 path (one persistent launch per step, CUDA graphs) against
+    the plain FP64 path that solves one tube at a time through a handle."""
+    import torch
+    from paper_1602_02675_gb300 import inputs as I
+    from paper_1602_02675_gb300 import lbm as L
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    specs = I.tubes_batch(args.tubes)
+    tubes, nus = [], 0
+    for t in specs:
+        ns, lam = t.steps_and_lambda(T_END)
+        tubes.append(L.make_tube(t.n, ns, lam / t.n, t.left, t.right))
+        nus += t.n * ns
+    stream = torch.cuda.Stream()
+    times = []
+    for rep in range(1 + args.batch_reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with L.Batch(tubes, precision=L.F32, kahan=1,
+                     stream=stream.cuda_stream) as b:
+            b.run()
+            b.sync()
+        dt = time.perf_counter() - t0
+        if rep > 0:
+            times.append(dt)
+    tb = statistics.median(times)
+    # plain FP64 one tube at a time, seeded subsample
+    rng = __import__("random").Random(20260)
+    sub = rng.sample(range(len(specs)), min(args.seq_tubes, len(specs)))
+    t64, nus64, lat = 0.0, 0, []
+    for j in sub:
+        t = specs[j]
+        ns, lam = t.steps_and_lambda(T_END)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cfg = L.make_config(1, t.n, dt=lam / t.n, precision=L.F64,
+                            bc_x=L.TRANSMISSIVE, stream=stream.cuda_stream)
+        with L.Solver(cfg) as s:
+            s.init_riemann(t.left, t.right, L.PLANAR_X, 0.5)
+            s.step(ns)
+            s.moments()
+        d = time.perf_counter() - t0
+        t64 += d
+        lat.append(d)
+        nus64 += t.n * ns
+    solves_b = len(specs) / tb
+    solves_64 = len(sub) / t64
+    lat.sort()
+    return {
+        "metric": "solves/s", "value": solves_b, "unit": "solves/s",
+        "workload": f"tubes_batch_{len(specs)}", "dtype": "f32",
+        "batched": {"solves_per_s": solves_b, "node_updates_per_s": nus / tb,
+                    "wall_s": tb, "node_updates": nus, "tubes": len(specs)},
+        "plain_fp64_one_at_a_time": {
+            "solves_per_s": solves_64, "node_updates_per_s": nus64 / t64,
+            "sample_tubes": len(sub),
+            "latency_ms_p50": 1e3 * lat[len(lat) // 2],
+            "latency_ms_p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "speedup_solves_per_s": solves_b / solves_64,
+    }
+
+
 def run_reference(args, rank, world):
     """The CPU oracle as it stands: K bounded samples of the workload."""
     if rank != 0:
@@ -367,7 +431,11 @@ def main():
                     help="ncu dram bytes per step-kernel launch, if measured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-l1", action="store_true")
-    ap.add_argument("--workload", default="sod2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="sod2d",
+                    choices=sorted(WORKLOADS) + ["tubes"])
+    ap.add_argument("--tubes", type=int, default=4096)
+    ap.add_argument("--batch-reps", type=int, default=2)
+    ap.add_argument("--seq-tubes", type=int, default=24)
     ap.add_argument("--precision", default="both", choices=["both", "f32"])
     ap.add_argument("--kahan", type=int, default=0, choices=[0, 1],
                     help="FP32 kernel: 0 register kernel, 1 compensated "
@@ -378,6 +446,9 @@ def main():
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.workload == "tubes":
+        print(json.dumps(run_tubes(args)))
+        return
     if args.impl == "reference":
         line = run_reference(args, rank, world)
         if line is not None:

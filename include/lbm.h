@@ -177,6 +177,59 @@ const char* lbm_last_error(const lbm_handle* h);
    work first. */
 void lbm_destroy(lbm_handle* h);
 
+/* ---- batched 1-D tubes --------------------------------------------------
+ *
+ * Many independent 1-D shock tubes (Section V.C, each on [0, 1] with its own
+ * node count, Riemann state, time step and step count) advanced together:
+ * one persistent kernel launch per step covers every tube that still has
+ * steps to take, and the launches are replayed from a captured CUDA graph.
+ * Each tube's step is the same tau = 1 step as lbm_step on a 1-D handle
+ * (eq 10; Section III.B; Section IV.A; Section V.B), so in FP64 a tube's
+ * result is the result of running it alone.
+ */
+typedef struct lbm_batch lbm_batch;
+
+typedef struct {
+  int64_t n;       /* nodes; dx = 1/n */
+  int64_t nsteps;  /* steps this tube takes */
+  double dt;       /* time step; lambda = dt*n */
+  double x_d;      /* diaphragm position in (0, 1) */
+  lbm_prim left, right;  /* states for x < x_d and x >= x_d (v ignored) */
+  int32_t bc;      /* lbm_bc at both ends */
+  int32_t pad_;
+} lbm_tube;
+
+/* Create a batch: device buffers for all tubes, their initial states and
+   first reach.  precision: lbm_precision; theta as lbm_config.theta; kahan
+   (F32): compensated summation of each destination's arrivals.  Tubes keep
+   the caller's indices in every other call.  Synchronous. */
+lbm_status lbm_batch_create(int32_t precision, double gamma, double theta,
+                            int32_t kahan, const lbm_tube* tubes, int64_t count,
+                            void* stream, lbm_batch** out);
+
+/* Queue up to max_launches steps (negative: until every tube has taken its
+   steps).  One persistent launch per step; stream-ordered, does not wait. */
+lbm_status lbm_batch_run(lbm_batch* b, int64_t max_launches);
+
+/* Wait; report launches executed and device flags (bit 0 LBM_ESTATE, bit 1
+   LBM_EREACH).  Either pointer may be NULL. */
+lbm_status lbm_batch_sync(lbm_batch* b, int64_t* steps_done, uint32_t* flags);
+
+/* Physical rho, rho*u, rho*E and (if p != NULL) pressure of one tube after
+   its last step (or its latest step if the batch has not finished).  n must
+   be the tube's node count.  Waits. */
+lbm_status lbm_batch_moments(lbm_batch* b, int64_t tube, double* rho,
+                             double* mx, double* rhoE, double* p, int64_t n);
+
+/* FP64 totals (rho, rho*u, rho*E; physical units) of every tube, 3 per tube
+   in the caller's order; count = number of tubes.  Waits. */
+lbm_status lbm_batch_totals(lbm_batch* b, double* out, int64_t count);
+
+const char* lbm_batch_last_error(const lbm_batch* b);
+
+/* Free a batch; NULL-safe; waits for queued work. */
+void lbm_batch_destroy(lbm_batch* b);
+
 /* ---- allocation-free single step --------------------------------------
  *
  * The paper has no counterpart to this entry point; it exists for callers

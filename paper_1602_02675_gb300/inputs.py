@@ -14,6 +14,7 @@ Workloads (Section V.C shock tube and its extensions):
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -95,6 +96,21 @@ class Tube:
     n: int
     left: tuple   # (rho, u, p)
     right: tuple
+
+    def lattice_speed_scale(self) -> float:
+        """lambda0 = dt/dx before rounding to a whole number of steps:
+        1 unless one side is hotter (larger p/rho) than the left Sod state
+        (1, 0, 1); then scaled down so that the hottest initial state has
+        that same lattice temperature: lambda0^2 max(p/rho) = 1."""
+        t = max(self.left[2] / self.left[0], self.right[2] / self.right[0])
+        return min(1.0, (1.0 / t) ** 0.5)
+
+    def steps_and_lambda(self, t_end: float = 0.2):
+        """Whole number of steps reaching t_end with dt/dx <= lambda0."""
+        dx = 1.0 / self.n
+        n = max(1, int(math.ceil(t_end / (self.lattice_speed_scale() * dx)
+                                 - 1e-9)))
+        return n, t_end / (n * dx)
 
 
 def tubes_batch(count: int = 4096, seed: int = SEED + 2,

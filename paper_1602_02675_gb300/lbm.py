@@ -48,6 +48,13 @@ class lbm_noalloc_desc(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("theta", ctypes.c_double)]
 
 
+class lbm_tube(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nsteps", ctypes.c_int64),
+                ("dt", ctypes.c_double), ("x_d", ctypes.c_double),
+                ("left", lbm_prim), ("right", lbm_prim),
+                ("bc", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
 class LbmError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -89,6 +96,18 @@ def load() -> ctypes.CDLL:
         "lbm_lambda": ([_H], ctypes.c_double),
         "lbm_last_error": ([_H], ctypes.c_char_p),
         "lbm_destroy": ([_H], None),
+        "lbm_batch_create": ([ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                              ctypes.c_int32, ctypes.POINTER(lbm_tube),
+                              ctypes.c_int64, ctypes.c_void_p,
+                              ctypes.POINTER(_H)], ctypes.c_int),
+        "lbm_batch_run": ([_H, ctypes.c_int64], ctypes.c_int),
+        "lbm_batch_sync": ([_H, ctypes.POINTER(ctypes.c_int64),
+                            ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+        "lbm_batch_moments": ([_H, ctypes.c_int64, _DP, _DP, _DP, _DP,
+                               ctypes.c_int64], ctypes.c_int),
+        "lbm_batch_totals": ([_H, _DP, ctypes.c_int64], ctypes.c_int),
+        "lbm_batch_last_error": ([_H], ctypes.c_char_p),
+        "lbm_batch_destroy": ([_H], None),
         "lbm_step_noalloc": ([ctypes.POINTER(lbm_noalloc_desc),
                               ctypes.c_void_p * 4, ctypes.c_void_p * 4,
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -240,3 +259,66 @@ def lbm_step_noalloc(desc: lbm_noalloc_desc, inputs, outputs, totals=0,
                               err, len(err))
     if st != OK:
         raise LbmError(st, err.value.decode())
+
+
+def make_tube(n, nsteps, dt, left, right, x_d=0.5, bc=TRANSMISSIVE) -> lbm_tube:
+    """left/right: (rho, u, p)."""
+    L_ = lbm_prim(float(left[0]), float(left[1]), 0.0, float(left[2]))
+    R_ = lbm_prim(float(right[0]), float(right[1]), 0.0, float(right[2]))
+    return lbm_tube(int(n), int(nsteps), float(dt), float(x_d), L_, R_, bc, 0)
+
+
+class Batch:
+    """Many independent 1-D tubes advanced together (lbm_batch_*)."""
+
+    def __init__(self, tubes, precision=F32, gamma=1.4, theta=0.5, kahan=1,
+                 stream=None):
+        lib = load()
+        arr = (lbm_tube * len(tubes))(*tubes)
+        self.tubes = list(tubes)
+        h = _H()
+        st = lib.lbm_batch_create(precision, gamma, theta, kahan, arr,
+                                  len(tubes), stream, ctypes.byref(h))
+        if st != OK:
+            raise LbmError(st, "lbm_batch_create")
+        self.h = h
+
+    def _check(self, st):
+        if st != OK:
+            msg = load().lbm_batch_last_error(self.h)
+            raise LbmError(st, msg.decode() if msg else "")
+
+    def run(self, max_launches=-1):
+        self._check(load().lbm_batch_run(self.h, int(max_launches)))
+
+    def sync(self):
+        s, f = ctypes.c_int64(0), ctypes.c_uint32(0)
+        self._check(load().lbm_batch_sync(self.h, ctypes.byref(s),
+                                          ctypes.byref(f)))
+        return s.value
+
+    def moments(self, j) -> dict:
+        n = self.tubes[j].n
+        out = {k: np.empty(n) for k in ("rho", "mx", "rhoE", "p")}
+        self._check(load().lbm_batch_moments(
+            self.h, j, _dp(out["rho"]), _dp(out["mx"]), _dp(out["rhoE"]),
+            _dp(out["p"]), n))
+        return out
+
+    def totals(self) -> np.ndarray:
+        out = np.zeros(3 * len(self.tubes))
+        self._check(load().lbm_batch_totals(self.h, _dp(out), len(self.tubes)))
+        return out.reshape(-1, 3)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbm_batch_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

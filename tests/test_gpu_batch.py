@@ -1,0 +1,116 @@
+"""Batched 1-D tubes (lbm_batch_*): every tube of a mixed batch against the
+FP64 oracle run of that tube alone, and the same tube alone vs in the mix."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1602_02675_gb300 import inputs as I
+from paper_1602_02675_gb300 import lbm as L
+
+pytestmark = pytest.mark.gpu
+
+
+def _tubes(count, seed, nmin=40, nmax=700):
+    specs = I.tubes_batch(count, seed=seed, nmin=nmin, nmax=nmax)
+    out = []
+    for t in specs:
+        nsteps, lam = t.steps_and_lambda(0.2)
+        # the library receives dt = lam/n and forms lambda = dt*n
+        out.append((t, nsteps, (lam / t.n) * t.n))
+    return out
+
+
+def _oracle_tube(t, nsteps, lam):
+    P = O.Params(dim=1, nx=t.n, bc_x=O.TRANSMISSIVE)
+    s = O.riemann_planar(P, 0.0, 1.0, 0.5, t.left, t.right, lam)
+    s2, _ = O.run(P, s, nsteps)
+    return O.lattice_to_physical(1.4, lam, s2), O.totals(s2)
+
+
+def _oracle_fp32_storage_error(t, nsteps, lam):
+    """L1 (of range) error the oracle itself incurs when its state is
+    rounded to FP32 after every step: the floor any FP32 path can reach.
+    Near the top of a level interval (X = D(gamma-1)e/(1-theta) close to
+    c2^2) the 1-D step amplifies perturbations, so this floor can exceed
+    1e-5 for some tubes."""
+    P = O.Params(dim=1, nx=t.n, bc_x=O.TRANSMISSIVE)
+    s = O.riemann_planar(P, 0.0, 1.0, 0.5, t.left, t.right, lam)
+    ref, _ = O.run(P, s, nsteps)
+    r = lambda a: a.astype(np.float32).astype(np.float64)
+    for _ in range(nsteps):
+        s, _, _ = O.step(P, s)
+        s = O.State(r(s.rho), r(s.mx), None, r(s.rhoE))
+    out = {}
+    for f, a, b in (("rho", s.rho, ref.rho), ("mx", s.mx, ref.mx),
+                    ("rhoE", s.rhoE, ref.rhoE)):
+        out[f] = np.mean(np.abs(a - b)) / (b.max() - b.min())
+    return out
+
+
+def _make(specs, precision, kahan=1):
+    tubes = [L.make_tube(t.n, ns, lam / t.n, t.left, t.right)
+             for t, ns, lam in specs]
+    return L.Batch(tubes, precision=precision, kahan=kahan)
+
+
+@pytest.mark.parametrize("precision", [L.F64, L.F32])
+def test_batch_matches_oracle_per_tube(precision):
+    """FP64: bit for bit.  FP32: mean |error| within 1e-5 of the range, or
+    within 4x the error of FP32 storage itself where the flow amplifies
+    rounding."""
+    specs = _tubes(24, seed=77)
+    with _make(specs, precision) as b:
+        b.run()
+        b.sync()
+        tot = b.totals()
+        for j, (t, ns, lam) in enumerate(specs):
+            g = b.moments(j)
+            o, ot = _oracle_tube(t, ns, lam)
+            for f in ("rho", "mx", "rhoE"):
+                if precision == L.F64:
+                    assert np.array_equal(g[f], o[f]), (j, f)
+                else:
+                    rng = o[f].max() - o[f].min()
+                    err = np.mean(np.abs(g[f] - o[f])) / rng
+                    if err > 1e-5:
+                        floor = _oracle_fp32_storage_error(t, ns, lam)[f]
+                        assert err <= 4.0 * floor, (j, f, err, floor)
+            scale = np.array([ot[0], max(abs(ot[1]), ot[0]), ot[3]])
+            want = np.array([ot[0], ot[1] / lam, ot[3] / lam ** 2])
+            tol = 1e-12 if precision == L.F64 else 1e-5
+            assert np.all(np.abs(tot[j] - want) <= tol * scale), (j, tot[j], want)
+
+
+@pytest.mark.parametrize("precision", [L.F32, L.F64])
+def test_tube_alone_equals_tube_in_the_mix(precision):
+    specs = _tubes(16, seed=5)
+    with _make(specs, precision) as b:
+        b.run()
+        b.sync()
+        mixed = [b.moments(j) for j in (0, 7, 15)]
+    for k, j in enumerate((0, 7, 15)):
+        with _make([specs[j]], precision) as b1:
+            b1.run()
+            b1.sync()
+            alone = b1.moments(0)
+        for f in ("rho", "mx", "rhoE", "p"):
+            assert np.array_equal(alone[f], mixed[k][f]), (j, f)
+
+
+def test_partial_runs_compose():
+    """run(a) then run(b) equals run(a + b): the device step counter and the
+    per-tube reach carry over between calls (graph replays included)."""
+    specs = _tubes(10, seed=9)
+    with _make(specs, L.F32) as a:
+        a.run()
+        a.sync()
+        ref = [a.moments(j) for j in range(10)]
+    with _make(specs, L.F32) as b:
+        b.run(37)
+        b.run(5)
+        b.run()
+        b.sync()
+        got = [b.moments(j) for j in range(10)]
+    for r, g in zip(ref, got):
+        for f in ("rho", "mx", "rhoE"):
+            assert np.array_equal(r[f], g[f])
