@@ -387,6 +387,55 @@ def run_tubes(args):
     }
 
 
+def run_serve(args):
+    """Serving: Poisson arrivals of a seeded mix (70 % 1-D tubes of
+    512..65536 nodes, 30 % 2-D grids, random Riemann states, t_end in
+    [0.05, 0.25]) through the continuous-batching server (FP32) within a
+    device-memory budget; the plain FP64 path serves a seeded subsample one
+    solve at a time."""
+    import numpy as np
+    import torch
+    from paper_1602_02675_gb300 import lbm as L
+    from paper_1602_02675_gb300 import serve as S
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    reqs = S.mixed_requests(args.requests, seed=20264,
+                            n2=(256, args.max_side))
+    arrivals = S.poisson_arrivals(len(reqs), args.rate, seed=20265)
+    # warm-up: compile caches, allocator
+    w = S.Server(budget=int(args.budget_gb * (1 << 30)), precision=L.F32)
+    for r in S.mixed_requests(6, seed=7, n1=(512, 2048), n2=(256, 300)):
+        w.submit(r)
+    w.drain()
+    w.close()
+    srv = S.Server(budget=int(args.budget_gb * (1 << 30)), precision=L.F32)
+    try:
+        stats = S.run_trace(srv, reqs, arrivals)
+        stats["peak_admitted_gb"] = srv.peak_used / (1 << 30)
+    finally:
+        srv.close()
+    rng = __import__("random").Random(20266)
+    sub = rng.sample(range(len(reqs)), min(args.seq_tubes, len(reqs)))
+    t_seq, lat = 0.0, []
+    for j in sub:
+        r = reqs[j]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.solve_alone(r, L.F64)
+        d = time.perf_counter() - t0
+        t_seq += d
+        lat.append(d)
+    base = {"solves_per_s": len(sub) / t_seq, "sample": len(sub),
+            "service_ms_p50": float(1e3 * np.percentile(lat, 50)),
+            "service_ms_p99": float(1e3 * np.percentile(lat, 99))}
+    return {"metric": "solves/s", "value": stats["solves_per_s"],
+            "unit": "solves/s", "workload": f"serve_{len(reqs)}_poisson_{args.rate}",
+            "dtype": "f32", "served": stats,
+            "budget_gb": args.budget_gb,
+            "max_2d_side": args.max_side,
+            "plain_fp64_one_at_a_time": base,
+            "speedup_solves_per_s": stats["solves_per_s"] / base["solves_per_s"]}
+
+
 def run_reference(args, rank, world):
     """The CPU oracle as it stands: K bounded samples of the workload."""
     if rank != 0:
@@ -432,7 +481,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-l1", action="store_true")
     ap.add_argument("--workload", default="sod2d",
-                    choices=sorted(WORKLOADS) + ["tubes"])
+                    choices=sorted(WORKLOADS) + ["tubes", "serve"])
+    ap.add_argument("--requests", type=int, default=300)
+    ap.add_argument("--rate", type=float, default=40.0,
+                    help="serve: Poisson arrival rate (requests/s)")
+    ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--max-side", type=int, default=1024)
     ap.add_argument("--tubes", type=int, default=4096)
     ap.add_argument("--batch-reps", type=int, default=2)
     ap.add_argument("--seq-tubes", type=int, default=24)
@@ -448,6 +502,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.workload == "tubes":
         print(json.dumps(run_tubes(args)))
+        return
+    if args.workload == "serve":
+        print(json.dumps(run_serve(args)))
         return
     if args.impl == "reference":
         line = run_reference(args, rank, world)

@@ -230,6 +230,44 @@ const char* lbm_batch_last_error(const lbm_batch* b);
 /* Free a batch; NULL-safe; waits for queued work. */
 void lbm_batch_destroy(lbm_batch* b);
 
+/* ---- tube pool for continuous batching ---------------------------------
+ *
+ * 1-D tubes (lbm_tube) join and leave between steps; each lbm_pool_step is
+ * one launch that advances every tube still short of its step count by one
+ * step.  Each tube keeps its own step counter, so a tube's result does not
+ * depend on when it joined or what else is in the pool (same step as
+ * lbm_step on a 1-D handle).  Node ranges come from one buffer of
+ * capacity_nodes nodes per field and parity, allocated at creation.
+ */
+typedef struct lbm_pool lbm_pool;
+
+lbm_status lbm_pool_create(int32_t precision, double gamma, double theta,
+                           int32_t kahan, int64_t capacity_nodes,
+                           int32_t max_slots, void* stream, lbm_pool** out);
+
+/* Take a slot and a node range for the tube and initialise it (stream-
+   ordered).  LBM_EBUDGET when no slot or contiguous range is free. */
+lbm_status lbm_pool_add(lbm_pool* p, const lbm_tube* t, int32_t* slot);
+
+/* One step of every tube that still has steps to take (one launch). */
+lbm_status lbm_pool_step(lbm_pool* p);
+
+/* Steps taken and step count of a slot (host-side, does not wait). */
+lbm_status lbm_pool_progress(lbm_pool* p, int32_t slot, int64_t* taken,
+                             int64_t* nsteps);
+
+/* Physical rho, rho*u, rho*E and pressure (nullable) of a slot's current
+   state; n = the tube's node count.  Waits for the pool's stream. */
+lbm_status lbm_pool_read(lbm_pool* p, int32_t slot, double* rho, double* mx,
+                         double* rhoE, double* pr, int64_t n);
+
+/* Release a slot and its node range. */
+lbm_status lbm_pool_remove(lbm_pool* p, int32_t slot);
+
+const char* lbm_pool_last_error(const lbm_pool* p);
+
+void lbm_pool_destroy(lbm_pool* p);
+
 /* ---- allocation-free single step --------------------------------------
  *
  * The paper has no counterpart to this entry point; it exists for callers

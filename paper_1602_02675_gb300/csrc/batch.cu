@@ -22,11 +22,12 @@
 #include "lbm.h"
 #include "lbm_internal.h"
 #include "step_kernel.cuh"
+#include "tile1d.cuh"
 
 namespace lbm {
 namespace batch {
 
-constexpr int TILE = 256;
+constexpr int TILE = kTile1d;
 
 struct Tube {
   long long off;     // first node in the concatenated buffers
@@ -57,116 +58,6 @@ struct Args {
 };
 
 template <typename T, bool KAHAN>
-__device__ void tile_step(const Args& a, const T* __restrict__ in0,
-                          const T* __restrict__ in1, const T* __restrict__ in2,
-                          T* __restrict__ o0, T* __restrict__ o1,
-                          T* __restrict__ o2, const Tube& tb, int tile, int R,
-                          int* reach_next, unsigned char* smem) {
-  using S = TileShape<1>;
-  const int tid = threadIdx.x;
-  SrcLayout<T, 1> L;
-  L.bind(smem, a.r_cap);
-  const int x0 = tile * TILE;
-  const int W = TILE + 2 * R;
-  unsigned long long clamps = 0;
-  bool bad = false;
-  for (int i = tid; i < W; i += TILE) {
-    const long long sx = (long long)x0 - R + i;
-    bool fx;
-    const int gx = virtual_axis(tb.bc, tb.n, sx, &fx);
-    const long long g = tb.off + gx;
-    T rho = in0[g], mx = in1[g], rE = in2[g];
-    if (fx) mx = -mx;
-    Equil<T> q = equilibrium<T, 1>(rho, mx, T(0), rE, a.k);
-    if (sx >= x0 && sx < x0 + TILE && sx < tb.n) {
-      clamps += q.clamp ? 1 : 0;
-      bad |= q.bad;
-    }
-    if (!q.emits) {
-      L.c1[i] = -1;
-      continue;
-    }
-    L.c1[i] = (short)q.c1;
-    L.n0[i] = (short)q.n0;
-    L.f0[i] = q.f0;
-    L.mass[0 * L.cap + i] = q.d0;
-    L.mass[1 * L.cap + i] = q.d1;
-    L.mass[2 * L.cap + i] = q.d2;
-#pragma unroll
-    for (int p = 0; p < S::NP; ++p) {
-      int cx, cy, lev;
-      packet<1>(p, q.c1, &cx, &cy, &lev);
-      const T d = L.mass[lev * L.cap + i];
-      const T cbx = q.V0 + (T)cx;
-      L.Px[p * L.cap + i] = d * cbx;
-      L.PE[p * L.cap + i] = d * (T(0.5) * (cbx * cbx) + q.phi);
-    }
-  }
-  if (clamps) atomicAdd(a.eclamps, clamps);
-  if (bad) atomicOr(a.flags, kFlagState);
-  __syncthreads();
-
-  const int dx = x0 + tid;
-  int my_reach = 0;
-  if (dx < tb.n) {
-    // one source row; ascending x, packet order, corner order (as the
-    // single-tube kernel and the oracle)
-    T r = T(0), x = T(0), e = T(0);
-    T cr = T(0), cx_ = T(0), ce = T(0);
-    for (int i = 0; i <= 2 * R; ++i) {
-      const int s = tid + i;
-      const int c1 = L.c1[s];
-      if (c1 < 0) continue;
-      const int c2 = c1 + 1;
-      const int ox = R - i - L.n0[s];
-      if (ox < -c2 || ox > c2 + 1) continue;
-      const T fx0 = L.f0[s];
-      const T wx[2] = {T(1) - fx0, fx0};
-#pragma unroll
-      for (int p = 0; p < S::NP; ++p) {
-        int px, py, lev;
-        packet<1>(p, c1, &px, &py, &lev);
-#pragma unroll
-        for (int kk = 0; kk < S::NK; ++kk) {
-          if (px + kk != ox) continue;
-          const T al = wx[kk];
-          if (KAHAN) {
-            T y = al * L.mass[lev * L.cap + s] - cr;
-            T t = r + y;
-            cr = (t - r) - y;
-            r = t;
-            y = al * L.Px[p * L.cap + s] - cx_;
-            t = x + y;
-            cx_ = (t - x) - y;
-            x = t;
-            y = al * L.PE[p * L.cap + s] - ce;
-            t = e + y;
-            ce = (t - e) - y;
-            e = t;
-          } else {
-            r = r + al * L.mass[lev * L.cap + s];
-            x = x + al * L.Px[p * L.cap + s];
-            e = e + al * L.PE[p * L.cap + s];
-          }
-        }
-      }
-    }
-    // the single-tube kernel adds the row sum to a zero total: 0 + s = s
-    const long long o = tb.off + dx;
-    o0[o] = T(0) + r;
-    o1[o] = T(0) + x;
-    o2[o] = T(0) + e;
-    my_reach = reach_bound((double)r, (double)x, 0.0, (double)e,
-                           (float)a.k.kreach);
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1)
-    my_reach = max(my_reach, __shfl_xor_sync(0xffffffffu, my_reach, off));
-  if ((tid & 31) == 0 && my_reach > 0) atomicMax(reach_next, my_reach);
-  __syncthreads();  // shared records are reused by the next item
-}
-
-template <typename T, bool KAHAN>
 __global__ void __launch_bounds__(TILE) batch_step(const Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int is_last;
@@ -193,8 +84,9 @@ __global__ void __launch_bounds__(TILE) batch_step(const Args a) {
       if (threadIdx.x == 0) atomicOr(a.flags, kFlagReach);
       continue;
     }
-    tile_step<T, KAHAN>(a, in0, in1, in2, o0, o1, o2, tb, w.y, R,
-                        rnext + w.x, smem);
+    tile1d_step<T, KAHAN>(in0, in1, in2, o0, o1, o2, tb.off, tb.n, tb.bc,
+                          w.y, R, a.r_cap, a.k, rnext + w.x, a.flags,
+                          a.eclamps, smem);
   }
   __syncthreads();
   if (threadIdx.x == 0) {

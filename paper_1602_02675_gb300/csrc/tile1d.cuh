@@ -1,0 +1,132 @@
+// One 256-node tile of the 1-D tau = 1 step, for kernels that process many
+// tubes (batched tubes, the serving pool).  Same arithmetic and summation
+// order as the single-tube step kernel: equilibrium packets of the tile's
+// sources within reach R in shared memory (Section III.B eqs 13-15, 24-26;
+// Section IV.A), then each thread sums the arrivals at its node over the
+// sources in ascending order, packets in table order, corners in order (eqs
+// 6, 10, 22, 28); additional points beyond the ends per Section V.B.
+// FP64 instantiations must be compiled without contraction to round as the
+// oracle does.
+#pragma once
+
+#include "step_kernel.cuh"
+
+namespace lbm {
+
+constexpr int kTile1d = 256;
+
+template <typename T, bool KAHAN>
+__device__ void tile1d_step(const T* __restrict__ in0,
+                            const T* __restrict__ in1,
+                            const T* __restrict__ in2, T* __restrict__ o0,
+                            T* __restrict__ o1, T* __restrict__ o2,
+                            long long off, int n, int bc, int tile, int R,
+                            int r_cap, const EqConst& k, int* reach_next,
+                            unsigned* flags, unsigned long long* eclamps,
+                            unsigned char* smem) {
+  using S = TileShape<1>;
+  const int tid = threadIdx.x;
+  SrcLayout<T, 1> L;
+  L.bind(smem, r_cap);
+  const int x0 = tile * kTile1d;
+  const int W = kTile1d + 2 * R;
+  unsigned long long clamps = 0;
+  bool bad = false;
+  for (int i = tid; i < W; i += kTile1d) {
+    const long long sx = (long long)x0 - R + i;
+    bool fx;
+    const int gx = virtual_axis(bc, n, sx, &fx);
+    const long long g = off + gx;
+    T rho = in0[g], mx = in1[g], rE = in2[g];
+    if (fx) mx = -mx;
+    Equil<T> q = equilibrium<T, 1>(rho, mx, T(0), rE, k);
+    if (sx >= x0 && sx < x0 + kTile1d && sx < n) {
+      clamps += q.clamp ? 1 : 0;
+      bad |= q.bad;
+    }
+    if (!q.emits) {
+      L.c1[i] = -1;
+      continue;
+    }
+    L.c1[i] = (short)q.c1;
+    L.n0[i] = (short)q.n0;
+    L.f0[i] = q.f0;
+    L.mass[0 * L.cap + i] = q.d0;
+    L.mass[1 * L.cap + i] = q.d1;
+    L.mass[2 * L.cap + i] = q.d2;
+#pragma unroll
+    for (int p = 0; p < S::NP; ++p) {
+      int cx, cy, lev;
+      packet<1>(p, q.c1, &cx, &cy, &lev);
+      const T d = L.mass[lev * L.cap + i];
+      const T cbx = q.V0 + (T)cx;
+      L.Px[p * L.cap + i] = d * cbx;
+      L.PE[p * L.cap + i] = d * (T(0.5) * (cbx * cbx) + q.phi);
+    }
+  }
+  if (clamps) atomicAdd(eclamps, clamps);
+  if (bad) atomicOr(flags, kFlagState);
+  __syncthreads();
+
+  const int dx = x0 + tid;
+  int my_reach = 0;
+  if (dx < n) {
+    // one source row; ascending x, packet order, corner order (as the
+    // single-tube kernel and the oracle)
+    T r = T(0), x = T(0), e = T(0);
+    T cr = T(0), cx_ = T(0), ce = T(0);
+    for (int i = 0; i <= 2 * R; ++i) {
+      const int s = tid + i;
+      const int c1 = L.c1[s];
+      if (c1 < 0) continue;
+      const int c2 = c1 + 1;
+      const int ox = R - i - L.n0[s];
+      if (ox < -c2 || ox > c2 + 1) continue;
+      const T fx0 = L.f0[s];
+      const T wx[2] = {T(1) - fx0, fx0};
+#pragma unroll
+      for (int p = 0; p < S::NP; ++p) {
+        int px, py, lev;
+        packet<1>(p, c1, &px, &py, &lev);
+#pragma unroll
+        for (int kk = 0; kk < S::NK; ++kk) {
+          if (px + kk != ox) continue;
+          const T al = wx[kk];
+          if (KAHAN) {
+            T y = al * L.mass[lev * L.cap + s] - cr;
+            T t = r + y;
+            cr = (t - r) - y;
+            r = t;
+            y = al * L.Px[p * L.cap + s] - cx_;
+            t = x + y;
+            cx_ = (t - x) - y;
+            x = t;
+            y = al * L.PE[p * L.cap + s] - ce;
+            t = e + y;
+            ce = (t - e) - y;
+            e = t;
+          } else {
+            r = r + al * L.mass[lev * L.cap + s];
+            x = x + al * L.Px[p * L.cap + s];
+            e = e + al * L.PE[p * L.cap + s];
+          }
+        }
+      }
+    }
+    // the single-tube kernel adds the row sum to a zero total: 0 + s = s
+    const long long o = off + dx;
+    o0[o] = T(0) + r;
+    o1[o] = T(0) + x;
+    o2[o] = T(0) + e;
+    my_reach = reach_bound((double)r, (double)x, 0.0, (double)e,
+                           (float)k.kreach);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+    my_reach = max(my_reach, __shfl_xor_sync(0xffffffffu, my_reach, off));
+  if ((tid & 31) == 0 && my_reach > 0) atomicMax(reach_next, my_reach);
+  __syncthreads();  // shared records are reused by the next item
+}
+
+
+}  // namespace lbm

@@ -108,6 +108,19 @@ def load() -> ctypes.CDLL:
         "lbm_batch_totals": ([_H, _DP, ctypes.c_int64], ctypes.c_int),
         "lbm_batch_last_error": ([_H], ctypes.c_char_p),
         "lbm_batch_destroy": ([_H], None),
+        "lbm_pool_create": ([ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                             ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                             ctypes.c_void_p, ctypes.POINTER(_H)], ctypes.c_int),
+        "lbm_pool_add": ([_H, ctypes.POINTER(lbm_tube),
+                          ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "lbm_pool_step": ([_H], ctypes.c_int),
+        "lbm_pool_progress": ([_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "lbm_pool_read": ([_H, ctypes.c_int32, _DP, _DP, _DP, _DP,
+                           ctypes.c_int64], ctypes.c_int),
+        "lbm_pool_remove": ([_H, ctypes.c_int32], ctypes.c_int),
+        "lbm_pool_last_error": ([_H], ctypes.c_char_p),
+        "lbm_pool_destroy": ([_H], None),
         "lbm_step_noalloc": ([ctypes.POINTER(lbm_noalloc_desc),
                               ctypes.c_void_p * 4, ctypes.c_void_p * 4,
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -313,6 +326,68 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             load().lbm_batch_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Pool:
+    """Tube pool for continuous batching (lbm_pool_*)."""
+
+    def __init__(self, capacity_nodes, max_slots=4096, precision=F32,
+                 gamma=1.4, theta=0.5, kahan=1, stream=None):
+        lib = load()
+        h = _H()
+        st = lib.lbm_pool_create(precision, gamma, theta, kahan,
+                                 int(capacity_nodes), int(max_slots), stream,
+                                 ctypes.byref(h))
+        if st != OK:
+            raise LbmError(st, "lbm_pool_create")
+        self.h = h
+        self.n = {}
+
+    def _check(self, st):
+        if st != OK:
+            msg = load().lbm_pool_last_error(self.h)
+            raise LbmError(st, msg.decode() if msg else "")
+
+    def add(self, tube: lbm_tube) -> int:
+        s = ctypes.c_int32(-1)
+        self._check(load().lbm_pool_add(self.h, ctypes.byref(tube),
+                                        ctypes.byref(s)))
+        self.n[s.value] = tube.n
+        return s.value
+
+    def step(self):
+        self._check(load().lbm_pool_step(self.h))
+
+    def progress(self, slot):
+        a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+        self._check(load().lbm_pool_progress(self.h, slot, ctypes.byref(a),
+                                             ctypes.byref(b)))
+        return a.value, b.value
+
+    def read(self, slot) -> dict:
+        n = self.n[slot]
+        out = {k: np.empty(n) for k in ("rho", "mx", "rhoE", "p")}
+        self._check(load().lbm_pool_read(self.h, slot, _dp(out["rho"]),
+                                         _dp(out["mx"]), _dp(out["rhoE"]),
+                                         _dp(out["p"]), n))
+        return out
+
+    def remove(self, slot):
+        self._check(load().lbm_pool_remove(self.h, slot))
+        self.n.pop(slot, None)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbm_pool_destroy(self.h)
             self.h = None
 
     __del__ = close
