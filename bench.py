@@ -57,6 +57,42 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def max_over_ranks(values, world, device):
+    """Element-wise maximum of per-rank timings over all ranks (identity on
+    one rank).  Works with the NCCL (CUDA tensors) and gloo (CPU) groups."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_rate(units_per_rank, world, t_max):
+    """Whole-job throughput of independent replicas: all ranks' units over
+    the slowest rank's time."""
+    return world * units_per_rank / t_max
+
+
+def measured_traffic(nodes):
+    """DRAM bytes per launch of the FP32 2-D step kernel from the committed
+    ncu summary, scaled by nodes; None unless the kernel sources are the
+    ones that summary was taken from."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "step2d_f32_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    h = hashlib.sha256()
+    for src in rec["sources"]:
+        with open(os.path.join(ROOT, src), "rb") as g:
+            h.update(g.read())
+    if h.hexdigest() != rec["sha256"]:
+        return None
+    return rec["dram_bytes_per_node"] * nodes
+
+
 def steps_and_lambda(t_end, dx):
     n = max(1, int(math.ceil(t_end / dx - 1e-9)))
     return n, t_end / (n * dx)
@@ -184,14 +220,10 @@ def run_ours(args, rank, world):
         ms64, _ = timed_steps(s64, k64, max(3, args.warmup))
         s64.close()
 
-    t32 = sum(ms32) / 1e3
-    t64 = sum(ms64) / 1e3
-    if world > 1:
-        t = torch.tensor([t32, t64], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t32, t64 = float(t[0]), float(t[1])
-    value = world * N * args.steps / t32
-    v64 = world * N * k64 / t64
+    t32, t64 = max_over_ranks([sum(ms32) / 1e3, sum(ms64) / 1e3], world,
+                              "cuda")
+    value = job_rate(N * args.steps, world, t32)
+    v64 = job_rate(N * k64, world, t64)
 
     # e2e: whole solves through the C ABI from pinned host memory
     e2e = (run_e2e(args, L, torch, stream, lam, nsolve, world)
@@ -203,7 +235,9 @@ def run_ours(args, rank, world):
     achieved = bytes_per_launch / (mean_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
             "unit": "GB/s", "frac": round(achieved / peak, 4),
-            "traffic": args.traffic, "peak_kind": peak_kind,
+            "traffic": (args.traffic if args.traffic is not None else
+                        (measured_traffic(N) if args.kahan == 0 else None)),
+            "peak_kind": peak_kind,
             "kernel": ("lbm::fast::step2d_f32" if args.kahan == 0
                        else "step_kernel<float,2,true>"),
             "bytes_per_launch": bytes_per_launch}

@@ -91,6 +91,7 @@ class _Active1D:
     req: Request
     slot: int
     steps: int
+    taken: int = 0   # host count: every pool step advances every tube
 
 
 @dataclass
@@ -177,6 +178,9 @@ class Server:
     def _advance(self) -> None:
         if self._a1:
             self._pool.step()
+            for a in self._a1:
+                if a.taken < a.steps:
+                    a.taken += 1
         for a in self._a2:
             if a.taken < a.steps:
                 a.solver.step(1)
@@ -185,8 +189,7 @@ class Server:
     def _retire(self) -> None:
         keep1 = []
         for a in self._a1:
-            taken, _ = self._pool.progress(a.slot)
-            if taken < a.steps:
+            if a.taken < a.steps:
                 keep1.append(a)
                 continue
             try:
