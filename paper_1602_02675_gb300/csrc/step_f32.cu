@@ -20,7 +20,8 @@ cudaError_t launch_step_f32(int dim, const StepArgs& a, size_t smem,
     dim3 grid((a.nx + fast::TX - 1) / fast::TX, (a.ny + fast::TY - 1) / fast::TY);
     StepArgs b = a;  // the last-block ticket counts this kernel's tiles
     b.nblocks = (int)(grid.x * grid.y);
-    fast::step2d_f32<<<grid, fast::NTHR, smem, s>>>(b);
+    // its own fixed layout: no more shared memory than that (occupancy)
+    fast::step2d_f32<<<grid, fast::NTHR, fast::smem_bytes(), s>>>(b);
   }
   return cudaGetLastError();
 }
