@@ -15,8 +15,12 @@
  * Conventions shared by every entry point:
  *  - Plain C types only.  Host arrays are caller-owned, hold n = nx*ny
  *    doubles with x fastest, and are not retained after the call returns.
- *  - All device memory (the two moment buffers and a few scratch words) is
- *    owned by the handle and allocated in lbm_create.
+ *  - All device memory is owned by the handle and allocated in lbm_create:
+ *    two moment buffers (4 fields x n x 4 or 8 bytes each), a few scratch
+ *    words, and for an F32 square-lattice handle with kahan = 0 and
+ *    max_reach <= 6 two sets of per-node equilibrium records (24 bytes per
+ *    node each), which carry each node's equilibrium (Section III.B) from
+ *    the step that produced the node to the step that uses it.
  *  - Work is issued on the stream given in lbm_config.stream (a
  *    cudaStream_t, or NULL for the default stream), in call order.
  *    lbm_step returns before the GPU finishes; lbm_moments, lbm_conservation,

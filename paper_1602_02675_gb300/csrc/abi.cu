@@ -25,6 +25,11 @@ struct lbm_handle {
   int nblocks = 0;
   void* buf[2][4] = {{nullptr}};
   int cur = 0;
+  // FP32 square lattice: equilibrium records of buf[b] in rec[b] (float4
+  // and float2 arrays); rec_ok says whether rec[cur] matches buf[cur].
+  bool use_rec = false;
+  void* rec[2][2] = {{nullptr}};
+  bool rec_ok = false;
   Scratch* scr = nullptr;
   double* part = nullptr;
   int part_cap = 0;
@@ -181,6 +186,11 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
       if (f == 2 && c.dim == 1) continue;
       ok = cudaMalloc(&h->buf[b][f], fb) == cudaSuccess;
     }
+  h->use_rec = step_uses_records(c.dim, h->f64, c.kahan ? 1 : 0, h->r_cap);
+  for (int b = 0; b < 2 && ok && h->use_rec; ++b) {
+    ok = cudaMalloc(&h->rec[b][0], 16 * (size_t)h->n) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->rec[b][1], 8 * (size_t)h->n) == cudaSuccess;
+  }
   ok = ok && cudaMalloc(&h->scr, sizeof(Scratch)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->part, sizeof(double) * 4 * (size_t)h->part_cap) ==
                  cudaSuccess;
@@ -235,6 +245,7 @@ lbm_status lbm_init_riemann(lbm_handle* h, const lbm_prim* inner,
     d[2] = h->dim == 2 ? s[j]->v : 0.0;
     d[3] = s[j]->p;
   }
+  h->rec_ok = false;
   LBM_CUDA(h, launch_init(h->f64, a, h->stream), "init kernel");
   LBM_CUDA(h, cudaMemsetAsync(h->scr, 0, sizeof(Scratch), h->stream),
            "scratch clear");
@@ -265,6 +276,7 @@ static lbm_status set_from_host(lbm_handle* h, int kind, const double* a,
            "copy to device");
   void* f[4];
   cur_fields(h, f);
+  h->rec_ok = false;
   LBM_CUDA(h, launch_from_host_layout(h->f64, kind, h->dim, h->staging, f, n,
                                       h->lambda, h->cfg.gamma, h->stream),
            "convert kernel");
@@ -310,6 +322,19 @@ lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
     }
     const int every = h->cfg.cons_every;
     a.do_cons = (every > 0 && ((h->steps + 1) % every) == 0) ? 1 : 0;
+    if (h->use_rec) {
+      if (!h->rec_ok) {
+        const void* f[4] = {a.in[0], a.in[1], a.in[2], a.in[3]};
+        LBM_CUDA(h, launch_records_f32(f, h->rec[h->cur][0], h->rec[h->cur][1],
+                                       h->n, h->k, h->stream),
+                 "records kernel");
+        h->rec_ok = true;
+      }
+      a.rin_a = h->rec[h->cur][0];
+      a.rin_b = h->rec[h->cur][1];
+      a.rout_a = h->rec[h->cur ^ 1][0];
+      a.rout_b = h->rec[h->cur ^ 1][1];
+    }
     LBM_CUDA(h, launch_step(h->dim, h->f64, a, h->smem, h->stream),
              "step kernel");
     h->cur ^= 1;
@@ -411,6 +436,9 @@ void lbm_destroy(lbm_handle* h) {
   for (int b = 0; b < 2; ++b)
     for (int f = 0; f < 4; ++f)
       if (h->buf[b][f]) cudaFree(h->buf[b][f]);
+  for (int b = 0; b < 2; ++b)
+    for (int f = 0; f < 2; ++f)
+      if (h->rec[b][f]) cudaFree(h->rec[b][f]);
   if (h->scr) cudaFree(h->scr);
   if (h->part) cudaFree(h->part);
   if (h->staging) cudaFree(h->staging);

@@ -41,6 +41,16 @@ struct StepArgs {
   EqConst k;
   Scratch* scr;
   double* part;       // [nblocks * 4] FP64 partial sums
+  // FP32 square lattice only: per-node equilibrium records of the input
+  // (rin) and of the output (rout) state, or null.  rec_a = (V_x, V_y, d1,
+  // d2), rec_b = (E_b, flag word); see step_fast_f32.cuh.
+  const void* rin_a = nullptr;
+  const void* rin_b = nullptr;
+  void* rout_a = nullptr;
+  void* rout_b = nullptr;
+  // Tiles resident at once (set by the launcher): a block prefetches into
+  // L2 the input records of the tile that many launches ahead.
+  int prefetch_ahead = 0;
 };
 
 // Launch helpers (step kernels).
@@ -49,6 +59,15 @@ cudaError_t step_prepare(int dim, bool f64, size_t smem);
 int step_blocks(int dim, int nx, int ny);
 cudaError_t launch_step(int dim, bool f64, const StepArgs& a, size_t smem,
                         cudaStream_t s);
+
+// FP32 square-lattice handles whose steps carry equilibrium records between
+// launches (the fast kernel's path); records take 24 bytes per node.
+bool step_uses_records(int dim, bool f64, int kahan, int r_cap);
+// Records of the state f (FP32 moments) into rec_a [n] float4, rec_b [n]
+// float2.
+cudaError_t launch_records_f32(const void* const f[4], void* rec_a,
+                               void* rec_b, int64_t n, const EqConst& k,
+                               cudaStream_t s);
 
 // Auxiliary kernels (init, conversion, reductions).
 struct InitArgs {

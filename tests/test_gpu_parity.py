@@ -291,3 +291,70 @@ def test_uniform_state_stays_uniform_bitwise():
             if f == "my" and dim == 1:
                 continue
             assert np.all(g[f] == g[f][0])
+
+
+def test_restart_fp32_records_bitwise():
+    """FP32 square lattice with kahan = 0 carries each node's equilibrium
+    from the step that produced it to the next step (global records).
+    Checkpoint through lbm_moments / lbm_set_moments rebuilds them with the
+    records kernel instead: n then m steps must equal n + m steps bit for
+    bit (lambda = 1, so the unit conversion is exact)."""
+    nx, ny = 77, 45
+    prims = I.random_smooth_prims(2, nx, ny, seed=71)
+    cfg = L.make_config(2, nx, ny, precision=L.F32, bc_x=L.TRANSMISSIVE,
+                        bc_y=L.REFLECTING, kahan=0)
+    with L.Solver(cfg) as a:
+        a.set_primitives(*prims)
+        a.step(13)
+        ref = a.moments()
+    with L.Solver(cfg) as b:
+        b.set_primitives(*prims)
+        for part in (4, 6, 3):
+            b.step(part)
+            m = b.moments()
+            b.set_moments(m["rho"], m["mx"], m["my"], m["rhoE"])
+        got = b.moments()
+    for f in FIELDS:
+        assert np.array_equal(got[f], ref[f]), f
+
+
+@pytest.mark.parametrize("prec,kahan", [(L.F64, 1), (L.F32, 1), (L.F32, 0)])
+def test_energy_clamps_counted_like_oracle(prec, kahan):
+    """Nodes whose internal energy e = E - |V|^2/2 is negative are clamped to
+    e = 0 and counted once per step that uses them, by every kernel (the
+    FP32 register kernel reads the clamp from the node's record)."""
+    nx, ny = 48, 40
+    n = nx * ny
+    rng = np.random.default_rng(8)
+    rho = rng.uniform(0.5, 1.5, n)
+    u = rng.uniform(-0.4, 0.4, n)
+    v = rng.uniform(-0.4, 0.4, n)
+    rhoE = rho * (0.5 * (u * u + v * v) + rng.uniform(0.3, 0.8, n))
+    bad = rng.choice(n, 37, replace=False)
+    rhoE[bad] = 0.5 * rho[bad] * (u[bad] ** 2 + v[bad] ** 2) * 0.5
+    cfg = L.make_config(2, nx, ny, precision=prec, bc_x=L.PERIODIC,
+                        bc_y=L.PERIODIC, kahan=kahan)
+    with L.Solver(cfg) as s:
+        s.set_moments(rho, rho * u, rho * v, rhoE)
+        s.step(1)
+        d = s.diagnostics()
+    P = O.Params(dim=2, nx=nx, ny=ny, bc_x=O.PERIODIC, bc_y=O.PERIODIC)
+    st = O.State(rho.copy(), (rho * u).copy(), (rho * v).copy(), rhoE.copy())
+    _, ec = O.run(P, st, 1)
+    assert ec == 37
+    assert d["eclamps"] == ec
+
+
+def test_fp32_register_kernel_reports_bad_state():
+    nx, ny = 64, 40
+    cfg = L.make_config(2, nx, ny, precision=L.F32, bc_x=L.PERIODIC,
+                        bc_y=L.PERIODIC, kahan=0)
+    with L.Solver(cfg) as s:
+        rho = np.ones(nx * ny)
+        rho[700] = -1.0
+        z = np.zeros(nx * ny)
+        with pytest.raises(L.LbmError) as e:
+            s.set_primitives(rho, z, z, np.ones(nx * ny))
+            s.step(1)
+            s.moments()
+        assert e.value.status == L.ESTATE
