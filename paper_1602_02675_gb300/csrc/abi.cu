@@ -30,6 +30,8 @@ struct lbm_handle {
   bool use_rec = false;
   void* rec[2][2] = {{nullptr}};
   bool rec_ok = false;
+  int rec_pitch = 0;      // nodes per record row (nx rounded up to even)
+  TmaMap rec_map[2][2];   // TMA tensor maps of rec[b][0], rec[b][1]
   Scratch* scr = nullptr;
   double* part = nullptr;
   int part_cap = 0;
@@ -96,6 +98,9 @@ lbm_status check_flags(lbm_handle* h) {
   if (s.flags & kFlagState)
     return fail(h, LBM_ESTATE,
                 "lbm: a node reached rho < 0 or a non-finite moment");
+  if (s.flags & kFlagTimeout)
+    return fail(h, LBM_ETIMEOUT,
+                "lbm: a bounded wait for a shared-memory copy gave up");
   if (s.flags & kFlagReach)
     return fail(h, LBM_EREACH,
                 "lbm: migration reach exceeded max_reach (raise "
@@ -187,9 +192,14 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
       ok = cudaMalloc(&h->buf[b][f], fb) == cudaSuccess;
     }
   h->use_rec = step_uses_records(c.dim, h->f64, c.kahan ? 1 : 0, h->r_cap);
+  h->rec_pitch = h->nx + (h->nx & 1);
+  const size_t rec_nodes = (size_t)h->rec_pitch * (size_t)h->ny;
   for (int b = 0; b < 2 && ok && h->use_rec; ++b) {
-    ok = cudaMalloc(&h->rec[b][0], 16 * (size_t)h->n) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->rec[b][1], 8 * (size_t)h->n) == cudaSuccess;
+    ok = cudaMalloc(&h->rec[b][0], 16 * rec_nodes) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->rec[b][1], 8 * rec_nodes) == cudaSuccess;
+    ok = ok && make_record_maps(h->rec[b][0], h->rec[b][1], h->nx, h->ny,
+                                h->rec_pitch, &h->rec_map[b][0],
+                                &h->rec_map[b][1]) == cudaSuccess;
   }
   ok = ok && cudaMalloc(&h->scr, sizeof(Scratch)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->part, sizeof(double) * 4 * (size_t)h->part_cap) ==
@@ -326,7 +336,8 @@ lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
       if (!h->rec_ok) {
         const void* f[4] = {a.in[0], a.in[1], a.in[2], a.in[3]};
         LBM_CUDA(h, launch_records_f32(f, h->rec[h->cur][0], h->rec[h->cur][1],
-                                       h->n, h->k, h->stream),
+                                       h->nx, h->ny, h->rec_pitch, h->k,
+                                       h->stream),
                  "records kernel");
         h->rec_ok = true;
       }
@@ -334,6 +345,9 @@ lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
       a.rin_b = h->rec[h->cur][1];
       a.rout_a = h->rec[h->cur ^ 1][0];
       a.rout_b = h->rec[h->cur ^ 1][1];
+      a.rec_pitch = h->rec_pitch;
+      a.map_a = &h->rec_map[h->cur][0];
+      a.map_b = &h->rec_map[h->cur][1];
     }
     LBM_CUDA(h, launch_step(h->dim, h->f64, a, h->smem, h->stream),
              "step kernel");

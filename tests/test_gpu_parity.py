@@ -358,3 +358,17 @@ def test_fp32_register_kernel_reports_bad_state():
             s.step(1)
             s.moments()
         assert e.value.status == L.ESTATE
+
+
+@pytest.mark.parametrize("bcs", BC2)
+@pytest.mark.parametrize("shape", [(3, 2), (7, 5), (33, 9)])
+def test_tiny_grids_fp32_register_kernel(bcs, shape):
+    """Grids narrower than the migration halo: most window slots of the
+    register kernel lie outside the grid and are filled from the nodes that
+    supply them (possibly several reflections or wraps away)."""
+    nx, ny = shape
+    prims = I.random_smooth_prims(2, nx, ny, seed=4100 + nx * ny + bcs[0])
+    g = _gpu(2, nx, ny, *bcs, prims=prims, steps=8, precision=L.F32,
+             kahan=0)
+    o = _oracle(2, nx, ny, *bcs, prims=prims, steps=8)
+    _assert_l1(g, o, 2)
