@@ -365,10 +365,20 @@ def test_fp32_register_kernel_reports_bad_state():
 def test_tiny_grids_fp32_register_kernel(bcs, shape):
     """Grids narrower than the migration halo: most window slots of the
     register kernel lie outside the grid and are filled from the nodes that
-    supply them (possibly several reflections or wraps away)."""
+    supply them (possibly several reflections or wraps away).  On a 3 x 2
+    grid a field may vary by only 1e-4 of its size, and m_y between two
+    walls one row apart is a near-cancelling sum of O(1) terms, so the mean
+    error is taken relative to the field's size (momentum: the larger of
+    max |m_x| and max |m_y|): a slot filled from the wrong node or with the
+    wrong mirror sign errs by the size of its contribution itself."""
     nx, ny = shape
     prims = I.random_smooth_prims(2, nx, ny, seed=4100 + nx * ny + bcs[0])
     g = _gpu(2, nx, ny, *bcs, prims=prims, steps=8, precision=L.F32,
              kahan=0)
     o = _oracle(2, nx, ny, *bcs, prims=prims, steps=8)
-    _assert_l1(g, o, 2)
+    mom = max(np.max(np.abs(o["mx"])), np.max(np.abs(o["my"])))
+    for f in FIELDS:
+        size = mom if f in ("mx", "my") else np.max(np.abs(o[f]))
+        scale = max(np.ptp(o[f]), size, 1e-300)
+        err = np.mean(np.abs(g[f] - o[f])) / scale
+        assert err <= 1e-5, (f, err)
