@@ -248,6 +248,18 @@ def run_ours(args, rank, world):
                          "one-block finalize kernel" if args.kahan == 0 else
                          "CUDA events around lbm_step: one step kernel")}
     mean64 = t64 / k64 * 1e3
+    # Arithmetic roof: the gather's 32 arrivals x 4 fields of multiply-adds
+    # (256 flop per node update, a lower bound on the method's arithmetic)
+    # against this GPU's measured FMA throughput.
+    peak32 = L.lbm_measure_fma_peak(L.F32, stream.cuda_stream)
+    peak64 = L.lbm_measure_fma_peak(L.F64, stream.cuda_stream)
+    alu = {"flop_per_node_update": 256,
+           "basis": "32 packet arrivals x 4 fields, multiply + add each",
+           "fp32_fma_peak_tflops": round(peak32 / 1e12, 2),
+           "fp64_fma_peak_tflops": round(peak64 / 1e12, 3),
+           "fp32_frac": round(value * 256 / peak32, 4),
+           "fp64_frac": (round(v64 * 256 / peak64, 4)
+                         if args.precision == "both" else None)}
     line = {
         "metric": METRIC, "value": value, "unit": "node-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -264,6 +276,7 @@ def run_ours(args, rank, world):
                  "parity": "bit-exact with the FP64 oracle (tests)"},
         "e2e": e2e,
         "roofline": roof,
+        "alu_check": alu,
         "clocks": clk,
         "gpu_launches": args.steps * (2 if args.kahan == 0 else 1),
         "wall_s_timed_fp32": round(wall32, 4),
@@ -491,6 +504,66 @@ def run_serve(args):
                         "(tests); FP32 vs FP64 oracle within 1e-5 of range"}
 
 
+def run_sod1d(args):
+    """The 1-D Sod tube (Section V.C): 1000 nodes, FP64, lambda = 1, 200
+    steps to t = 0.2.  Time to solution (initial state + 200 steps, device
+    time by CUDA events) over `--repeats` solves, once with plain launches
+    through the C ABI and once replaying one CUDA graph that holds the whole
+    solve; 201 launches per solve make it launch-bound."""
+    import numpy as np
+    import torch
+    from paper_1602_02675_gb300 import lbm as L
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.Stream()
+    n = 1000
+    nsteps, lam = steps_and_lambda(T_END, 1.0 / n)
+    cfg = L.make_config(1, n, dt=lam / n, precision=L.F64,
+                        bc_x=L.TRANSMISSIVE, stream=stream.cuda_stream)
+    solver = L.Solver(cfg)
+
+    def solve():
+        solver.init_riemann((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), L.PLANAR_X,
+                            0.5)
+        solver.step(nsteps)
+
+    def timed(run):
+        ms = []
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                run()
+            stream.synchronize()
+            for _ in range(args.repeats):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                run()
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+        return {"p50_ms": float(np.percentile(ms, 50)),
+                "p99_ms": float(np.percentile(ms, 99)),
+                "mean_ms": float(np.mean(ms))}
+
+    plain = timed(solve)
+    rho_plain = solver.moments()["rho"].copy()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        solve()
+    stream.synchronize()
+    graphed = timed(graph.replay)
+    rho_graph = solver.moments()["rho"]
+    solver.close()
+    return {"metric": "time to solution", "value": graphed["p50_ms"],
+            "unit": "ms", "higher_is_better": False, "dtype": "f64",
+            "data": "synthetic (Sod initial state, Section V.C)",
+            "config": {"workload": "sod_1d_1000", "nodes": n,
+                       "steps": nsteps, "lambda": lam,
+                       "repeats": args.repeats},
+            "graph": graphed, "plain": plain,
+            "gpu_launches_per_solve": 2 + nsteps,
+            "graph_equals_plain": bool(np.array_equal(rho_plain, rho_graph))}
+
+
 def run_reference(args, rank, world):
     """The CPU oracle as it stands: K bounded samples of the workload."""
     if rank != 0:
@@ -536,7 +609,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-l1", action="store_true")
     ap.add_argument("--workload", default="sod2d",
-                    choices=sorted(WORKLOADS) + ["tubes", "serve"])
+                    choices=sorted(WORKLOADS) + ["tubes", "serve", "sod1d"])
+    ap.add_argument("--repeats", type=int, default=100,
+                    help="sod1d: solves timed")
     ap.add_argument("--requests", type=int, default=300)
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--max-side", type=int, default=1024)
@@ -558,6 +633,9 @@ def main():
         return
     if args.workload == "serve":
         print(json.dumps(run_serve(args)))
+        return
+    if args.workload == "sod1d":
+        print(json.dumps(run_sod1d(args)))
         return
     if args.impl == "reference":
         line = run_reference(args, rank, world)

@@ -321,6 +321,21 @@ lbm_status lbm_step_noalloc(const lbm_noalloc_desc* d, const void* const in[4],
                             uint32_t* flags, void* stream, char* err,
                             size_t err_len);
 
+/* ---- measurement: arithmetic roof of the device ------------------------
+ * The paper has no counterpart: this reports the device's fused
+ * multiply-add throughput so that the step kernels' arithmetic can be stated
+ * as a fraction of what the current GPU sustains.
+ *
+ * Runs, on the current device and the given stream (cudaStream_t, NULL =
+ * default), a kernel of independent FMA chains in precision (lbm_precision:
+ * FP32 or FP64), several times, and writes the best rate to *flops_per_s
+ * (2 flops per FMA).  Synchronizes the stream; allocates nothing.  Returns
+ * LBM_EINVAL for a NULL pointer or unknown precision, LBM_ECUDA if a launch
+ * or timing call fails.
+ */
+lbm_status lbm_measure_fma_peak(int32_t precision, double* flops_per_s,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,7 @@ cudaError_t step_prepare(int dim, bool f64, size_t smem) {
 }
 
 int step_blocks(int dim, int nx, int ny) {
-  if (dim == 1) return (nx + TileShape<1>::TX - 1) / TileShape<1>::TX;
+  if (dim == 1) return (nx + step_tile_1d(nx) - 1) / step_tile_1d(nx);
   return ((nx + TileShape<2>::TX - 1) / TileShape<2>::TX) *
          ((ny + TileShape<2>::TY - 1) / TileShape<2>::TY);
 }

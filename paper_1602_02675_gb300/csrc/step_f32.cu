@@ -37,8 +37,14 @@ int fast_resident_blocks() {
 cudaError_t launch_step_f32(int dim, const StepArgs& a, size_t smem,
                             cudaStream_t s) {
   if (dim == 1) {
-    dim3 grid((a.nx + TileShape<1>::TX - 1) / TileShape<1>::TX, 1);
-    if (a.kahan)
+    const int tw = step_tile_1d(a.nx);
+    dim3 grid((a.nx + tw - 1) / tw, 1);
+    const size_t sm32 = step_smem_bytes_t<float, 1, 32>(a.r_cap);
+    if (tw == 32 && a.kahan)
+      step_kernel<float, 1, true, 32><<<grid, 32, sm32, s>>>(a);
+    else if (tw == 32)
+      step_kernel<float, 1, false, 32><<<grid, 32, sm32, s>>>(a);
+    else if (a.kahan)
       step_kernel<float, 1, true><<<grid, 256, smem, s>>>(a);
     else
       step_kernel<float, 1, false><<<grid, 256, smem, s>>>(a);
@@ -142,11 +148,16 @@ size_t step_smem_f32(int dim, int r_cap) {
 cudaError_t step_prepare_f32(int dim, size_t smem) {
   cudaError_t e;
   if (dim == 1) {
-    e = cudaFuncSetAttribute(step_kernel<float, 1, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(step_kernel<float, 1, false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const void* fns[4] = {(const void*)step_kernel<float, 1, true>,
+                          (const void*)step_kernel<float, 1, false>,
+                          (const void*)step_kernel<float, 1, true, 32>,
+                          (const void*)step_kernel<float, 1, false, 32>};
+    for (const void* fn : fns) {
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
   e = cudaFuncSetAttribute(step_kernel<float, 2, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -170,12 +181,14 @@ namespace lbm {
 // Raise (never lower) the dynamic shared-memory limit of the FP32 step
 // kernels so a launch needing smem bytes is allowed.
 cudaError_t step_raise_smem_f32(int dim, size_t smem) {
-  const void* fns[3] = {
+  const void* fns[4] = {
       dim == 1 ? (const void*)step_kernel<float, 1, true>
                : (const void*)step_kernel<float, 2, true>,
       dim == 1 ? (const void*)step_kernel<float, 1, false>
                : (const void*)step_kernel<float, 2, false>,
-      dim == 1 ? (const void*)step_kernel<float, 1, false>
+      dim == 1 ? (const void*)step_kernel<float, 1, true, 32>
+               : (const void*)fast::step2d_f32,
+      dim == 1 ? (const void*)step_kernel<float, 1, false, 32>
                : (const void*)fast::step2d_f32};
   for (const void* fn : fns) {
     cudaFuncAttributes at;

@@ -8,8 +8,13 @@ namespace lbm {
 cudaError_t launch_step_f64(int dim, const StepArgs& a, size_t smem,
                             cudaStream_t s) {
   if (dim == 1) {
-    dim3 grid((a.nx + TileShape<1>::TX - 1) / TileShape<1>::TX, 1);
-    step_kernel<double, 1, false><<<grid, 256, smem, s>>>(a);
+    const int tw = step_tile_1d(a.nx);
+    dim3 grid((a.nx + tw - 1) / tw, 1);
+    if (tw == 32)
+      step_kernel<double, 1, false, 32><<<grid, 32,
+                                          step_smem_bytes_t<double, 1, 32>(a.r_cap), s>>>(a);
+    else
+      step_kernel<double, 1, false><<<grid, 256, smem, s>>>(a);
   } else {
     dim3 grid((a.nx + TileShape<2>::TX - 1) / TileShape<2>::TX,
               (a.ny + TileShape<2>::TY - 1) / TileShape<2>::TY);
@@ -24,10 +29,15 @@ size_t step_smem_f64(int dim, int r_cap) {
 }
 
 cudaError_t step_prepare_f64(int dim, size_t smem) {
-  if (dim == 1)
+  if (dim == 1) {
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<double, 1, false, 32>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(step_kernel<double, 1, false>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
+  }
   return cudaFuncSetAttribute(step_kernel<double, 2, false>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem);
@@ -40,14 +50,20 @@ namespace lbm {
 // Raise (never lower) the dynamic shared-memory limit of the FP64 step
 // kernel so a launch needing smem bytes is allowed.
 cudaError_t step_raise_smem_f64(int dim, size_t smem) {
-  cudaFuncAttributes at;
-  const void* fn = dim == 1 ? (const void*)step_kernel<double, 1, false>
-                            : (const void*)step_kernel<double, 2, false>;
-  cudaError_t e = cudaFuncGetAttributes(&at, fn);
-  if (e != cudaSuccess) return e;
-  if ((size_t)at.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+  const void* fns[2] = {dim == 1 ? (const void*)step_kernel<double, 1, false>
+                                 : (const void*)step_kernel<double, 2, false>,
+                        dim == 1 ? (const void*)step_kernel<double, 1, false, 32>
+                                 : (const void*)step_kernel<double, 2, false>};
+  for (const void* fn : fns) {
+    cudaFuncAttributes at;
+    cudaError_t e = cudaFuncGetAttributes(&at, fn);
+    if (e != cudaSuccess) return e;
+    if ((size_t)at.maxDynamicSharedSizeBytes >= smem) continue;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace lbm

@@ -34,10 +34,20 @@ struct TileShape<2> {
   static constexpr int TX = 32, TY = 8, NP = 8, NK = 4, NLEV = 2;
 };
 
+// 1-D tile width of the exact-order kernel for a tube of nx nodes: 32 until
+// tiles of 256 would give two blocks per multiprocessor of a GB300 (152),
+// so that short tubes spread over many multiprocessors (the FP64 rate per
+// multiprocessor is low).  Each destination's sum order does not depend on
+// the tile.
+__host__ __device__ inline int step_tile_1d(int nx) {
+  return nx < 2 * 152 * 256 ? 32 : 256;
+}
+
 // Shared-memory layout of the source records, structure of arrays, sized
-// for r_cap.  Per source: packet fields Px, Py (2-D), PE per packet, the mass
-// per level, split fractions f, and packed integers (c1, n_x, n_y).
-template <typename T, int DIM>
+// for r_cap and a tile TXW destinations wide.  Per source: packet fields Px,
+// Py (2-D), PE per packet, the mass per level, split fractions f, and packed
+// integers (c1, n_x, n_y).
+template <typename T, int DIM, int TXW = TileShape<DIM>::TX>
 struct SrcLayout {
   using S = TileShape<DIM>;
   int cap;  // sources the buffers hold
@@ -52,7 +62,7 @@ struct SrcLayout {
   short* n1;
 
   __host__ __device__ static int capacity(int r_cap) {
-    return (S::TX + 2 * r_cap) * (DIM == 2 ? (S::TY + 2 * r_cap) : 1);
+    return (TXW + 2 * r_cap) * (DIM == 2 ? (S::TY + 2 * r_cap) : 1);
   }
   __host__ __device__ static size_t bytes(int r_cap) {
     size_t c = (size_t)capacity(r_cap);
@@ -234,13 +244,16 @@ __device__ __forceinline__ T ld(const void* p, long long i) {
   return reinterpret_cast<const T*>(p)[i];
 }
 
-template <typename T, int DIM, bool KAHAN>
-__global__ void __launch_bounds__(256)
+template <typename T, int DIM, bool KAHAN, int NT = 256>
+__global__ void __launch_bounds__(NT)
     step_kernel(const StepArgs a) {
   using S = TileShape<DIM>;
+  // tile width: NT destinations in 1-D (one per thread), TXW in 2-D
+  constexpr int TXW = DIM == 1 ? NT : S::TX;
+  static_assert(DIM == 2 ? NT == S::TX * S::TY : NT % 32 == 0, "tile");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red_sum[4][256 / 32];
-  __shared__ int red_reach[256 / 32];
+  __shared__ double red_sum[4][NT / 32];
+  __shared__ int red_reach[NT / 32];
   __shared__ int is_last;
 
   const int tid = threadIdx.x;
@@ -251,19 +264,19 @@ __global__ void __launch_bounds__(256)
     return;
   }
   const int Ry = (DIM == 2) ? R : 0;
-  const int x0 = blockIdx.x * S::TX;
+  const int x0 = blockIdx.x * TXW;
   const int y0 = blockIdx.y * S::TY;
-  const int W = S::TX + 2 * R;
+  const int W = TXW + 2 * R;
   const int H = (DIM == 2) ? S::TY + 2 * R : 1;
   const int NS = W * H;
 
-  SrcLayout<T, DIM> L;
+  SrcLayout<T, DIM, TXW> L;
   L.bind(smem_raw, a.r_cap);
 
   // ---- 1. equilibrium packets of every source in reach of the tile ----
   unsigned long long my_clamps = 0;
   bool my_bad = false;
-  for (int i = tid; i < NS; i += 256) {
+  for (int i = tid; i < NS; i += NT) {
     int ly = i / W;
     int lx = i - ly * W;
     long long sx = (long long)x0 - R + lx;
@@ -279,7 +292,7 @@ __global__ void __launch_bounds__(256)
     if (fx) mx = -mx;
     if (fy) my = -my;
     Equil<T> q = equilibrium<T, DIM>(rho, mx, my, rE, a.k);
-    bool own = sx >= x0 && sx < x0 + S::TX && sx < a.nx &&
+    bool own = sx >= x0 && sx < x0 + TXW && sx < a.nx &&
                (DIM == 1 || (sy >= y0 && sy < y0 + S::TY && sy < a.ny));
     if (own) {
       my_clamps += q.clamp ? 1 : 0;
@@ -324,8 +337,8 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
 
   // ---- 2. gather the arrivals at this thread's destination ----
-  const int tx = tid % S::TX;
-  const int ty = tid / S::TX;
+  const int tx = tid % TXW;
+  const int ty = tid / TXW;
   const int dx = x0 + tx;
   const int dy = y0 + ty;
   const bool valid = dx < a.nx && dy < a.ny;
@@ -446,7 +459,7 @@ __global__ void __launch_bounds__(256)
   if (tid == 0) {
     int rb = red_reach[0];
     double bs[4] = {red_sum[0][0], red_sum[1][0], red_sum[2][0], red_sum[3][0]};
-    for (int w = 1; w < 256 / 32; ++w) {
+    for (int w = 1; w < NT / 32; ++w) {
       rb = max(rb, red_reach[w]);
 #pragma unroll
       for (int f = 0; f < 4; ++f) bs[f] += red_sum[f][w];
@@ -467,7 +480,7 @@ __global__ void __launch_bounds__(256)
   __threadfence();
   if (a.do_cons) {
     double s[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = tid; b < nblk; b += 256) {
+    for (int b = tid; b < nblk; b += NT) {
 #pragma unroll
       for (int f = 0; f < 4; ++f) s[f] += __ldcg(&a.part[(long long)b * 4 + f]);
     }
@@ -484,7 +497,7 @@ __global__ void __launch_bounds__(256)
     if (tid == 0) {
       for (int f = 0; f < 4; ++f) {
         double t = red_sum[f][0];
-        for (int w = 1; w < 256 / 32; ++w) t += red_sum[f][w];
+        for (int w = 1; w < NT / 32; ++w) t += red_sum[f][w];
         a.scr->cons[f] = t;
       }
     }
@@ -498,9 +511,9 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <typename T, int DIM>
+template <typename T, int DIM, int TXW = TileShape<DIM>::TX>
 size_t step_smem_bytes_t(int r_cap) {
-  return SrcLayout<T, DIM>::bytes(r_cap);
+  return SrcLayout<T, DIM, TXW>::bytes(r_cap);
 }
 
 }  // namespace lbm

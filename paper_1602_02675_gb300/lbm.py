@@ -121,6 +121,8 @@ def load() -> ctypes.CDLL:
         "lbm_pool_remove": ([_H, ctypes.c_int32], ctypes.c_int),
         "lbm_pool_last_error": ([_H], ctypes.c_char_p),
         "lbm_pool_destroy": ([_H], None),
+        "lbm_measure_fma_peak": ([ctypes.c_int32, _DP, ctypes.c_void_p],
+                                 ctypes.c_int),
         "lbm_step_noalloc": ([ctypes.POINTER(lbm_noalloc_desc),
                               ctypes.c_void_p * 4, ctypes.c_void_p * 4,
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -272,6 +274,17 @@ def lbm_step_noalloc(desc: lbm_noalloc_desc, inputs, outputs, totals=0,
                               err, len(err))
     if st != OK:
         raise LbmError(st, err.value.decode())
+
+
+def lbm_measure_fma_peak(precision, stream=None) -> float:
+    """Fused multiply-add throughput (flop/s) of the current device in
+    precision F32 or F64 (measurement; see include/lbm.h)."""
+    out = ctypes.c_double(0.0)
+    st = load().lbm_measure_fma_peak(int(precision), ctypes.byref(out),
+                                     stream)
+    if st != OK:
+        raise LbmError(st, "lbm_measure_fma_peak")
+    return out.value
 
 
 def make_tube(n, nsteps, dt, left, right, x_d=0.5, bc=TRANSMISSIVE) -> lbm_tube:

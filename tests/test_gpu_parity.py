@@ -382,3 +382,33 @@ def test_tiny_grids_fp32_register_kernel(bcs, shape):
         scale = max(np.ptp(o[f]), size, 1e-300)
         err = np.mean(np.abs(g[f] - o[f])) / scale
         assert err <= 1e-5, (f, err)
+
+
+def test_sod_1d_solve_replayed_from_cuda_graph_bitwise():
+    """A whole solve (initial state + 200 steps, FP64) captured through the
+    C ABI into one CUDA graph: every replay gives the oracle's result bit
+    for bit (the step's device state - reach, flags, ticket - is reset by
+    the solve itself, so replays do not drift)."""
+    import torch
+    stream = torch.cuda.Stream()
+    cfg = L.make_config(1, 1000, precision=L.F64, bc_x=L.TRANSMISSIVE,
+                        stream=stream.cuda_stream)
+    o = _oracle(1, 1000, 1, O.TRANSMISSIVE, 0, riemann=SOD, steps=200)
+    with L.Solver(cfg) as s:
+        def solve():
+            s.init_riemann((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), L.PLANAR_X,
+                           0.5)
+            s.step(200)
+        with torch.cuda.stream(stream):
+            solve()  # warm-up outside capture
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            solve()
+        for _ in range(2):
+            with torch.cuda.stream(stream):
+                g.replay()
+            stream.synchronize()
+            m = s.moments()
+            for f in ("rho", "mx", "rhoE"):
+                assert np.array_equal(m[f], o[f]), f
