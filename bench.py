@@ -20,7 +20,14 @@ the solver's stream.
   roofline   step: algorithmic bytes (4 fields read + 4 written per node) /
              mean step time (both kernels), against the measured HBM copy
              rate
+  alu_check  the arrivals' multiply-adds (256 flop per node update) of the
+             FP32 and FP64 steps against this GPU's measured FMA peaks
   cpu_baseline  the FP64 oracle on this host's cores, bounded sample
+
+Other workloads (one JSON line each): --workload cylinder2d (8192^2 periodic
+cylinder), sod1d (1-D Sod time to solution, plain and CUDA-graph), tubes
+(4096 batched 1-D tubes vs plain FP64 one at a time), serve (continuous
+batching: capacity and Poisson sweep vs plain FP64 one at a time).
 
 --impl reference times the oracle alone (the CPU reference arm).
 Multi-GPU (torchrun): independent replicas, one per rank (weak scaling).
