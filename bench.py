@@ -123,7 +123,7 @@ class Clocks:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -361,25 +361,30 @@ def cpu_baseline(seconds: float) -> dict:
 
 
 def l1_vs_oracle(L) -> dict:
-    """FP32 path against the FP64 oracle: mean |error| / field range on the
-    1-D Sod tube (1000 nodes, 200 steps to t = 0.2)."""
+    """FP32 and FP64 paths against the FP64 oracle on the benchmark workload:
+    a whole 4096 x 512 solve to t = 0.2 (820 steps), mean |error| / field
+    range of every row against the oracle's row stored in
+    tests/golden/sod2d_row_4096_t0.2.txt (written from oracle/ alone; the
+    data vary along x only, so every row is that row)."""
     import numpy as np
-    from oracle import oracle as O
-    n = 1000
-    P = O.Params(dim=1, nx=n, bc_x=O.TRANSMISSIVE)
-    st, _ = O.run(P, O.riemann_planar(P, 0, 1, 0.5, (1.0, 0.0, 1.0),
-                                      (0.125, 0.0, 0.1), 1.0), 200)
-    o = O.lattice_to_physical(1.4, 1.0, st)
+    ref = np.loadtxt(os.path.join(ROOT, "tests", "golden",
+                                  "sod2d_row_4096_t0.2.txt"))
+    o = {"rho": ref[:, 0], "mx": ref[:, 1], "rhoE": ref[:, 2]}
+    nsolve, lam = steps_and_lambda(T_END, 1.0 / NX)
     out = {}
     for prec, name in ((L.F32, "f32"), (L.F64, "f64")):
-        with L.Solver(L.make_config(1, n, precision=prec)) as s:
-            s.init_riemann((1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
-            s.step(200)
+        cfg = L.make_config(2, NX, NY, dt=lam / NX, precision=prec,
+                            bc_x=L.TRANSMISSIVE, bc_y=L.REFLECTING,
+                            kahan=0 if prec == L.F32 else 1)
+        with L.Solver(cfg) as s:
+            s.init_riemann((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), L.PLANAR_X, 0.5)
+            s.step(nsolve)
             g = s.moments()
-        out[name] = {f: float(np.mean(np.abs(g[f] - o[f])) /
+        out[name] = {f: float(np.mean(np.abs(g[f].reshape(NY, NX) - o[f])) /
                               (o[f].max() - o[f].min()))
                      for f in ("rho", "mx", "rhoE")}
-    out["case"] = "sod_1d_1000, 200 steps"
+        out[name]["my_max_abs"] = float(np.max(np.abs(g["my"])))
+    out["case"] = "sod_2d_4096x512, 820 steps to t = 0.2, every row"
     return out
 
 
@@ -605,7 +610,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-solves", type=int, default=2)

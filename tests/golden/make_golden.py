@@ -25,9 +25,32 @@ def sod_l1(N, t_end=0.2):
                         ph["p"])
 
 
+def sod2d_row(nx=4096, t_end=0.2):
+    """One row of the 2-D square-lattice Sod tube between reflecting walls
+    (x-only data: every row of the 4096 x 512 tube is this row), physical
+    units, after the whole solve."""
+    P = O.Params(dim=2, nx=nx, ny=1, bc_x=O.TRANSMISSIVE, bc_y=O.REFLECTING)
+    n, lam = O.steps_and_lambda(t_end, 1.0 / nx)
+    s, _ = O.run(P, O.riemann_planar(P, 0, 1, 0.5, SOD_L, SOD_R, lam), n)
+    return n, lam, O.lattice_to_physical(1.4, lam, s)
+
+
+def write_sod2d_row(path):
+    n, lam, ph = sod2d_row()
+    with open(path, "w") as f:
+        f.write("# One row of the 4096 x 512 square-lattice Sod tube (Section V.C;\n"
+                "# transmissive x ends, reflecting y walls, x-only initial jump at\n"
+                "# x = 0.5), FP64 oracle, after %d steps to t = 0.2 (lambda = %.17g).\n"
+                "# Physical units.  Written by tests/golden/make_golden.py from\n"
+                "# oracle/ only.  columns: rho m_x rhoE\n" % (n, lam))
+        for r, m, e in zip(ph["rho"], ph["mx"], ph["rhoE"]):
+            f.write(f"{float(r)!r} {float(m)!r} {float(e)!r}\n")
+
+
 def main():
-    out = os.path.join(os.path.dirname(os.path.abspath(__file__)),
-                       "sod_l1_errors.txt")
+    here = os.path.dirname(os.path.abspath(__file__))
+    write_sod2d_row(os.path.join(here, "sod2d_row_4096_t0.2.txt"))
+    out = os.path.join(here, "sod_l1_errors.txt")
     with open(out, "w") as f:
         f.write("# L1 (mean absolute) error of the 1-D lattice Boltzmann Sod tube\n"
                 "# against the exact Riemann solution at t = 0.2 (Section V.C-D),\n"

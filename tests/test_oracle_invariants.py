@@ -260,3 +260,17 @@ def test_restart_composes():
     b, _ = O.run(P, s, 12)
     for fa, fb in zip(a.fields(), b.fields()):
         assert np.array_equal(fa, fb)
+
+
+def test_stored_sod2d_row_is_the_oracle_solution():
+    """The stored oracle row of the 4096 x 512 tube (written by
+    tests/golden/make_golden.py) has one row per node and conserves mass:
+    at t = 0.2 no wave has reached the transmissive ends, so the total is
+    that of the initial state, 0.5 * 1 + 0.5 * 0.125."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden",
+                        "sod2d_row_4096_t0.2.txt")
+    a = np.loadtxt(path)
+    assert a.shape == (4096, 3)
+    np.testing.assert_allclose(a[:, 0].sum() / 4096, 0.5625, rtol=1e-13)
+    assert a[0, 0] == 1.0 and a[-1, 0] == 0.125   # undisturbed ends
