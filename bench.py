@@ -409,9 +409,10 @@ def run_tubes(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with L.Batch(tubes, precision=L.F32, kahan=1,
-                     stream=stream.cuda_stream) as b:
+                     stream=stream.cuda_stream) as b:   # tunes the tile
             b.run()
             b.sync()
+            tuning = b.tuning()
         dt = time.perf_counter() - t0
         if rep > 0:
             times.append(dt)
@@ -442,7 +443,9 @@ def run_tubes(args):
         "metric": "solves/s", "value": solves_b, "unit": "solves/s",
         "workload": f"tubes_batch_{len(specs)}", "dtype": "f32",
         "batched": {"solves_per_s": solves_b, "node_updates_per_s": nus / tb,
-                    "wall_s": tb, "node_updates": nus, "tubes": len(specs)},
+                    "wall_s": tb, "node_updates": nus, "tubes": len(specs),
+                    "tile_tuning": tuning,
+                    "timed": "creation (tile tuning included) to results"},
         "plain_fp64_one_at_a_time": {
             "solves_per_s": solves_64, "node_updates_per_s": nus64 / t64,
             "sample_tubes": len(sub),

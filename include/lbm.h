@@ -206,7 +206,10 @@ typedef struct {
 /* Create a batch: device buffers for all tubes, their initial states and
    first reach.  precision: lbm_precision; theta as lbm_config.theta; kahan
    (F32): compensated summation of each destination's arrivals.  Tubes keep
-   the caller's indices in every other call.  Synchronous. */
+   the caller's indices in every other call.  Synchronous.  Creation also
+   picks the tile width (nodes per work item: 128, 256 or 512) by timing a
+   few steps of this batch with each and keeping the fastest, then resets
+   every tube to its initial state; the width does not change any result. */
 lbm_status lbm_batch_create(int32_t precision, double gamma, double theta,
                             int32_t kahan, const lbm_tube* tubes, int64_t count,
                             void* stream, lbm_batch** out);
@@ -228,6 +231,17 @@ lbm_status lbm_batch_moments(lbm_batch* b, int64_t tube, double* rho,
 /* FP64 totals (rho, rho*u, rho*E; physical units) of every tube, 3 per tube
    in the caller's order; count = number of tubes.  Waits. */
 lbm_status lbm_batch_totals(lbm_batch* b, double* out, int64_t count);
+
+/* The tile width in use and the measured ms per step of the candidates
+   128, 256, 512 (ms_per_step[3], -1 where not timed; either pointer may be
+   NULL). */
+lbm_status lbm_batch_tuning(const lbm_batch* b, int32_t* tile,
+                            double* ms_per_step);
+
+/* Use tile width `tile` (128, 256 or 512) instead of the tuned one.  Only
+   before the first lbm_batch_run (LBM_EINVAL after); resets every tube to
+   its initial state.  Synchronous. */
+lbm_status lbm_batch_set_tile(lbm_batch* b, int32_t tile);
 
 const char* lbm_batch_last_error(const lbm_batch* b);
 

@@ -5,12 +5,20 @@
 // Layout: every tube's nodes are concatenated (tube after tube) in one SoA
 // buffer of three fields (rho, m, rhoE), two ping-pong copies.  Tubes are
 // ordered by decreasing step count, so at global step s the tubes still
-// running are a prefix, and so are their work items (tube, 256-node tile):
+// running are a prefix, and so are their work items (tube, tile of TW nodes):
 // the kernel reads how many items are active from a table indexed by the
 // device step counter.  Each item runs the 1-D tau = 1 step of its tile with
 // the same arithmetic and summation order as the single-tube step kernel
 // (Section III.B eqs 13-15, 24-26; Section IV.A; eqs 6, 10, 22, 28; Section
 // V.B boundaries).  A tube that has taken its steps keeps its last state.
+//
+// Tile width: lbm_batch_create times a few real steps of the batch with each
+// candidate width (kTileChoices) and keeps the fastest (an autotuner over
+// the tile shape of this batch); the state is then reset to the initial
+// one.  The result does not depend on the width: every destination sums its
+// arrivals in the same order.  The shared-memory halo is sized for the
+// maximum reach (64) rather than tuned: a halo tuned below the reach a later
+// step meets would end the run with LBM_EREACH.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -27,7 +35,8 @@
 namespace lbm {
 namespace batch {
 
-constexpr int TILE = kTile1d;
+constexpr int TILE = kTile1d;              // block size of the helper kernels
+constexpr int kTileChoices[3] = {128, 256, 512};
 
 struct Tube {
   long long off;     // first node in the concatenated buffers
@@ -57,8 +66,8 @@ struct Args {
   unsigned long long* eclamps;
 };
 
-template <typename T, bool KAHAN>
-__global__ void __launch_bounds__(TILE) batch_step(const Args a) {
+template <typename T, bool KAHAN, int TW>
+__global__ void __launch_bounds__(TW) batch_step(const Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int is_last;
   const int s = *a.step;
@@ -75,7 +84,7 @@ __global__ void __launch_bounds__(TILE) batch_step(const Args a) {
   int* rnext = a.reach + ((s + 1) % 3) * a.ntubes;
   int* rclear = a.reach + ((s + 2) % 3) * a.ntubes;
   if (blockIdx.x == 0)
-    for (int t = threadIdx.x; t < a.ntubes; t += TILE) rclear[t] = 0;
+    for (int t = threadIdx.x; t < a.ntubes; t += TW) rclear[t] = 0;
   for (int it = blockIdx.x; it < nact; it += gridDim.x) {
     const int2 w = a.items[it];
     const Tube tb = a.tubes[w.x];
@@ -84,7 +93,7 @@ __global__ void __launch_bounds__(TILE) batch_step(const Args a) {
       if (threadIdx.x == 0) atomicOr(a.flags, kFlagReach);
       continue;
     }
-    tile1d_step<T, KAHAN>(in0, in1, in2, o0, o1, o2, tb.off, tb.n, tb.bc,
+    tile1d_step<T, KAHAN, TW>(in0, in1, in2, o0, o1, o2, tb.off, tb.n, tb.bc,
                           w.y, R, a.r_cap, a.k, rnext + w.x, a.flags,
                           a.eclamps, smem);
   }
@@ -198,6 +207,11 @@ struct lbm_batch {
   int kahan = 1;
   size_t smem = 0;
   int grid = 0;
+  int tile = 256;                // nodes per work item (chosen by tuning)
+  double tune_ms[3] = {-1.0, -1.0, -1.0};  // ms per step of kTileChoices
+  int nsm = 0;
+  double* d_st = nullptr;        // initial states (for resets)
+  int runs = 0;                  // lbm_batch_run calls so far
   EqConst k{};
   std::vector<int> order;        // sorted position -> caller's tube index
   std::vector<int> pos;          // caller's tube index -> sorted position
@@ -261,15 +275,161 @@ Args make_args(lbm_batch* b) {
   return a;
 }
 
+template <int TW>
+const void* step_fn_tw(bool f64, int kahan) {
+  if (f64) return (const void*)batch_step<double, false, TW>;
+  return kahan ? (const void*)batch_step<float, true, TW>
+               : (const void*)batch_step<float, false, TW>;
+}
+
+const void* step_fn(bool f64, int kahan, int tile) {
+  return tile == 128 ? step_fn_tw<128>(f64, kahan)
+                     : (tile == 512 ? step_fn_tw<512>(f64, kahan)
+                                    : step_fn_tw<256>(f64, kahan));
+}
+
+template <int TW>
+void launch_tw(lbm_batch* b, const Args& a) {
+  if (b->f64)
+    batch_step<double, false, TW><<<b->grid, TW, b->smem, b->stream>>>(a);
+  else if (b->kahan)
+    batch_step<float, true, TW><<<b->grid, TW, b->smem, b->stream>>>(a);
+  else
+    batch_step<float, false, TW><<<b->grid, TW, b->smem, b->stream>>>(a);
+}
+
 cudaError_t launch_one(lbm_batch* b) {
   Args a = make_args(b);
-  if (b->f64)
-    batch_step<double, false><<<b->grid, TILE, b->smem, b->stream>>>(a);
-  else if (b->kahan)
-    batch_step<float, true><<<b->grid, TILE, b->smem, b->stream>>>(a);
+  if (b->tile == 128)
+    launch_tw<128>(b, a);
+  else if (b->tile == 512)
+    launch_tw<512>(b, a);
   else
-    batch_step<float, false><<<b->grid, TILE, b->smem, b->stream>>>(a);
+    launch_tw<256>(b, a);
   return cudaGetLastError();
+}
+
+size_t step_smem(bool f64, int tile, int r_cap) {
+  if (f64)
+    return tile == 128 ? step_smem_bytes_t<double, 1, 128>(r_cap)
+           : tile == 512 ? step_smem_bytes_t<double, 1, 512>(r_cap)
+                         : step_smem_bytes_t<double, 1, 256>(r_cap);
+  return tile == 128 ? step_smem_bytes_t<float, 1, 128>(r_cap)
+         : tile == 512 ? step_smem_bytes_t<float, 1, 512>(r_cap)
+                       : step_smem_bytes_t<float, 1, 256>(r_cap);
+}
+
+// Work items, active-item table, shared memory and persistent grid for
+// tiles of `tile` nodes; uploads the tables (stream-ordered).
+cudaError_t configure(lbm_batch* b, int tile) {
+  std::vector<int2> items;
+  std::vector<int> items_upto(b->ntubes + 1, 0);
+  for (int i = 0; i < b->ntubes; ++i) {
+    const int nt = (int)((b->tubes[i].n + tile - 1) / tile);
+    for (int q = 0; q < nt; ++q) items.push_back(make_int2(i, q));
+    items_upto[i + 1] = items_upto[i] + nt;
+  }
+  // the tubes with nsteps > s form a prefix of the sorted order, and so do
+  // their items
+  std::vector<int> active(std::max(b->max_steps, 1), 0);
+  int p = b->ntubes;
+  for (int st = 0; st < b->max_steps; ++st) {
+    while (p > 0 && b->tubes[p - 1].nsteps <= st) --p;
+    active[st] = items_upto[p];
+  }
+  b->tile = tile;
+  b->smem = step_smem(b->f64, tile, b->r_cap);
+  const void* fn = step_fn(b->f64, b->kahan, tile);
+  cudaError_t e = cudaFuncSetAttribute(
+      fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, tile, b->smem);
+  if (e != cudaSuccess) return e;
+  b->grid = std::max(1, per_sm) * b->nsm;
+  e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(int2) * items.size(),
+                      cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_active, active.data(), sizeof(int) * active.size(),
+                        cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e;
+}
+
+// Initial state of every tube, step counter, reach, flags: as after
+// creation.
+cudaError_t reset_state(lbm_batch* b) {
+  cudaStream_t s = b->stream;
+  const int count = b->ntubes;
+  cudaError_t e = cudaMemsetAsync(b->d_reach, 0, sizeof(int) * 3 * count, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_step, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_flags, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(b->d_eclamps, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  Args a = make_args(b);
+  const int g = std::min(b->ntubes, 65535);
+  if (b->f64) {
+    batch_init<double><<<g, TILE, 0, s>>>(a, (double*)b->buf[0][0],
+                                          (double*)b->buf[0][1],
+                                          (double*)b->buf[0][2], b->d_st);
+    batch_reach_seed<double><<<g, TILE, 0, s>>>(
+        a, (double*)b->buf[0][0], (double*)b->buf[0][1],
+        (double*)b->buf[0][2], b->total);
+  } else {
+    batch_init<float><<<g, TILE, 0, s>>>(a, (float*)b->buf[0][0],
+                                         (float*)b->buf[0][1],
+                                         (float*)b->buf[0][2], b->d_st);
+    batch_reach_seed<float><<<g, TILE, 0, s>>>(
+        a, (float*)b->buf[0][0], (float*)b->buf[0][1], (float*)b->buf[0][2],
+        b->total);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+
+// Times up to 6 steps (after one untimed) with each candidate width from
+// the initial state, keeps the fastest, and resets.
+cudaError_t tune(lbm_batch* b) {
+  const int K = std::min(6, b->max_steps - 1);
+  if (K < 2) return configure(b, 256);
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  int best = 256;
+  double best_ms = -1.0;
+  for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+    const int tw = kTileChoices[c];
+    e = configure(b, tw);
+    if (e == cudaSuccess) e = reset_state(b);
+    if (e == cudaSuccess) e = launch_one(b);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+    for (int k = 0; k < K && e == cudaSuccess; ++k) e = launch_one(b);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess) {
+      b->tune_ms[c] = ms / K;
+      if (best_ms < 0.0 || b->tune_ms[c] < best_ms) {
+        best_ms = b->tune_ms[c];
+        best = tw;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return e;
+  e = configure(b, best);
+  if (e == cudaSuccess) e = reset_state(b);
+  return e;
 }
 
 }  // namespace
@@ -317,9 +477,8 @@ lbm_status lbm_batch_create(int32_t precision, double gamma, double theta,
     return tubes[x].nsteps > tubes[y].nsteps;
   });
   b->pos.resize(count);
-  std::vector<int2> items;
   std::vector<double> st(9 * (size_t)count);
-  long long off = 0;
+  long long off = 0, max_items = 0;
   for (int i = 0; i < (int)count; ++i) {
     const lbm_tube& t = tubes[b->order[i]];
     b->pos[b->order[i]] = i;
@@ -327,51 +486,23 @@ lbm_status lbm_batch_create(int32_t precision, double gamma, double theta,
     b->tubes.push_back(tb);
     const double lam = t.dt * (double)t.n;  // dx = 1/n on [0, 1]
     b->lambda.push_back(lam);
-    const int nt = (int)((t.n + TILE - 1) / TILE);
-    for (int q = 0; q < nt; ++q) items.push_back(make_int2(i, q));
-    double* s = &st[9 * (size_t)i];
-    s[0] = t.x_d;
-    s[1] = lam;
-    s[2] = gamma;
-    s[3] = t.left.rho;
-    s[4] = t.left.u;
-    s[5] = t.left.p;
-    s[6] = t.right.rho;
-    s[7] = t.right.u;
-    s[8] = t.right.p;
+    max_items += (t.n + kTileChoices[0] - 1) / kTileChoices[0];
+    double* q = &st[9 * (size_t)i];
+    q[0] = t.x_d;
+    q[1] = lam;
+    q[2] = gamma;
+    q[3] = t.left.rho;
+    q[4] = t.left.u;
+    q[5] = t.left.p;
+    q[6] = t.right.rho;
+    q[7] = t.right.u;
+    q[8] = t.right.p;
     off += t.n;
   }
-  // active item count per step: the tubes with nsteps > s form a prefix of
-  // the sorted order, and so do their items
-  std::vector<int> active(std::max(maxs, 1), 0);
-  {
-    std::vector<int> items_upto(count + 1, 0);
-    for (int j = 0; j < (int)count; ++j)
-      items_upto[j + 1] =
-          items_upto[j] + (int)((b->tubes[j].n + TILE - 1) / TILE);
-    int p = (int)count;
-    for (int s = 0; s < maxs; ++s) {
-      while (p > 0 && b->tubes[p - 1].nsteps <= s) --p;
-      active[s] = items_upto[p];
-    }
-  }
-  int dev = 0, nsm = 0;
+  int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = step_prepare(1, b->f64, b->smem);
-  if (e == cudaSuccess) {
-    cudaFuncAttributes fa;
-    const void* fn = b->f64 ? (const void*)batch_step<double, false>
-                            : (b->kahan ? (const void*)batch_step<float, true>
-                                        : (const void*)batch_step<float, false>);
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)b->smem);
-    int per_sm = 0;
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TILE, b->smem);
-    if (e == cudaSuccess) b->grid = std::max(1, per_sm) * nsm;
-    (void)fa;
-  }
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) {
     delete b;
     return LBM_ECUDA;
@@ -382,62 +513,30 @@ lbm_status lbm_batch_create(int32_t precision, double gamma, double theta,
     for (int f = 0; f < 3 && ok; ++f)
       ok = cudaMalloc(&b->buf[p][f], es * (size_t)total) == cudaSuccess;
   ok = ok && cudaMalloc(&b->d_tubes, sizeof(Tube) * count) == cudaSuccess;
-  ok = ok && cudaMalloc(&b->d_items, sizeof(int2) * items.size()) == cudaSuccess;
-  ok = ok && cudaMalloc(&b->d_active, sizeof(int) * active.size()) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->d_items, sizeof(int2) * (size_t)max_items) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->d_active, sizeof(int) * (size_t)std::max(maxs, 1)) ==
+                 cudaSuccess;
   ok = ok && cudaMalloc(&b->d_reach, sizeof(int) * 3 * count) == cudaSuccess;
   ok = ok && cudaMalloc(&b->d_step, sizeof(int)) == cudaSuccess;
   ok = ok && cudaMalloc(&b->d_ticket, sizeof(unsigned)) == cudaSuccess;
   ok = ok && cudaMalloc(&b->d_flags, sizeof(unsigned)) == cudaSuccess;
   ok = ok && cudaMalloc(&b->d_eclamps, sizeof(unsigned long long)) == cudaSuccess;
   ok = ok && cudaMalloc(&b->d_totals, sizeof(double) * 3 * count) == cudaSuccess;
-  double* d_st = nullptr;
-  ok = ok && cudaMalloc(&d_st, sizeof(double) * st.size()) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->d_st, sizeof(double) * st.size()) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
-    if (d_st) cudaFree(d_st);
     lbm_batch_destroy(b);
     return LBM_ENOMEM;
   }
-  cudaStream_t s = b->stream;
   e = cudaMemcpyAsync(b->d_tubes, b->tubes.data(), sizeof(Tube) * count,
-                      cudaMemcpyHostToDevice, s);
+                      cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(int2) * items.size(),
-                        cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_active, active.data(), sizeof(int) * active.size(),
-                        cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_st, st.data(), sizeof(double) * st.size(),
-                        cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_reach, 0, sizeof(int) * 3 * count, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_step, 0, sizeof(int), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_flags, 0, sizeof(unsigned), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_eclamps, 0, sizeof(unsigned long long), s);
-  if (e == cudaSuccess) {
-    Args a = make_args(b);
-    const int g = std::min(b->ntubes, 65535);
-    if (b->f64) {
-      batch_init<double><<<g, TILE, 0, s>>>(a, (double*)b->buf[0][0],
-                                            (double*)b->buf[0][1],
-                                            (double*)b->buf[0][2], d_st);
-      batch_reach_seed<double><<<g, TILE, 0, s>>>(
-          a, (double*)b->buf[0][0], (double*)b->buf[0][1],
-          (double*)b->buf[0][2], total);
-    } else {
-      batch_init<float><<<g, TILE, 0, s>>>(a, (float*)b->buf[0][0],
-                                           (float*)b->buf[0][1],
-                                           (float*)b->buf[0][2], d_st);
-      batch_reach_seed<float><<<g, TILE, 0, s>>>(
-          a, (float*)b->buf[0][0], (float*)b->buf[0][1], (float*)b->buf[0][2],
-          total);
-    }
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(d_st);
+    e = cudaMemcpyAsync(b->d_st, st.data(), sizeof(double) * st.size(),
+                        cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = step_prepare(1, b->f64, b->smem);
+  if (e == cudaSuccess) e = tune(b);  // leaves the initial state
   if (e != cudaSuccess) {
+    cudaGetLastError();
     lbm_batch_destroy(b);
     return LBM_ECUDA;
   }
@@ -448,6 +547,7 @@ lbm_status lbm_batch_create(int32_t precision, double gamma, double theta,
 lbm_status lbm_batch_run(lbm_batch* b, int64_t max_launches) {
   if (!b) return LBM_EINVAL;
   if (b->broken) return bfail(b, LBM_ECUDA, "lbm_batch: in an error state: " + b->err);
+  b->runs += 1;
   int64_t want = b->max_steps - b->steps_done;
   if (max_launches >= 0 && max_launches < want) want = max_launches;
   if (want <= 0) return LBM_OK;
@@ -568,6 +668,25 @@ lbm_status lbm_batch_totals(lbm_batch* b, double* out, int64_t count) {
   return LBM_OK;
 }
 
+lbm_status lbm_batch_tuning(const lbm_batch* b, int32_t* tile,
+                            double* ms_per_step) {
+  if (!b) return LBM_EINVAL;
+  if (tile) *tile = b->tile;
+  if (ms_per_step)
+    for (int c = 0; c < 3; ++c) ms_per_step[c] = b->tune_ms[c];
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_set_tile(lbm_batch* b, int32_t tile) {
+  if (!b || (tile != 128 && tile != 256 && tile != 512)) return LBM_EINVAL;
+  if (b->runs > 0)
+    return bfail(b, LBM_EINVAL, "lbm_batch_set_tile: the batch has run");
+  if (b->broken) return bfail(b, LBM_ECUDA, "lbm_batch: in an error state: " + b->err);
+  BCUDA(b, configure(b, tile), "configure");
+  BCUDA(b, reset_state(b), "reset");
+  return LBM_OK;
+}
+
 const char* lbm_batch_last_error(const lbm_batch* b) {
   return b ? b->err.c_str() : "lbm_batch: NULL handle";
 }
@@ -580,7 +699,7 @@ void lbm_batch_destroy(lbm_batch* b) {
     for (int f = 0; f < 3; ++f)
       if (b->buf[p][f]) cudaFree(b->buf[p][f]);
   void* ptrs[] = {b->d_tubes, b->d_items, b->d_active, b->d_reach, b->d_step,
-                  b->d_ticket, b->d_flags, b->d_eclamps, b->d_totals};
+                  b->d_ticket, b->d_flags, b->d_eclamps, b->d_totals, b->d_st};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   cudaGetLastError();

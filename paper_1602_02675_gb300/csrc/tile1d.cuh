@@ -1,5 +1,6 @@
-// One 256-node tile of the 1-D tau = 1 step, for kernels that process many
-// tubes (batched tubes, the serving pool).  Same arithmetic and summation
+// One tile (TW nodes, one per thread; 256 by default) of the 1-D tau = 1
+// step, for kernels that process many tubes (batched tubes, the serving
+// pool).  Same arithmetic and summation
 // order as the single-tube step kernel: equilibrium packets of the tile's
 // sources within reach R in shared memory (Section III.B eqs 13-15, 24-26;
 // Section IV.A), then each thread sums the arrivals at its node over the
@@ -15,7 +16,7 @@ namespace lbm {
 
 constexpr int kTile1d = 256;
 
-template <typename T, bool KAHAN>
+template <typename T, bool KAHAN, int TW = kTile1d>
 __device__ void tile1d_step(const T* __restrict__ in0,
                             const T* __restrict__ in1,
                             const T* __restrict__ in2, T* __restrict__ o0,
@@ -26,13 +27,13 @@ __device__ void tile1d_step(const T* __restrict__ in0,
                             unsigned char* smem) {
   using S = TileShape<1>;
   const int tid = threadIdx.x;
-  SrcLayout<T, 1> L;
+  SrcLayout<T, 1, TW> L;
   L.bind(smem, r_cap);
-  const int x0 = tile * kTile1d;
-  const int W = kTile1d + 2 * R;
+  const int x0 = tile * TW;
+  const int W = TW + 2 * R;
   unsigned long long clamps = 0;
   bool bad = false;
-  for (int i = tid; i < W; i += kTile1d) {
+  for (int i = tid; i < W; i += TW) {
     const long long sx = (long long)x0 - R + i;
     bool fx;
     const int gx = virtual_axis(bc, n, sx, &fx);
@@ -40,7 +41,7 @@ __device__ void tile1d_step(const T* __restrict__ in0,
     T rho = in0[g], mx = in1[g], rE = in2[g];
     if (fx) mx = -mx;
     Equil<T> q = equilibrium<T, 1>(rho, mx, T(0), rE, k);
-    if (sx >= x0 && sx < x0 + kTile1d && sx < n) {
+    if (sx >= x0 && sx < x0 + TW && sx < n) {
       clamps += q.clamp ? 1 : 0;
       bad |= q.bad;
     }

@@ -123,6 +123,9 @@ def load() -> ctypes.CDLL:
         "lbm_pool_destroy": ([_H], None),
         "lbm_measure_fma_peak": ([ctypes.c_int32, _DP, ctypes.c_void_p],
                                  ctypes.c_int),
+        "lbm_batch_tuning": ([_H, ctypes.POINTER(ctypes.c_int32), _DP],
+                             ctypes.c_int),
+        "lbm_batch_set_tile": ([_H, ctypes.c_int32], ctypes.c_int),
         "lbm_step_noalloc": ([ctypes.POINTER(lbm_noalloc_desc),
                               ctypes.c_void_p * 4, ctypes.c_void_p * 4,
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -335,6 +338,17 @@ class Batch:
         out = np.zeros(3 * len(self.tubes))
         self._check(load().lbm_batch_totals(self.h, _dp(out), len(self.tubes)))
         return out.reshape(-1, 3)
+
+    def tuning(self) -> dict:
+        """Tile width in use and measured ms per step of 128, 256, 512."""
+        t = ctypes.c_int32(0)
+        ms = (ctypes.c_double * 3)()
+        self._check(load().lbm_batch_tuning(self.h, ctypes.byref(t), ms))
+        return {"tile": t.value,
+                "ms_per_step": dict(zip((128, 256, 512), list(ms)))}
+
+    def set_tile(self, tile: int):
+        self._check(load().lbm_batch_set_tile(self.h, int(tile)))
 
     def close(self):
         if getattr(self, "h", None):

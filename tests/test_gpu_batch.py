@@ -114,3 +114,32 @@ def test_partial_runs_compose():
     for r, g in zip(ref, got):
         for f in ("rho", "mx", "rhoE"):
             assert np.array_equal(r[f], g[f])
+
+
+def test_tile_width_is_tuned_and_does_not_change_results():
+    """Creation times each candidate tile width on the batch and keeps the
+    fastest; forcing any width gives the same FP64 results bit for bit (every
+    destination sums in the same order), and those equal the oracle's."""
+    specs = _tubes(40, seed=77, nmin=40, nmax=1500)
+    with _make(specs, L.F64) as probe:
+        tn = probe.tuning()
+    assert tn["tile"] in (128, 256, 512)
+    assert all(v > 0 for v in tn["ms_per_step"].values())
+    results = {}
+    for tile in (128, 256, 512):
+        with _make(specs, L.F64) as b:
+            b.set_tile(tile)
+            assert b.tuning()["tile"] == tile
+            b.run()
+            b.sync()
+            results[tile] = [b.moments(j) for j in range(len(specs))]
+    for j in (0, 7, 23, 39):
+        t, ns, lam = specs[j]
+        ph, _ = _oracle_tube(t, ns, lam)
+        for tile in (128, 256, 512):
+            for f in ("rho", "mx", "rhoE"):
+                assert np.array_equal(results[tile][j][f], ph[f]), (tile, j, f)
+    with _make(specs, L.F64) as b:
+        b.run(1)
+        with pytest.raises(L.LbmError):
+            b.set_tile(256)
