@@ -10,11 +10,92 @@
 // oracle does.
 #pragma once
 
+#include <utility>
+
 #include "step_kernel.cuh"
 
 namespace lbm {
 
 constexpr int kTile1d = 256;
+
+// Fast path of the gather for a warp whose sources all share the lattice
+// shift n = floor(V) (N) and the level c1 (C1): packet p, corner k of the
+// source at window slot tid + R + delta lands on the thread's destination,
+// delta = -(N + c_p + k) (eq 28).  The ten landings, sorted as the general
+// loop visits them (source ascending, then packet, then corner), with the
+// same arithmetic, so results are identical to it.
+struct Landing1 {
+  int delta, p, k;
+};
+
+__host__ __device__ constexpr int pk1_cx(int p, int c1) {
+  return p == 0 ? 0 : (p == 1 ? c1 : (p == 2 ? -c1 : (p == 3 ? c1 + 1 : -(c1 + 1))));
+}
+
+template <int N, int C1>
+struct Landings1 {
+  Landing1 v[10];
+  __host__ __device__ constexpr Landings1() : v{} {
+    int m = 0;
+    for (int p = 0; p < 5; ++p)
+      for (int k = 0; k < 2; ++k) v[m++] = Landing1{-N - pk1_cx(p, C1) - k, p, k};
+    for (int a = 1; a < 10; ++a) {
+      Landing1 x = v[a];
+      int b = a - 1;
+      while (b >= 0 && (v[b].delta > x.delta ||
+                        (v[b].delta == x.delta &&
+                         (v[b].p > x.p || (v[b].p == x.p && v[b].k > x.k))))) {
+        v[b + 1] = v[b];
+        --b;
+      }
+      v[b + 1] = x;
+    }
+  }
+};
+
+template <typename T, bool KAHAN, int N, int C1, int I, typename Lay>
+__device__ __forceinline__ void land1(const Lay& L, int base, T& r, T& x,
+                                      T& e, T& cr, T& cx_, T& ce) {
+  constexpr Landings1<N, C1> list{};
+  constexpr Landing1 q = list.v[I];
+  constexpr int lev = q.p == 0 ? 0 : (q.p <= 2 ? 1 : 2);
+  const int s = base + q.delta;
+  const T fx0 = L.f0[s];
+  const T al = q.k == 0 ? T(1) - fx0 : fx0;
+  if (KAHAN) {
+    T y = al * L.mass[lev * L.cap + s] - cr;
+    T t = r + y;
+    cr = (t - r) - y;
+    r = t;
+    y = al * L.Px[q.p * L.cap + s] - cx_;
+    t = x + y;
+    cx_ = (t - x) - y;
+    x = t;
+    y = al * L.PE[q.p * L.cap + s] - ce;
+    t = e + y;
+    ce = (t - e) - y;
+    e = t;
+  } else {
+    r = r + al * L.mass[lev * L.cap + s];
+    x = x + al * L.Px[q.p * L.cap + s];
+    e = e + al * L.PE[q.p * L.cap + s];
+  }
+}
+
+template <typename T, bool KAHAN, int N, int C1, typename Lay, int... I>
+__device__ __forceinline__ void land1_all(const Lay& L, int base, T& r, T& x,
+                                          T& e, T& cr, T& cx_, T& ce,
+                                          std::integer_sequence<int, I...>) {
+  (land1<T, KAHAN, N, C1, I>(L, base, r, x, e, cr, cx_, ce), ...);
+}
+
+template <typename T, bool KAHAN, int N, int C1, typename Lay>
+__device__ __forceinline__ void fast_gather1(const Lay& L, int base, T& r,
+                                             T& x, T& e, T& cr, T& cx_,
+                                             T& ce) {
+  land1_all<T, KAHAN, N, C1>(L, base, r, x, e, cr, cx_, ce,
+                             std::make_integer_sequence<int, 10>{});
+}
 
 template <typename T, bool KAHAN, int TW = kTile1d>
 __device__ void tile1d_step(const T* __restrict__ in0,
@@ -71,7 +152,41 @@ __device__ void tile1d_step(const T* __restrict__ in0,
 
   const int dx = x0 + tid;
   int my_reach = 0;
-  if (dx < n) {
+  // Does every source of this warp's destinations (window slots wb ..
+  // wb + 31 + 2R) share one type with n in {-1, 0} and c1 <= 3?
+  int sel = -1;
+  if (R <= 16) {
+    const int lane = tid & 31, wb = tid & ~31;
+    const int c1r = L.c1[wb], n0r = L.n0[wb];
+    // (R >= c1 + 2 keeps every landing's source inside the window)
+    bool same = c1r >= 0 && c1r <= 3 && n0r >= -1 && n0r <= 0 && R >= c1r + 2 &&
+                L.c1[wb + lane] == c1r && L.n0[wb + lane] == n0r;
+    if (lane < 2 * R)
+      same = same && L.c1[wb + lane + 32] == c1r && L.n0[wb + lane + 32] == n0r;
+    if (__all_sync(0xffffffffu, same)) sel = c1r * 2 + (n0r + 1);
+  }
+  if (dx < n && sel >= 0) {
+    T r = T(0), x = T(0), e = T(0);
+    T cr = T(0), cx_ = T(0), ce = T(0);
+    const int base = tid + R;
+    switch (sel) {
+      case 0: fast_gather1<T, KAHAN, -1, 0>(L, base, r, x, e, cr, cx_, ce); break;
+      case 1: fast_gather1<T, KAHAN, 0, 0>(L, base, r, x, e, cr, cx_, ce); break;
+      case 2: fast_gather1<T, KAHAN, -1, 1>(L, base, r, x, e, cr, cx_, ce); break;
+      case 3: fast_gather1<T, KAHAN, 0, 1>(L, base, r, x, e, cr, cx_, ce); break;
+      case 4: fast_gather1<T, KAHAN, -1, 2>(L, base, r, x, e, cr, cx_, ce); break;
+      case 5: fast_gather1<T, KAHAN, 0, 2>(L, base, r, x, e, cr, cx_, ce); break;
+      case 6: fast_gather1<T, KAHAN, -1, 3>(L, base, r, x, e, cr, cx_, ce); break;
+      default: fast_gather1<T, KAHAN, 0, 3>(L, base, r, x, e, cr, cx_, ce); break;
+    }
+    // the single-tube kernel adds the row sum to a zero total: 0 + s = s
+    const long long o = off + dx;
+    o0[o] = T(0) + r;
+    o1[o] = T(0) + x;
+    o2[o] = T(0) + e;
+    my_reach = reach_bound((double)r, (double)x, 0.0, (double)e,
+                           (float)k.kreach);
+  } else if (dx < n) {
     // one source row; ascending x, packet order, corner order (as the
     // single-tube kernel and the oracle)
     T r = T(0), x = T(0), e = T(0);
