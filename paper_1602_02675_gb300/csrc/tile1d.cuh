@@ -12,11 +12,57 @@
 
 #include <utility>
 
+#include "fp32_arith.cuh"
 #include "step_kernel.cuh"
 
 namespace lbm {
 
 constexpr int kTile1d = 256;
+
+// Equilibrium of one node on the 1-D lattice in FP32 (Section III.B: d0 =
+// theta rho, b0 = 1, b1 = b2 = 2; eqs 13-15, 24-26), branch-free: the
+// quantities of the general equilibrium, with X = D (gamma - 1) e /
+// (1 - theta), c1 from c1_of, d1 by the corrected quotient and d2 from the
+// mass constraint d0 + 2 (d1 + d2) = rho, phi = e - (D/2)(gamma - 1) e.  V a
+// hair below an integer (f = V - floor(V) rounds to 1) is taken as
+// (n + 1, f = 0): the same landings up to a zero-weight term.
+__device__ __forceinline__ Equil<float> equilibrium_1d_f32(float rho, float mx,
+                                                          float rhoE,
+                                                          const EqConst& k) {
+  Equil<float> q;
+  const float inv = rcp_nr(rho);
+  q.V0 = mx * inv;
+  q.V1 = 0.0f;
+  const float e_raw = rhoE * inv - 0.5f * (q.V0 * q.V0);
+  const float e = fmaxf(e_raw, 0.0f);
+  q.e = e;
+  const float X = (float)k.kreach * e;
+  const bool finite_in = fabsf(rho + mx + rhoE) <= 3.0e38f;
+  q.bad = !finite_in || rho < 0.0f || (rho > 0.0f && rho < 1.17549435e-38f) ||
+          !(X <= 1099511627776.0f);
+  q.emits = !q.bad && rho > 0.0f;
+  q.clamp = q.emits && e_raw < 0.0f;
+  const float c1f = c1_of(X);
+  q.c1 = (int)c1f;
+  const float c2f = c1f + 1.0f;
+  const float c1sq = c1f * c1f, c2sq = c2f * c2f;
+  const float den = 2.0f * (c2sq - c1sq);
+  q.d0 = (float)k.theta * rho;
+  const float rho_p = rho - q.d0;
+  q.d1 = div_markstein(rho_p * (c2sq - X), den, rcp_nr(den));
+  q.d2 = 0.5f * rho_p - q.d1;
+  q.phi = e - 0.5f * ((float)k.kq * e);
+  const float fl = floorf(q.V0);
+  q.n0 = (int)fl;
+  q.f0 = q.V0 - fl;
+  if (q.f0 == 1.0f) {
+    q.n0 += 1;
+    q.f0 = 0.0f;
+  }
+  q.n1 = 0;
+  q.f1 = 0.0f;
+  return q;
+}
 
 // Fast path of the gather for a warp whose sources all share the lattice
 // shift n = floor(V) (N) and the level c1 (C1): packet p, corner k of the
@@ -121,7 +167,11 @@ __device__ void tile1d_step(const T* __restrict__ in0,
     const long long g = off + gx;
     T rho = in0[g], mx = in1[g], rE = in2[g];
     if (fx) mx = -mx;
-    Equil<T> q = equilibrium<T, 1>(rho, mx, T(0), rE, k);
+    Equil<T> q;
+    if constexpr (sizeof(T) == sizeof(float))
+      q = equilibrium_1d_f32(rho, mx, rE, k);
+    else
+      q = equilibrium<T, 1>(rho, mx, T(0), rE, k);
     if (sx >= x0 && sx < x0 + TW && sx < n) {
       clamps += q.clamp ? 1 : 0;
       bad |= q.bad;
@@ -184,8 +234,11 @@ __device__ void tile1d_step(const T* __restrict__ in0,
     o0[o] = T(0) + r;
     o1[o] = T(0) + x;
     o2[o] = T(0) + e;
-    my_reach = reach_bound((double)r, (double)x, 0.0, (double)e,
-                           (float)k.kreach);
+    if constexpr (sizeof(T) == sizeof(float))
+      my_reach = reach_bound_f32(r, x, 0.0f, e, (float)k.kreach);
+    else
+      my_reach = reach_bound((double)r, (double)x, 0.0, (double)e,
+                             (float)k.kreach);
   } else if (dx < n) {
     // one source row; ascending x, packet order, corner order (as the
     // single-tube kernel and the oracle)
@@ -234,8 +287,11 @@ __device__ void tile1d_step(const T* __restrict__ in0,
     o0[o] = T(0) + r;
     o1[o] = T(0) + x;
     o2[o] = T(0) + e;
-    my_reach = reach_bound((double)r, (double)x, 0.0, (double)e,
-                           (float)k.kreach);
+    if constexpr (sizeof(T) == sizeof(float))
+      my_reach = reach_bound_f32(r, x, 0.0f, e, (float)k.kreach);
+    else
+      my_reach = reach_bound((double)r, (double)x, 0.0, (double)e,
+                             (float)k.kreach);
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1)
