@@ -197,9 +197,20 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
   for (int b = 0; b < 2 && ok && h->use_rec; ++b) {
     ok = cudaMalloc(&h->rec[b][0], 16 * rec_nodes) == cudaSuccess;
     ok = ok && cudaMalloc(&h->rec[b][1], 8 * rec_nodes) == cudaSuccess;
-    ok = ok && make_record_maps(h->rec[b][0], h->rec[b][1], h->nx, h->ny,
-                                h->rec_pitch, &h->rec_map[b][0],
-                                &h->rec_map[b][1]) == cudaSuccess;
+    if (ok && make_record_maps(h->rec[b][0], h->rec[b][1], h->nx, h->ny,
+                               h->rec_pitch, &h->rec_map[b][0],
+                               &h->rec_map[b][1]) != cudaSuccess) {
+      // no TMA tensor maps on this driver: the handle steps with the
+      // exact-order FP32 kernel instead (no records)
+      cudaGetLastError();
+      for (int q = 0; q < 2; ++q)
+        for (int f = 0; f < 2; ++f)
+          if (h->rec[q][f]) {
+            cudaFree(h->rec[q][f]);
+            h->rec[q][f] = nullptr;
+          }
+      h->use_rec = false;
+    }
   }
   ok = ok && cudaMalloc(&h->scr, sizeof(Scratch)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->part, sizeof(double) * 4 * (size_t)h->part_cap) ==
