@@ -270,6 +270,10 @@ lbm_status lbm_pool_add(lbm_pool* p, const lbm_tube* t, int32_t* slot);
 /* One step of every tube that still has steps to take (one launch). */
 lbm_status lbm_pool_step(lbm_pool* p);
 
+/* nsteps successive lbm_pool_step calls in one call (stops early once no
+   tube has steps left); stream-ordered, does not wait. */
+lbm_status lbm_pool_run(lbm_pool* p, int64_t nsteps);
+
 /* Steps taken and step count of a slot (host-side, does not wait). */
 lbm_status lbm_pool_progress(lbm_pool* p, int32_t slot, int64_t* taken,
                              int64_t* nsteps);

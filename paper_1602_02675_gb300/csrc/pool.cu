@@ -388,6 +388,16 @@ lbm_status lbm_pool_step(lbm_pool* p) {
   return LBM_OK;
 }
 
+lbm_status lbm_pool_run(lbm_pool* p, int64_t nsteps) {
+  if (!p || nsteps < 0) return LBM_EINVAL;
+  for (int64_t i = 0; i < nsteps; ++i) {
+    const lbm_status st = lbm_pool_step(p);
+    if (st != LBM_OK) return st;
+    if (p->stepping.empty() && !p->dirty) break;  // nothing left to step
+  }
+  return LBM_OK;
+}
+
 lbm_status lbm_pool_progress(lbm_pool* p, int32_t slot, int64_t* taken,
                              int64_t* nsteps) {
   if (!p || slot < 0 || slot >= p->max_slots || !p->slots[slot].live)

@@ -114,6 +114,7 @@ def load() -> ctypes.CDLL:
         "lbm_pool_add": ([_H, ctypes.POINTER(lbm_tube),
                           ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "lbm_pool_step": ([_H], ctypes.c_int),
+        "lbm_pool_run": ([_H, ctypes.c_int64], ctypes.c_int),
         "lbm_pool_progress": ([_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                                ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "lbm_pool_read": ([_H, ctypes.c_int32, _DP, _DP, _DP, _DP,
@@ -393,6 +394,10 @@ class Pool:
 
     def step(self):
         self._check(load().lbm_pool_step(self.h))
+
+    def run(self, nsteps: int):
+        """nsteps pool steps in one call."""
+        self._check(load().lbm_pool_run(self.h, int(nsteps)))
 
     def progress(self, slot):
         a, b = ctypes.c_int64(0), ctypes.c_int64(0)

@@ -6,9 +6,10 @@ Section V.C) arrive over time.  Every tick the server
 1. admits waiting requests in arrival order while the device-memory budget
    has room for them (a request that does not fit waits; later, smaller
    ones may pass it);
-2. advances every admitted solve by one step: all 1-D tubes together with
-   one ``lbm_pool_step`` launch, each 2-D grid with one ``lbm_step`` on its
-   own CUDA stream, so their kernels overlap on the device;
+2. advances every admitted solve by up to ``steps_per_tick`` steps: all 1-D
+   tubes together with one ``lbm_pool_run`` call (a launch per step), each 2-D
+   grid with one ``lbm_step`` call on its own CUDA stream, so their kernels
+   overlap on the device;
 3. retires the solves that reached their step count, reading their moments
    back and freeing their memory.
 
@@ -103,6 +104,7 @@ class Server:
     precision: int = L.F32
     pool_nodes: int = 1 << 25
     max_slots: int = 4096
+    steps_per_tick: int = 8   # steps per solve between admissions
     clock: object = time.perf_counter
     pending: list = field(default_factory=list)
     results: dict = field(default_factory=dict)
@@ -178,15 +180,18 @@ class Server:
         self.pending = waiting
 
     def _advance(self) -> None:
+        k = max(1, int(self.steps_per_tick))
         if self._a1:
-            self._pool.step()
+            # the pool advances only the tubes still short of their steps
+            kk = min(k, max(a.steps - a.taken for a in self._a1))
+            self._pool.run(kk)
             for a in self._a1:
-                if a.taken < a.steps:
-                    a.taken += 1
+                a.taken = min(a.steps, a.taken + kk)
         for a in self._a2:
-            if a.taken < a.steps:
-                a.solver.step(1)
-                a.taken += 1
+            n = min(k, a.steps - a.taken)
+            if n > 0:
+                a.solver.step(n)
+                a.taken += n
 
     def _retire(self) -> None:
         keep1 = []
