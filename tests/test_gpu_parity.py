@@ -412,3 +412,16 @@ def test_sod_1d_solve_replayed_from_cuda_graph_bitwise():
             m = s.moments()
             for f in ("rho", "mx", "rhoE"):
                 assert np.array_equal(m[f], o[f]), f
+
+
+def test_fma_peak_measurement():
+    """lbm_measure_fma_peak reports this GPU's FP32 and FP64 FMA rates: both
+    positive, FP32 far above FP64 on a GB300 (FP64 runs at a small fraction
+    of the FP32 rate), and bad arguments are rejected."""
+    p32 = L.lbm_measure_fma_peak(L.F32)
+    p64 = L.lbm_measure_fma_peak(L.F64)
+    assert 1e12 < p32 < 1e15 and 1e10 < p64 < 1e14
+    assert p32 > 8 * p64
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_measure_fma_peak(7)
+    assert e.value.status == L.EINVAL
