@@ -32,6 +32,9 @@ struct lbm_handle {
   bool rec_ok = false;
   int rec_pitch = 0;      // nodes per record row (nx rounded up to even)
   TmaMap rec_map[2][2];   // TMA tensor maps of rec[b][0], rec[b][1]
+  // FP64 square lattice: source records of the state being stepped,
+  // rewritten before every step.
+  double* src64 = nullptr;
   Scratch* scr = nullptr;
   double* part = nullptr;
   int part_cap = 0;
@@ -212,6 +215,8 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
       h->use_rec = false;
     }
   }
+  if (ok && h->f64 && c.dim == 2)
+    ok = cudaMalloc(&h->src64, src64_bytes(h->n)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->scr, sizeof(Scratch)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->part, sizeof(double) * 4 * (size_t)h->part_cap) ==
                  cudaSuccess;
@@ -336,6 +341,7 @@ lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
   a.k = h->k;
   a.scr = h->scr;
   a.part = h->part;
+  a.src64 = h->src64;
   for (int64_t s = 0; s < nsteps; ++s) {
     for (int f = 0; f < 4; ++f) {
       a.in[f] = h->buf[h->cur][f];
@@ -464,6 +470,7 @@ void lbm_destroy(lbm_handle* h) {
   for (int b = 0; b < 2; ++b)
     for (int f = 0; f < 2; ++f)
       if (h->rec[b][f]) cudaFree(h->rec[b][f]);
+  if (h->src64) cudaFree(h->src64);
   if (h->scr) cudaFree(h->scr);
   if (h->part) cudaFree(h->part);
   if (h->staging) cudaFree(h->staging);

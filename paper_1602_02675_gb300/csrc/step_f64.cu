@@ -5,6 +5,51 @@
 
 namespace lbm {
 
+// FP64 square lattice: the source records of the input state (one thread
+// per node), written before each step; energy clamps and bad states are
+// counted here, once per node.
+__global__ void __launch_bounds__(256) records2d_f64(const StepArgs a) {
+  const long long n = (long long)a.nx * a.ny;
+  double* Sr = a.src64;
+  unsigned long long clamps = 0;
+  bool bad = false;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n;
+       g += (long long)gridDim.x * blockDim.x) {
+    const Equil<double> q =
+        equilibrium<double, 2>(ld<double>(a.in[0], g), ld<double>(a.in[1], g),
+                               ld<double>(a.in[2], g), ld<double>(a.in[3], g),
+                               a.k);
+    clamps += q.clamp ? 1 : 0;
+    bad |= q.bad;
+    long long w = s64_word(-1, 0, 0);
+    if (q.emits) {
+#pragma unroll
+      for (int p = 0; p < TileShape<2>::NP; ++p) {
+        double px, py, pe;
+        packet_fields<double, 2>(q, p, &px, &py, &pe);
+        Sr[(kS64Px + p) * n + g] = px;
+        Sr[(kS64Py + p) * n + g] = py;
+        Sr[(kS64PE + p) * n + g] = pe;
+      }
+      Sr[kS64Mass * n + g] = q.d1;
+      Sr[(kS64Mass + 1) * n + g] = q.d2;
+      Sr[kS64F * n + g] = q.f0;
+      Sr[(kS64F + 1) * n + g] = q.f1;
+      Sr[kS64V * n + g] = q.V0;
+      Sr[(kS64V + 1) * n + g] = q.V1;
+      Sr[kS64Phi * n + g] = q.phi;
+      w = s64_word(q.c1, q.n0, q.n1);
+    }
+    reinterpret_cast<long long*>(Sr + kS64Word * n)[g] = w;
+  }
+  const unsigned long long wc = __reduce_add_sync(0xffffffffu, (unsigned)clamps);
+  const bool wb = __any_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0) {
+    if (wc) atomicAdd(&a.scr->eclamps, wc);
+    if (wb) atomicOr(&a.scr->flags, kFlagState);
+  }
+}
+
 cudaError_t launch_step_f64(int dim, const StepArgs& a, size_t smem,
                             cudaStream_t s) {
   if (dim == 1) {
@@ -16,6 +61,11 @@ cudaError_t launch_step_f64(int dim, const StepArgs& a, size_t smem,
     else
       step_kernel<double, 1, false><<<grid, 256, smem, s>>>(a);
   } else {
+    if (a.src64) {
+      const long long n = (long long)a.nx * a.ny;
+      const long long nb = (n + 255) / 256;
+      records2d_f64<<<(unsigned)(nb < 152 * 16 ? nb : 152 * 16), 256, 0, s>>>(a);
+    }
     dim3 grid((a.nx + TileShape<2>::TX - 1) / TileShape<2>::TX,
               (a.ny + TileShape<2>::TY - 1) / TileShape<2>::TY);
     step_kernel<double, 2, false><<<grid, 256, smem, s>>>(a);

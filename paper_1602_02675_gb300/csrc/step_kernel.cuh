@@ -133,6 +133,18 @@ __device__ __forceinline__ double dev_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float dev_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double dev_floor(double x) { return floor(x); }
 
+// Lattice shift n = floor(V) and split fraction f = V - n per axis (eqs
+// 23, 28, 29).
+template <typename T>
+__device__ __forceinline__ void equil_split(Equil<T>& q) {
+  T fl0 = dev_floor(q.V0);
+  q.n0 = (int)fl0;
+  q.f0 = q.V0 - fl0;
+  T fl1 = dev_floor(q.V1);
+  q.n1 = (int)fl1;
+  q.f1 = q.V1 - fl1;
+}
+
 // Equilibrium of one node (Section III.B): V and e (eq 13, eq 15 text),
 // c1 = int(sqrt(D (gamma-1) e rho / (rho - b0 d0))), c2 = c1 + 1 (eq 26),
 // d1, d2 (eqs 24-25), phi (eq 15), floor/fraction of V (eqs 23, 28, 29).
@@ -187,12 +199,7 @@ __device__ __forceinline__ Equil<T> equilibrium(T rho, T mx, T my, T rhoE,
   } else {
     q.phi = T(k.kphi) * e;
   }
-  T fl0 = dev_floor(q.V0);
-  q.n0 = (int)fl0;
-  q.f0 = q.V0 - fl0;
-  T fl1 = dev_floor(q.V1);
-  q.n1 = (int)fl1;
-  q.f1 = q.V1 - fl1;
+  equil_split(q);
   q.emits = true;
   return q;
 }
@@ -219,6 +226,53 @@ __device__ __forceinline__ void packet(int p, int c1, int* cx, int* cy,
   }
 }
 
+// Fields of packet p of an emitting node (eqs 11-14, 21): momentum d (V +
+// c') per axis and energy d (|V + c'|^2 / 2 + phi).
+template <typename T, int DIM>
+__device__ __forceinline__ void packet_fields(const Equil<T>& q, int p,
+                                              T* px, T* py, T* pe) {
+  int cx, cy, lev;
+  packet<DIM>(p, q.c1, &cx, &cy, &lev);
+  const T d = DIM == 1 ? (lev == 0 ? q.d0 : (lev == 1 ? q.d1 : q.d2))
+                       : (lev == 0 ? q.d1 : q.d2);
+  T cbx = q.V0 + (T)cx;  // eq 12: V + c'
+  if (DIM == 1) {
+    *px = d * cbx;
+    *py = T(0);
+    *pe = d * (T(0.5) * (cbx * cbx) + q.phi);
+  } else {
+    T cby = q.V1 + (T)cy;
+    *px = d * cbx;
+    *py = d * cby;
+    *pe = d * (T(0.5) * (cbx * cbx + cby * cby) + q.phi);
+  }
+}
+
+// FP64 square-lattice source records, written once per node before each
+// step (records2d_f64) and copied into the windows of the step's tiles
+// instead of forming each window source's equilibrium again.  Structure of
+// arrays, n = nx * ny doubles each, node y * nx + x: P_x of packets 0-7,
+// P_y of 0-7, P_E of 0-7, d1, d2, f_x, f_y, V_x, V_y, phi, then one array of
+// 64-bit words holding c1, n_x, n_y as 16-bit fields (c1 = -1: the node
+// emits nothing).
+enum : int {
+  kS64Px = 0,
+  kS64Py = 8,
+  kS64PE = 16,
+  kS64Mass = 24,
+  kS64F = 26,
+  kS64V = 28,
+  kS64Phi = 30,
+  kS64Word = 31,
+  kS64Arrays = 32
+};
+
+__device__ __forceinline__ long long s64_word(int c1, int n0, int n1) {
+  return (long long)(unsigned short)(short)c1 |
+         ((long long)(unsigned short)(short)n0 << 16) |
+         ((long long)(unsigned short)(short)n1 << 32);
+}
+
 // Conservative migration reach of one node: >= floor(|V_a|) + 1 + c2 as the
 // step computes them, evaluated in FP32 with margins that cover its rounding
 // (an over-estimate only widens the source window).
@@ -239,13 +293,190 @@ __device__ __forceinline__ int reach_bound(double rho, double mx, double my,
   return r > 1.0e8f ? 100000000 : (int)r;
 }
 
+// Adds a row pair's sums to a destination's totals (plain, or compensated
+// when KAHAN).
+template <typename T, bool KAHAN>
+__device__ __forceinline__ void add_pair(T (&tot)[4], T (&comp)[4],
+                                         const T (&pair)[4]) {
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    if (KAHAN) {
+      T yk = pair[f] - comp[f];
+      T t = tot[f] + yk;
+      comp[f] = (t - tot[f]) - yk;
+      tot[f] = t;
+    } else {
+      tot[f] = tot[f] + pair[f];
+    }
+  }
+}
+
+// ---- square lattice, uniform window ----
+// When every source of the block's window emits with the same level c1 and
+// the same lattice shift (n_x, n_y) = floor(V) (eqs 23, 29), packet p and
+// corner k of the source at offset a from a destination land on it exactly
+// when a = -(n + c'_p + k), so each of the 32 landings comes from a source
+// at a compile-time offset.  RowLandingList holds them in the order of the
+// scan in step 2: rows by j = |a_y| (a_y = -j first), then a_x, packet,
+// corner.  Visiting them with the same row, pair and total sums gives the
+// scan's result bit for bit: the scan's other candidates contribute no
+// term.
+__host__ __device__ constexpr int sq_cx(int p, int c1) {
+  return (p & 3) == 0 ? c1 + (p >> 2) : ((p & 3) == 1 ? -(c1 + (p >> 2)) : 0);
+}
+__host__ __device__ constexpr int sq_cy(int p, int c1) {
+  return (p & 3) == 2 ? c1 + (p >> 2) : ((p & 3) == 3 ? -(c1 + (p >> 2)) : 0);
+}
+
+struct RowLanding {
+  int j, side, ax, p, k;
+};
+
+template <int C1, int NX, int NY>
+struct RowLandingList {
+  static constexpr int N = 32;
+  RowLanding v[N];
+  __host__ __device__ constexpr RowLandingList() : v{} {
+    int n = 0;
+    for (int p = 0; p < 8; ++p)
+      for (int k = 0; k < 4; ++k) {
+        const int ax = -(NX + sq_cx(p, C1) + (k & 1));
+        const int ay = -(NY + sq_cy(p, C1) + (k >> 1));
+        v[n] = RowLanding{ay < 0 ? -ay : ay, ay > 0 ? 1 : 0, ax, p, k};
+        ++n;
+      }
+    for (int a = 1; a < N; ++a) {
+      RowLanding x = v[a];
+      int b = a - 1;
+      while (b >= 0 && before(x, v[b])) {
+        v[b + 1] = v[b];
+        --b;
+      }
+      v[b + 1] = x;
+    }
+  }
+  __host__ __device__ static constexpr bool before(const RowLanding& x,
+                                                   const RowLanding& y) {
+    if (x.j != y.j) return x.j < y.j;
+    if (x.side != y.side) return x.side < y.side;
+    if (x.ax != y.ax) return x.ax < y.ax;
+    if (x.p != y.p) return x.p < y.p;
+    return x.k < y.k;
+  }
+  // first landing of row (j, side) and one past its last
+  __host__ __device__ constexpr int begin(int j, int side) const {
+    int i = 0;
+    while (i < N && (v[i].j < j || (v[i].j == j && v[i].side < side))) ++i;
+    return i;
+  }
+  __host__ __device__ constexpr int end(int j, int side) const {
+    int i = begin(j, side);
+    while (i < N && v[i].j == j && v[i].side == side) ++i;
+    return i;
+  }
+  __host__ __device__ constexpr int jmax() const { return v[N - 1].j; }
+};
+
+// Landings I .. E-1 of one row into the row sums r (the scan's expressions:
+// corner weight (1 - f or f per axis, eq 29) times the packet's mass,
+// momentum and energy).  srow: the slot of the row's source at a_x = 0.
+template <typename T, class LL, int I, int E, typename Lay>
+__device__ __forceinline__ void row_range(const Lay& L, int srow, T (&w)[4],
+                                          T (&r)[4]) {
+  if constexpr (I < E) {
+    constexpr LL ll{};
+    constexpr RowLanding q = ll.v[I];
+    constexpr bool fresh = I == 0 || ll.v[I - 1].j != q.j ||
+                           ll.v[I - 1].side != q.side ||
+                           ll.v[I - 1].ax != q.ax;
+    const int s = srow + q.ax;
+    if constexpr (fresh) {
+      const T fx0 = L.f0[s];
+      const T fy0 = L.f1[s];
+      w[0] = T(1) - fx0;
+      w[1] = fx0;
+      w[2] = T(1) - fy0;
+      w[3] = fy0;
+    }
+    const T al = w[q.k & 1] * w[2 + (q.k >> 1)];
+    r[0] = r[0] + al * L.mass[(q.p >> 2) * L.cap + s];
+    r[1] = r[1] + al * L.Px[q.p * L.cap + s];
+    r[2] = r[2] + al * L.Py[q.p * L.cap + s];
+    r[3] = r[3] + al * L.PE[q.p * L.cap + s];
+    row_range<T, LL, I + 1, E>(L, srow, w, r);
+  }
+}
+
+// Rows J .. jmax of a uniform window; s0: the destination's slot, W: the
+// window's width.
+template <typename T, bool KAHAN, class LL, int J, typename Lay>
+__device__ __forceinline__ void uniform_rows(const Lay& L, int s0, int W,
+                                             T (&tot)[4], T (&comp)[4]) {
+  constexpr LL ll{};
+  if constexpr (J <= ll.jmax()) {
+    T w[4];
+    T pair[4];
+    {
+      T r[4] = {T(0), T(0), T(0), T(0)};
+      row_range<T, LL, ll.begin(J, 0), ll.end(J, 0)>(L, s0 - J * W, w, r);
+#pragma unroll
+      for (int f = 0; f < 4; ++f) pair[f] = r[f];
+    }
+    if constexpr (J > 0) {
+      T r[4] = {T(0), T(0), T(0), T(0)};
+      row_range<T, LL, ll.begin(J, 1), ll.end(J, 1)>(L, s0 + J * W, w, r);
+#pragma unroll
+      for (int f = 0; f < 4; ++f) pair[f] = pair[f] + r[f];
+    }
+    add_pair<T, KAHAN>(tot, comp, pair);
+    uniform_rows<T, KAHAN, LL, J + 1>(L, s0, W, tot, comp);
+  }
+}
+
+// A uniform window's gather: the compile-time rows, then rows jmax+1 .. R,
+// which hold no landing (their pair sums are zero, added as the scan adds
+// them).
+template <typename T, bool KAHAN, int C1, int NX, int NY, typename Lay>
+__device__ __forceinline__ void uniform_gather(const Lay& L, int s0, int W,
+                                            int R, T (&tot)[4],
+                                            T (&comp)[4]) {
+  using LL = RowLandingList<C1, NX, NY>;
+  uniform_rows<T, KAHAN, LL, 0>(L, s0, W, tot, comp);
+  for (int j = LL{}.jmax() + 1; j <= R; ++j) {
+    T pair[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int f = 0; f < 4; ++f) pair[f] = pair[f] + T(0);
+    add_pair<T, KAHAN>(tot, comp, pair);
+  }
+}
+
+// Type word of a source for the uniformity test: 0 if it does not emit,
+// else bit 31, c1 (bits 16..23) and n_x, n_y + 128 (bits 8..15, 0..7),
+// each clamped so that no other value aliases the fast path's.
+__device__ __forceinline__ unsigned window_type(bool emits, int c1, int n0,
+                                                int n1) {
+  if (!emits) return 0u;
+  const unsigned c = (unsigned)min(c1, 255);
+  const unsigned ux = (unsigned)(min(max(n0, -128), 127) + 128);
+  const unsigned uy = (unsigned)(min(max(n1, -128), 127) + 128);
+  return 0x80000000u | (c << 16) | (ux << 8) | uy;
+}
+
 template <typename T>
 __device__ __forceinline__ T ld(const void* p, long long i) {
   return reinterpret_cast<const T*>(p)[i];
 }
 
+// Blocks per multiprocessor the register budget is sized for: the FP64
+// square-lattice window fills the shared memory of a multiprocessor, so one
+// block may use up to 255 registers a thread.
+template <typename T, int DIM>
+constexpr int step_min_blocks() {
+  return (DIM == 2 && sizeof(T) == 8) ? 1 : 4;
+}
+
 template <typename T, int DIM, bool KAHAN, int NT = 256>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, (step_min_blocks<T, DIM>()))
     step_kernel(const StepArgs a) {
   using S = TileShape<DIM>;
   // tile width: NT destinations in 1-D (one per thread), TXW in 2-D
@@ -254,6 +485,7 @@ __global__ void __launch_bounds__(NT)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red_sum[4][NT / 32];
   __shared__ int red_reach[NT / 32];
+  __shared__ unsigned red_tmin[NT / 32], red_tmax[NT / 32];
   __shared__ int is_last;
 
   const int tid = threadIdx.x;
@@ -276,6 +508,12 @@ __global__ void __launch_bounds__(NT)
   // ---- 1. equilibrium packets of every source in reach of the tile ----
   unsigned long long my_clamps = 0;
   bool my_bad = false;
+  unsigned my_tmin = 0xffffffffu, my_tmax = 0u;  // window types (2-D)
+  // FP64 square lattice with source records: copy each window source's
+  // record; a mirror image (reflecting wall) flips V and forms its packets
+  // from the flipped V as the equilibrium would (the level densities, c1 and
+  // phi depend on |V| only).  Otherwise form every source's equilibrium.
+  const bool from_rec = DIM == 2 && sizeof(T) == 8 && a.src64 != nullptr;
   for (int i = tid; i < NS; i += NT) {
     int ly = i / W;
     int lx = i - ly * W;
@@ -285,18 +523,75 @@ __global__ void __launch_bounds__(NT)
     int gx = virtual_axis(a.bc_x, a.nx, sx, &fx);
     int gy = (DIM == 2) ? virtual_axis(a.bc_y, a.ny, sy, &fy) : 0;
     long long g = (long long)gy * a.nx + gx;
-    T rho = ld<T>(a.in[0], g);
-    T mx = ld<T>(a.in[1], g);
-    T my = (DIM == 2) ? ld<T>(a.in[2], g) : T(0);
-    T rE = ld<T>(a.in[3], g);
-    if (fx) mx = -mx;
-    if (fy) my = -my;
-    Equil<T> q = equilibrium<T, DIM>(rho, mx, my, rE, a.k);
-    bool own = sx >= x0 && sx < x0 + TXW && sx < a.nx &&
-               (DIM == 1 || (sy >= y0 && sy < y0 + S::TY && sy < a.ny));
-    if (own) {
-      my_clamps += q.clamp ? 1 : 0;
-      my_bad |= q.bad;
+    Equil<T> q;
+    if constexpr (DIM == 2 && sizeof(T) == 8) {
+      if (from_rec) {
+        const long long n = (long long)a.nx * a.ny;
+        const double* Sr = a.src64;
+        const long long w =
+            reinterpret_cast<const long long*>(Sr + kS64Word * n)[g];
+        const int c1 = (short)(w & 0xffff);
+        const int n0 = (short)((w >> 16) & 0xffff);
+        const int n1 = (short)((w >> 32) & 0xffff);
+        if (c1 < 0) {
+          L.c1[i] = -1;
+          my_tmin = 0u;
+          continue;
+        }
+        if (!fx && !fy) {
+          L.c1[i] = (short)c1;
+          L.n0[i] = (short)n0;
+          L.n1[i] = (short)n1;
+          L.f0[i] = Sr[kS64F * n + g];
+          L.f1[i] = Sr[(kS64F + 1) * n + g];
+          L.mass[i] = Sr[kS64Mass * n + g];
+          L.mass[L.cap + i] = Sr[(kS64Mass + 1) * n + g];
+#pragma unroll
+          for (int p = 0; p < S::NP; ++p) {
+            L.Px[p * L.cap + i] = Sr[(kS64Px + p) * n + g];
+            L.Py[p * L.cap + i] = Sr[(kS64Py + p) * n + g];
+            L.PE[p * L.cap + i] = Sr[(kS64PE + p) * n + g];
+          }
+          const unsigned wt = window_type(true, c1, n0, n1);
+          my_tmin = min(my_tmin, wt);
+          my_tmax = max(my_tmax, wt);
+          continue;
+        }
+        q.emits = true;
+        q.bad = false;
+        q.clamp = false;
+        q.c1 = c1;
+        q.V0 = Sr[kS64V * n + g];
+        q.V1 = Sr[(kS64V + 1) * n + g];
+        if (fx) q.V0 = -q.V0;
+        if (fy) q.V1 = -q.V1;
+        q.e = T(0);
+        q.d0 = T(0);
+        q.d1 = Sr[kS64Mass * n + g];
+        q.d2 = Sr[(kS64Mass + 1) * n + g];
+        q.phi = Sr[kS64Phi * n + g];
+        equil_split(q);
+      }
+    }
+    if (!from_rec) {
+      T rho = ld<T>(a.in[0], g);
+      T mx = ld<T>(a.in[1], g);
+      T my = (DIM == 2) ? ld<T>(a.in[2], g) : T(0);
+      T rE = ld<T>(a.in[3], g);
+      if (fx) mx = -mx;
+      if (fy) my = -my;
+      q = equilibrium<T, DIM>(rho, mx, my, rE, a.k);
+      bool own = sx >= x0 && sx < x0 + TXW && sx < a.nx &&
+                 (DIM == 1 || (sy >= y0 && sy < y0 + S::TY && sy < a.ny));
+      if (own) {
+        my_clamps += q.clamp ? 1 : 0;
+        my_bad |= q.bad;
+      }
+    }
+    if (DIM == 2) {
+      const unsigned wt = window_type(q.emits, q.c1, q.n0, q.n1);
+      my_tmin = min(my_tmin, wt);
+      my_tmax = max(my_tmax, wt);
     }
     if (!q.emits) {
       L.c1[i] = -1;
@@ -317,24 +612,42 @@ __global__ void __launch_bounds__(NT)
     }
 #pragma unroll
     for (int p = 0; p < S::NP; ++p) {
-      int cx, cy, lev;
-      packet<DIM>(p, q.c1, &cx, &cy, &lev);
-      T d = L.mass[lev * L.cap + i];
-      T cbx = q.V0 + (T)cx;  // eq 12: V + c'
-      if (DIM == 1) {
-        L.Px[p * L.cap + i] = d * cbx;
-        L.PE[p * L.cap + i] = d * (T(0.5) * (cbx * cbx) + q.phi);
-      } else {
-        T cby = q.V1 + (T)cy;
-        L.Px[p * L.cap + i] = d * cbx;
-        L.Py[p * L.cap + i] = d * cby;
-        L.PE[p * L.cap + i] = d * (T(0.5) * (cbx * cbx + cby * cby) + q.phi);
-      }
+      T px, py, pe;
+      packet_fields<T, DIM>(q, p, &px, &py, &pe);
+      L.Px[p * L.cap + i] = px;
+      if (DIM == 2) L.Py[p * L.cap + i] = py;
+      L.PE[p * L.cap + i] = pe;
     }
   }
   if (my_clamps) atomicAdd(&a.scr->eclamps, my_clamps);
   if (my_bad) atomicOr(&a.scr->flags, kFlagState);
+  if (DIM == 2) {
+    const unsigned wmin = __reduce_min_sync(0xffffffffu, my_tmin);
+    const unsigned wmax = __reduce_max_sync(0xffffffffu, my_tmax);
+    if ((tid & 31) == 0) {
+      red_tmin[tid >> 5] = wmin;
+      red_tmax[tid >> 5] = wmax;
+    }
+  }
   __syncthreads();
+  // One (c1, n) for the whole window?  Then step 2 takes the compile-time
+  // landings (c1 <= 2, n_x, n_y in {-1, 0}; their offsets are within c1 + 2
+  // <= R of the destination).
+  int uni_sel = -1;
+  if (DIM == 2) {
+    unsigned tmin = red_tmin[0], tmax = red_tmax[0];
+#pragma unroll
+    for (int w = 1; w < NT / 32; ++w) {
+      tmin = min(tmin, red_tmin[w]);
+      tmax = max(tmax, red_tmax[w]);
+    }
+    const int c1 = (int)((tmin >> 16) & 0xff);
+    const int nx = (int)((tmin >> 8) & 0xff) - 128;
+    const int ny = (int)(tmin & 0xff) - 128;
+    if (tmin == tmax && tmin != 0u && c1 <= 2 && c1 + 2 <= R && nx >= -1 &&
+        nx <= 0 && ny >= -1 && ny <= 0)
+      uni_sel = c1 * 4 + (nx + 1) * 2 + (ny + 1);
+  }
 
   // ---- 2. gather the arrivals at this thread's destination ----
   const int tx = tid % TXW;
@@ -344,7 +657,28 @@ __global__ void __launch_bounds__(NT)
   const bool valid = dx < a.nx && dy < a.ny;
   T tot[4] = {T(0), T(0), T(0), T(0)};
   T comp[4] = {T(0), T(0), T(0), T(0)};
-  if (valid) {
+  bool gathered = false;
+  if constexpr (DIM == 2) {
+   if (valid && uni_sel >= 0) {
+    gathered = true;
+    const int s0 = (ty + R) * W + (tx + R);
+    switch (uni_sel) {
+      case 0: uniform_gather<T, KAHAN, 0, -1, -1>(L, s0, W, R, tot, comp); break;
+      case 1: uniform_gather<T, KAHAN, 0, -1, 0>(L, s0, W, R, tot, comp); break;
+      case 2: uniform_gather<T, KAHAN, 0, 0, -1>(L, s0, W, R, tot, comp); break;
+      case 3: uniform_gather<T, KAHAN, 0, 0, 0>(L, s0, W, R, tot, comp); break;
+      case 4: uniform_gather<T, KAHAN, 1, -1, -1>(L, s0, W, R, tot, comp); break;
+      case 5: uniform_gather<T, KAHAN, 1, -1, 0>(L, s0, W, R, tot, comp); break;
+      case 6: uniform_gather<T, KAHAN, 1, 0, -1>(L, s0, W, R, tot, comp); break;
+      case 7: uniform_gather<T, KAHAN, 1, 0, 0>(L, s0, W, R, tot, comp); break;
+      case 8: uniform_gather<T, KAHAN, 2, -1, -1>(L, s0, W, R, tot, comp); break;
+      case 9: uniform_gather<T, KAHAN, 2, -1, 0>(L, s0, W, R, tot, comp); break;
+      case 10: uniform_gather<T, KAHAN, 2, 0, -1>(L, s0, W, R, tot, comp); break;
+      default: uniform_gather<T, KAHAN, 2, 0, 0>(L, s0, W, R, tot, comp); break;
+    }
+   }
+  }
+  if (valid && !gathered) {
     for (int j = 0; j <= Ry; ++j) {
       T pair[4];
 #pragma unroll 1
@@ -406,17 +740,7 @@ __global__ void __launch_bounds__(NT)
           pair[3] = pair[3] + e;
         }
       }
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        if (KAHAN) {  // compensated sum of the row-pair sums
-          T yk = pair[f] - comp[f];
-          T t = tot[f] + yk;
-          comp[f] = (t - tot[f]) - yk;
-          tot[f] = t;
-        } else {
-          tot[f] = tot[f] + pair[f];
-        }
-      }
+      add_pair<T, KAHAN>(tot, comp, pair);  // compensated when KAHAN
     }
   }
 

@@ -80,6 +80,33 @@ def random_smooth_prims(dim: int, nx: int, ny: int, seed: int,
     return out
 
 
+def banded_prims(nx: int, ny: int, seed: int, u_band=(0.1, 0.8),
+                 v_band=(-0.8, -0.1), p_over_rho: float = 1.0):
+    """Smooth random 2-D primitive fields (rho, u, v, p), x fastest, whose
+    velocities stay inside the given open bands and whose p/rho stays within
+    15 % of p_over_rho, so that every node starts with the same floor of
+    its lattice velocity (at lambda = 1) and the same level speeds."""
+    rng = np.random.default_rng(seed)
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    X, Y = np.meshgrid(x, y)
+    ph = rng.uniform(0.0, 2.0 * np.pi, 6)
+    k = rng.integers(1, 4, 6)
+
+    def wave(i, j):
+        return np.sin(2 * np.pi * (k[i] * X + k[j] * Y) + ph[i])
+
+    def band(lo, hi, w):
+        mid, half = 0.5 * (lo + hi), 0.45 * (hi - lo)
+        return mid + half * w
+
+    rho = 1.0 + 0.3 * wave(0, 1)
+    u = band(u_band[0], u_band[1], wave(2, 3))
+    v = band(v_band[0], v_band[1], wave(4, 5))
+    p = rho * p_over_rho * (1.0 + 0.15 * np.cos(2 * np.pi * (X - Y) + ph[1]))
+    return [rho.ravel(), u.ravel(), v.ravel(), p.ravel()]
+
+
 def random_node_prims(dim: int, n: int, seed: int):
     """Independent random states per node (harsh: exercises every level
     count, fractional velocities of both signs, large reach)."""

@@ -114,6 +114,26 @@ def test_random_2d_fp64_bitwise(bcs, shape):
     _assert_bitwise(g, o, 2)
 
 
+@pytest.mark.parametrize("bcs", [(L.PERIODIC, L.PERIODIC),
+                                 (L.TRANSMISSIVE, L.REFLECTING)])
+@pytest.mark.parametrize("bands,p_over_rho", [
+    (((0.1, 0.8), (-0.8, -0.1)), 1.0),   # c1 = 1, n = (0, -1)
+    (((-0.8, -0.1), (0.1, 0.8)), 0.3),   # c1 = 0, n = (-1, 0)
+    (((0.1, 0.8), (0.1, 0.8)), 3.0),     # c1 = 2, n = (0, 0)
+    (((-0.8, -0.1), (-0.8, -0.1)), 1.0)])
+def test_one_type_windows_fp64_bitwise(bcs, bands, p_over_rho):
+    """Every node of the first state has the same level speeds and lattice
+    shift, so the interior windows take the compile-time landings; the
+    result must still match the oracle's scan order bit for bit."""
+    nx, ny = 100, 44
+    prims = I.banded_prims(nx, ny, seed=3100 + int(10 * p_over_rho),
+                           u_band=bands[0], v_band=bands[1],
+                           p_over_rho=p_over_rho)
+    g = _gpu(2, nx, ny, *bcs, prims=prims, steps=3)
+    o = _oracle(2, nx, ny, *bcs, prims=prims, steps=3)
+    _assert_bitwise(g, o, 2)
+
+
 def test_sod_2d_paper_lattice_fp64_bitwise():
     """The paper's 400 x 4 square lattice (Section V.C) with x-only data."""
     lam = 1.0
