@@ -64,12 +64,12 @@ struct StepArgs {
   int prefetch_ahead = 0;
   // FP64 square lattice only: source records of the input state, written
   // by the launcher's records pass before each step (layout in
-  // step_kernel.cuh, kS64Arrays x 8 bytes per node), or null.
+  // step_kernel.cuh, 34 x 8 bytes per node), or null.
   double* src64 = nullptr;
 };
 
 // Bytes of the FP64 square-lattice source records of n nodes.
-inline size_t src64_bytes(long long n) { return (size_t)n * 32 * 8; }
+inline size_t src64_bytes(long long n) { return (size_t)n * 34 * 8; }
 
 // Launch helpers (step kernels).
 size_t step_smem_bytes(int dim, bool f64, int r_cap);

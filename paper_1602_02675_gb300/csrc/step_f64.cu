@@ -33,8 +33,10 @@ __global__ void __launch_bounds__(256) records2d_f64(const StepArgs a) {
       }
       Sr[kS64Mass * n + g] = q.d1;
       Sr[(kS64Mass + 1) * n + g] = q.d2;
-      Sr[kS64F * n + g] = q.f0;
-      Sr[(kS64F + 1) * n + g] = q.f1;
+      double w4[4];
+      corner_weights(q, w4);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) Sr[(kS64W + k) * n + g] = w4[k];
       Sr[kS64V * n + g] = q.V0;
       Sr[(kS64V + 1) * n + g] = q.V1;
       Sr[kS64Phi * n + g] = q.phi;

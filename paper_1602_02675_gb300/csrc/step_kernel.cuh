@@ -45,8 +45,9 @@ __host__ __device__ inline int step_tile_1d(int nx) {
 
 // Shared-memory layout of the source records, structure of arrays, sized
 // for r_cap and a tile TXW destinations wide.  Per source: packet fields Px,
-// Py (2-D), PE per packet, the mass per level, split fractions f, and packed
-// integers (c1, n_x, n_y).
+// Py (2-D), PE per packet, the mass per level, the split fraction f (1-D)
+// or the four corner weights (2-D, eq 29: (1-f_x)(1-f_y), f_x(1-f_y),
+// (1-f_x)f_y, f_x f_y), and packed integers (c1, n_x, n_y).
 template <typename T, int DIM, int TXW = TileShape<DIM>::TX>
 struct SrcLayout {
   using S = TileShape<DIM>;
@@ -55,8 +56,8 @@ struct SrcLayout {
   T* Py;
   T* PE;
   T* mass;
-  T* f0;
-  T* f1;
+  T* f0;  // 1-D
+  T* wt;  // 2-D, corner k at wt[k * cap + source]
   short* c1;
   short* n0;
   short* n1;
@@ -66,7 +67,7 @@ struct SrcLayout {
   }
   __host__ __device__ static size_t bytes(int r_cap) {
     size_t c = (size_t)capacity(r_cap);
-    size_t nt = (size_t)S::NP * (DIM == 2 ? 3 : 2) + S::NLEV + (DIM == 2 ? 2 : 1);
+    size_t nt = (size_t)S::NP * (DIM == 2 ? 3 : 2) + S::NLEV + (DIM == 2 ? 4 : 1);
     size_t b = c * nt * sizeof(T) + c * 3 * sizeof(short);
     return (b + 15) & ~size_t(15);
   }
@@ -85,13 +86,14 @@ struct SrcLayout {
     p += S::NP * cap;
     mass = p;
     p += S::NLEV * cap;
-    f0 = p;
-    p += cap;
     if (DIM == 2) {
-      f1 = p;
-      p += cap;
+      f0 = nullptr;
+      wt = p;
+      p += 4 * cap;
     } else {
-      f1 = nullptr;
+      f0 = p;
+      wt = nullptr;
+      p += cap;
     }
     short* q = reinterpret_cast<short*>(p);
     c1 = q;
@@ -252,20 +254,31 @@ __device__ __forceinline__ void packet_fields(const Equil<T>& q, int p,
 // step (records2d_f64) and copied into the windows of the step's tiles
 // instead of forming each window source's equilibrium again.  Structure of
 // arrays, n = nx * ny doubles each, node y * nx + x: P_x of packets 0-7,
-// P_y of 0-7, P_E of 0-7, d1, d2, f_x, f_y, V_x, V_y, phi, then one array of
-// 64-bit words holding c1, n_x, n_y as 16-bit fields (c1 = -1: the node
-// emits nothing).
+// P_y of 0-7, P_E of 0-7, d1, d2, the four corner weights, V_x, V_y, phi,
+// then one array of 64-bit words holding c1, n_x, n_y as 16-bit fields
+// (c1 = -1: the node emits nothing).
 enum : int {
   kS64Px = 0,
   kS64Py = 8,
   kS64PE = 16,
   kS64Mass = 24,
-  kS64F = 26,
-  kS64V = 28,
-  kS64Phi = 30,
-  kS64Word = 31,
-  kS64Arrays = 32
+  kS64W = 26,
+  kS64V = 30,
+  kS64Phi = 32,
+  kS64Word = 33,
+  kS64Arrays = 34
 };
+
+// Corner weights of a square-lattice source (eq 29), in corner order
+// (0,0), (1,0), (0,1), (1,1): products of (1 - f, f) per axis.
+template <typename T>
+__device__ __forceinline__ void corner_weights(const Equil<T>& q, T (&w)[4]) {
+  const T wx0 = T(1) - q.f0, wy0 = T(1) - q.f1;
+  w[0] = wx0 * wy0;
+  w[1] = q.f0 * wy0;
+  w[2] = wx0 * q.f1;
+  w[3] = q.f0 * q.f1;
+}
 
 __device__ __forceinline__ long long s64_word(int c1, int n0, int n1) {
   return (long long)(unsigned short)(short)c1 |
@@ -378,32 +391,20 @@ struct RowLandingList {
 };
 
 // Landings I .. E-1 of one row into the row sums r (the scan's expressions:
-// corner weight (1 - f or f per axis, eq 29) times the packet's mass,
-// momentum and energy).  srow: the slot of the row's source at a_x = 0.
+// corner weight (eq 29) times the packet's mass, momentum and energy).
+// srow: the slot of the row's source at a_x = 0.
 template <typename T, class LL, int I, int E, typename Lay>
-__device__ __forceinline__ void row_range(const Lay& L, int srow, T (&w)[4],
-                                          T (&r)[4]) {
+__device__ __forceinline__ void row_range(const Lay& L, int srow, T (&r)[4]) {
   if constexpr (I < E) {
     constexpr LL ll{};
     constexpr RowLanding q = ll.v[I];
-    constexpr bool fresh = I == 0 || ll.v[I - 1].j != q.j ||
-                           ll.v[I - 1].side != q.side ||
-                           ll.v[I - 1].ax != q.ax;
     const int s = srow + q.ax;
-    if constexpr (fresh) {
-      const T fx0 = L.f0[s];
-      const T fy0 = L.f1[s];
-      w[0] = T(1) - fx0;
-      w[1] = fx0;
-      w[2] = T(1) - fy0;
-      w[3] = fy0;
-    }
-    const T al = w[q.k & 1] * w[2 + (q.k >> 1)];
+    const T al = L.wt[q.k * L.cap + s];
     r[0] = r[0] + al * L.mass[(q.p >> 2) * L.cap + s];
     r[1] = r[1] + al * L.Px[q.p * L.cap + s];
     r[2] = r[2] + al * L.Py[q.p * L.cap + s];
     r[3] = r[3] + al * L.PE[q.p * L.cap + s];
-    row_range<T, LL, I + 1, E>(L, srow, w, r);
+    row_range<T, LL, I + 1, E>(L, srow, r);
   }
 }
 
@@ -414,17 +415,16 @@ __device__ __forceinline__ void uniform_rows(const Lay& L, int s0, int W,
                                              T (&tot)[4], T (&comp)[4]) {
   constexpr LL ll{};
   if constexpr (J <= ll.jmax()) {
-    T w[4];
     T pair[4];
     {
       T r[4] = {T(0), T(0), T(0), T(0)};
-      row_range<T, LL, ll.begin(J, 0), ll.end(J, 0)>(L, s0 - J * W, w, r);
+      row_range<T, LL, ll.begin(J, 0), ll.end(J, 0)>(L, s0 - J * W, r);
 #pragma unroll
       for (int f = 0; f < 4; ++f) pair[f] = r[f];
     }
     if constexpr (J > 0) {
       T r[4] = {T(0), T(0), T(0), T(0)};
-      row_range<T, LL, ll.begin(J, 1), ll.end(J, 1)>(L, s0 + J * W, w, r);
+      row_range<T, LL, ll.begin(J, 1), ll.end(J, 1)>(L, s0 + J * W, r);
 #pragma unroll
       for (int f = 0; f < 4; ++f) pair[f] = pair[f] + r[f];
     }
@@ -542,8 +542,8 @@ __global__ void __launch_bounds__(NT, (step_min_blocks<T, DIM>()))
           L.c1[i] = (short)c1;
           L.n0[i] = (short)n0;
           L.n1[i] = (short)n1;
-          L.f0[i] = Sr[kS64F * n + g];
-          L.f1[i] = Sr[(kS64F + 1) * n + g];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) L.wt[k * L.cap + i] = Sr[(kS64W + k) * n + g];
           L.mass[i] = Sr[kS64Mass * n + g];
           L.mass[L.cap + i] = Sr[(kS64Mass + 1) * n + g];
 #pragma unroll
@@ -600,8 +600,14 @@ __global__ void __launch_bounds__(NT, (step_min_blocks<T, DIM>()))
     L.c1[i] = (short)q.c1;
     L.n0[i] = (short)q.n0;
     L.n1[i] = (short)q.n1;
-    L.f0[i] = q.f0;
-    if (DIM == 2) L.f1[i] = q.f1;
+    if (DIM == 1) {
+      L.f0[i] = q.f0;
+    } else {
+      T w4[4];
+      corner_weights(q, w4);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) L.wt[k * L.cap + i] = w4[k];
+    }
     if (DIM == 1) {
       L.mass[0 * L.cap + i] = q.d0;
       L.mass[1 * L.cap + i] = q.d1;
@@ -703,13 +709,11 @@ __global__ void __launch_bounds__(NT, (step_min_blocks<T, DIM>()))
             bool yarm = (ox == 0 || ox == 1) && near_y;
             if (!xarm && !yarm) continue;
           }
-          const T fx0 = L.f0[s];
-          const T wx[2] = {T(1) - fx0, fx0};
-          T wy[2] = {T(1), T(0)};
-          if (DIM == 2) {
-            const T fy0 = L.f1[s];
-            wy[0] = T(1) - fy0;
-            wy[1] = fy0;
+          T wx[2] = {T(1), T(0)};
+          if (DIM == 1) {
+            const T fx0 = L.f0[s];
+            wx[0] = T(1) - fx0;
+            wx[1] = fx0;
           }
 #pragma unroll
           for (int p = 0; p < S::NP; ++p) {
@@ -720,7 +724,7 @@ __global__ void __launch_bounds__(NT, (step_min_blocks<T, DIM>()))
               const int kx = kk & 1, ky = kk >> 1;
               if (cx + kx != ox) continue;
               if (DIM == 2 && cy + ky != oy) continue;
-              const T al = (DIM == 1) ? wx[kx] : wx[kx] * wy[ky];
+              const T al = (DIM == 1) ? wx[kx] : L.wt[kk * L.cap + s];
               r = r + al * L.mass[lev * L.cap + s];
               x = x + al * L.Px[p * L.cap + s];
               if (DIM == 2) y = y + al * L.Py[p * L.cap + s];

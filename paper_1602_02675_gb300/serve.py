@@ -57,12 +57,12 @@ class Request:
 def bytes_needed(req: Request, precision: int) -> int:
     """Device bytes a solve holds while admitted: 2-D grids two moment sets
     (4 fields), two sets of 24-byte equilibrium records (FP32) or one set of
-    256-byte source records (FP64), the FP64 readback staging (5 fields) and
+    272-byte source records (FP64), the FP64 readback staging (5 fields) and
     per-tile partials; 1-D tubes two sets of 3 fields in the pool."""
     b = 8 if precision == L.F64 else 4
     n = req.nodes()
     if req.dim == 2:
-        rec = 2 * 24 if precision == L.F32 else 256
+        rec = 2 * 24 if precision == L.F32 else 272
         return n * (2 * 4 * b + rec + 5 * 8) + (n // 256 + 1) * 32 + (1 << 20)
     return n * 2 * 3 * b
 
