@@ -40,7 +40,12 @@ cudaError_t launch_step_f32(int dim, const StepArgs& a, size_t smem,
     const int tw = step_tile_1d(a.nx);
     dim3 grid((a.nx + tw - 1) / tw, 1);
     const size_t sm32 = step_smem_bytes_t<float, 1, 32>(a.r_cap);
-    if (tw == 32 && a.kahan)
+    const size_t sm16 = step_smem_bytes_t<float, 1, 16>(a.r_cap);
+    if (tw == 16 && a.kahan)
+      step_kernel<float, 1, true, 32, 16><<<grid, 32, sm16, s>>>(a);
+    else if (tw == 16)
+      step_kernel<float, 1, false, 32, 16><<<grid, 32, sm16, s>>>(a);
+    else if (tw == 32 && a.kahan)
       step_kernel<float, 1, true, 32><<<grid, 32, sm32, s>>>(a);
     else if (tw == 32)
       step_kernel<float, 1, false, 32><<<grid, 32, sm32, s>>>(a);
@@ -148,10 +153,12 @@ size_t step_smem_f32(int dim, int r_cap) {
 cudaError_t step_prepare_f32(int dim, size_t smem) {
   cudaError_t e;
   if (dim == 1) {
-    const void* fns[4] = {(const void*)step_kernel<float, 1, true>,
+    const void* fns[6] = {(const void*)step_kernel<float, 1, true>,
                           (const void*)step_kernel<float, 1, false>,
                           (const void*)step_kernel<float, 1, true, 32>,
-                          (const void*)step_kernel<float, 1, false, 32>};
+                          (const void*)step_kernel<float, 1, false, 32>,
+                          (const void*)step_kernel<float, 1, true, 32, 16>,
+                          (const void*)step_kernel<float, 1, false, 32, 16>};
     for (const void* fn : fns) {
       e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem);
@@ -181,7 +188,7 @@ namespace lbm {
 // Raise (never lower) the dynamic shared-memory limit of the FP32 step
 // kernels so a launch needing smem bytes is allowed.
 cudaError_t step_raise_smem_f32(int dim, size_t smem) {
-  const void* fns[4] = {
+  const void* fns[6] = {
       dim == 1 ? (const void*)step_kernel<float, 1, true>
                : (const void*)step_kernel<float, 2, true>,
       dim == 1 ? (const void*)step_kernel<float, 1, false>
@@ -189,6 +196,10 @@ cudaError_t step_raise_smem_f32(int dim, size_t smem) {
       dim == 1 ? (const void*)step_kernel<float, 1, true, 32>
                : (const void*)fast::step2d_f32,
       dim == 1 ? (const void*)step_kernel<float, 1, false, 32>
+               : (const void*)fast::step2d_f32,
+      dim == 1 ? (const void*)step_kernel<float, 1, true, 32, 16>
+               : (const void*)fast::step2d_f32,
+      dim == 1 ? (const void*)step_kernel<float, 1, false, 32, 16>
                : (const void*)fast::step2d_f32};
   for (const void* fn : fns) {
     cudaFuncAttributes at;

@@ -57,9 +57,12 @@ cudaError_t launch_step_f64(int dim, const StepArgs& a, size_t smem,
   if (dim == 1) {
     const int tw = step_tile_1d(a.nx);
     dim3 grid((a.nx + tw - 1) / tw, 1);
-    if (tw == 32)
+    if (tw == 16)
+      step_kernel<double, 1, false, 32, 16><<<grid, 32,
+          step_smem_bytes_t<double, 1, 16>(a.r_cap), s>>>(a);
+    else if (tw == 32)
       step_kernel<double, 1, false, 32><<<grid, 32,
-                                          step_smem_bytes_t<double, 1, 32>(a.r_cap), s>>>(a);
+          step_smem_bytes_t<double, 1, 32>(a.r_cap), s>>>(a);
     else
       step_kernel<double, 1, false><<<grid, 256, smem, s>>>(a);
   } else {
@@ -82,13 +85,15 @@ size_t step_smem_f64(int dim, int r_cap) {
 
 cudaError_t step_prepare_f64(int dim, size_t smem) {
   if (dim == 1) {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<double, 1, false, 32>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(step_kernel<double, 1, false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
+    const void* fns[3] = {(const void*)step_kernel<double, 1, false, 32, 16>,
+                          (const void*)step_kernel<double, 1, false, 32>,
+                          (const void*)step_kernel<double, 1, false>};
+    for (const void* fn : fns) {
+      cudaError_t e = cudaFuncSetAttribute(
+          fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
   return cudaFuncSetAttribute(step_kernel<double, 2, false>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -102,10 +107,13 @@ namespace lbm {
 // Raise (never lower) the dynamic shared-memory limit of the FP64 step
 // kernel so a launch needing smem bytes is allowed.
 cudaError_t step_raise_smem_f64(int dim, size_t smem) {
-  const void* fns[2] = {dim == 1 ? (const void*)step_kernel<double, 1, false>
-                                 : (const void*)step_kernel<double, 2, false>,
-                        dim == 1 ? (const void*)step_kernel<double, 1, false, 32>
-                                 : (const void*)step_kernel<double, 2, false>};
+  const void* fns[3] = {
+      dim == 1 ? (const void*)step_kernel<double, 1, false>
+               : (const void*)step_kernel<double, 2, false>,
+      dim == 1 ? (const void*)step_kernel<double, 1, false, 32>
+               : (const void*)step_kernel<double, 2, false>,
+      dim == 1 ? (const void*)step_kernel<double, 1, false, 32, 16>
+               : (const void*)step_kernel<double, 2, false>};
   for (const void* fn : fns) {
     cudaFuncAttributes at;
     cudaError_t e = cudaFuncGetAttributes(&at, fn);

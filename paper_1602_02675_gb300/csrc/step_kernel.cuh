@@ -34,13 +34,14 @@ struct TileShape<2> {
   static constexpr int TX = 32, TY = 8, NP = 8, NK = 4, NLEV = 2;
 };
 
-// 1-D tile width of the exact-order kernel for a tube of nx nodes: 32 until
-// tiles of 256 would give two blocks per multiprocessor of a GB300 (152),
-// so that short tubes spread over many multiprocessors (the FP64 rate per
-// multiprocessor is low).  Each destination's sum order does not depend on
-// the tile.
+// 1-D tile width of the exact-order kernel for a tube of nx nodes: 256 once
+// such tiles give two blocks per multiprocessor of a GB300 (152); below that
+// 32-thread blocks with narrow tiles, so that short tubes spread over many
+// multiprocessors (the FP64 rate per multiprocessor is low) and the window
+// of a tile (its width + 2 R sources) is formed in one pass of the block's
+// 32 threads.  Each destination's sum order does not depend on the tile.
 __host__ __device__ inline int step_tile_1d(int nx) {
-  return nx < 2 * 152 * 256 ? 32 : 256;
+  return nx < 2 * 152 * 256 ? (nx <= 152 * 16 ? 16 : 32) : 256;
 }
 
 // Shared-memory layout of the source records, structure of arrays, sized
@@ -475,13 +476,16 @@ constexpr int step_min_blocks() {
   return (DIM == 2 && sizeof(T) == 8) ? 1 : 4;
 }
 
-template <typename T, int DIM, bool KAHAN, int NT = 256>
+template <typename T, int DIM, bool KAHAN, int NT = 256, int TW1 = NT>
 __global__ void __launch_bounds__(NT, (step_min_blocks<T, DIM>()))
     step_kernel(const StepArgs a) {
   using S = TileShape<DIM>;
-  // tile width: NT destinations in 1-D (one per thread), TXW in 2-D
-  constexpr int TXW = DIM == 1 ? NT : S::TX;
-  static_assert(DIM == 2 ? NT == S::TX * S::TY : NT % 32 == 0, "tile");
+  // tile width: TW1 <= NT destinations in 1-D (one per thread; the other
+  // threads only help form the window's sources), TXW = 32 in 2-D
+  constexpr int TXW = DIM == 1 ? TW1 : S::TX;
+  static_assert(DIM == 2 ? NT == S::TX * S::TY
+                         : (NT % 32 == 0 && TW1 <= NT && NT % TW1 == 0),
+                "tile");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red_sum[4][NT / 32];
   __shared__ int red_reach[NT / 32];
