@@ -21,9 +21,10 @@
  *    max_reach <= 6 two sets of per-node equilibrium records (24 bytes per
  *    node each), which carry each node's equilibrium (Section III.B) from
  *    the step that produced the node to the step that uses it; an F64
- *    square-lattice handle holds one set of source records (272 bytes per
- *    node: the node's packets, level densities and corner weights),
- *    rewritten from the moments at the start of every step.
+ *    square-lattice handle holds one set of source records (248 bytes per
+ *    node of the grid padded by max_reach on every side: each source's
+ *    packets, level densities and corner weights), rewritten from the
+ *    moments at the start of every step.
  *  - Work is issued on the stream given in lbm_config.stream (a
  *    cudaStream_t, or NULL for the default stream), in call order.
  *    lbm_step returns before the GPU finishes; lbm_moments, lbm_conservation,

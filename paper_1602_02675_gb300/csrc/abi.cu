@@ -216,7 +216,8 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
     }
   }
   if (ok && h->f64 && c.dim == 2)
-    ok = cudaMalloc(&h->src64, src64_bytes(h->n)) == cudaSuccess;
+    ok = cudaMalloc(&h->src64, src64_bytes(h->nx, h->ny, h->r_cap)) ==
+         cudaSuccess;
   ok = ok && cudaMalloc(&h->scr, sizeof(Scratch)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->part, sizeof(double) * 4 * (size_t)h->part_cap) ==
                  cudaSuccess;

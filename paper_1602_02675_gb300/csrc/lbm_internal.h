@@ -62,14 +62,17 @@ struct StepArgs {
   // Tiles resident at once (set by the launcher): a block prefetches into
   // L2 the input records of the tile that many launches ahead.
   int prefetch_ahead = 0;
-  // FP64 square lattice only: source records of the input state, written
-  // by the launcher's records pass before each step (layout in
-  // step_kernel.cuh, 34 x 8 bytes per node), or null.
+  // FP64 square lattice only: source records of the input state over the
+  // grid padded by r_cap, written by the launcher's records pass before
+  // each step (layout in step_kernel.cuh), or null.
   double* src64 = nullptr;
 };
 
-// Bytes of the FP64 square-lattice source records of n nodes.
-inline size_t src64_bytes(long long n) { return (size_t)n * 34 * 8; }
+// Bytes of the FP64 square-lattice source records of an nx x ny grid with
+// reach limit r_cap: 31 x 8 bytes per padded node.
+inline size_t src64_bytes(int nx, int ny, int r_cap) {
+  return (size_t)(nx + 2 * r_cap) * (size_t)(ny + 2 * r_cap) * 31 * 8;
+}
 
 // Launch helpers (step kernels).
 size_t step_smem_bytes(int dim, bool f64, int r_cap);

@@ -1,17 +1,21 @@
 // Fused tau = 1 step: equilibrium + migration + summation + reach, one launch.
 //
-// One block owns a tile of destination nodes (1-D: 256 x 1, 2-D: 32 x 8,
-// one destination per thread).  It
+// One block owns a tile of destination nodes (1-D: 16, 32 or 256 x 1 by the
+// tube's length, 2-D: 32 x 8; one destination per thread).  It
 //  1. computes the equilibrium packets of every source node within the
 //     migration reach R of the tile once (Section III.B eqs 13-15, 24-26;
 //     packets eqs 11-14, 21; split weights eq 23, 28, 29) and keeps them in
 //     shared memory; sources beyond the domain edge are the additional points
-//     of Section V.B (zero-gradient, periodic image or mirror image);
+//     of Section V.B (zero-gradient, periodic image or mirror image).  FP64
+//     on the square lattice copies them from the source records a separate
+//     pass wrote for every node (the same arithmetic, once per node);
 //  2. lets each thread gather the arrivals at its destination (eqs 6, 10,
 //     22): source rows at distance j below and above the destination are
 //     summed row by row (ascending x, packet table order, corner order) and
 //     added as pairs, j = 0..R.  The order is the same relative to every
-//     destination and symmetric under y -> -y;
+//     destination and symmetric under y -> -y.  A square-lattice window
+//     whose sources share one type visits its 32 landings from a
+//     compile-time list in that order; other windows test every candidate;
 //  3. writes the new moments, reduces a conservative reach for the next step
 //     and, when asked, FP64 totals; the last block to finish publishes them.
 // No floating-point atomics anywhere; every sum has a fixed order.
@@ -251,23 +255,22 @@ __device__ __forceinline__ void packet_fields(const Equil<T>& q, int p,
   }
 }
 
-// FP64 square-lattice source records, written once per node before each
-// step (records2d_f64) and copied into the windows of the step's tiles
-// instead of forming each window source's equilibrium again.  Structure of
-// arrays, n = nx * ny doubles each, node y * nx + x: P_x of packets 0-7,
-// P_y of 0-7, P_E of 0-7, d1, d2, the four corner weights, V_x, V_y, phi,
-// then one array of 64-bit words holding c1, n_x, n_y as 16-bit fields
-// (c1 = -1: the node emits nothing).
+// FP64 square-lattice source records, written for every node and every
+// additional point before each step (records2d_f64) and read by the step's
+// gather instead of forming each window source's equilibrium again.
+// Structure of arrays over the grid padded by r_cap on every side (source
+// (x, y) at (y + r_cap) * (nx + 2 r_cap) + x + r_cap), one double per
+// source each: P_x of packets 0-7, P_y of 0-7, P_E of 0-7, d1, d2, the four
+// corner weights, then one array of 64-bit words holding c1, n_x, n_y as
+// 16-bit fields (c1 = -1: the source emits nothing).
 enum : int {
   kS64Px = 0,
   kS64Py = 8,
   kS64PE = 16,
   kS64Mass = 24,
   kS64W = 26,
-  kS64V = 30,
-  kS64Phi = 32,
-  kS64Word = 33,
-  kS64Arrays = 34
+  kS64Word = 30,
+  kS64Arrays = 31
 };
 
 // Corner weights of a square-lattice source (eq 29), in corner order
@@ -394,12 +397,12 @@ struct RowLandingList {
 // Landings I .. E-1 of one row into the row sums r (the scan's expressions:
 // corner weight (eq 29) times the packet's mass, momentum and energy).
 // srow: the slot of the row's source at a_x = 0.
-template <typename T, class LL, int I, int E, typename Lay>
-__device__ __forceinline__ void row_range(const Lay& L, int srow, T (&r)[4]) {
+template <typename T, class LL, int I, int E, typename Lay, typename Idx>
+__device__ __forceinline__ void row_range(const Lay& L, Idx srow, T (&r)[4]) {
   if constexpr (I < E) {
     constexpr LL ll{};
     constexpr RowLanding q = ll.v[I];
-    const int s = srow + q.ax;
+    const Idx s = srow + q.ax;
     const T al = L.wt[q.k * L.cap + s];
     r[0] = r[0] + al * L.mass[(q.p >> 2) * L.cap + s];
     r[1] = r[1] + al * L.Px[q.p * L.cap + s];
@@ -410,9 +413,9 @@ __device__ __forceinline__ void row_range(const Lay& L, int srow, T (&r)[4]) {
 }
 
 // Rows J .. jmax of a uniform window; s0: the destination's slot, W: the
-// window's width.
-template <typename T, bool KAHAN, class LL, int J, typename Lay>
-__device__ __forceinline__ void uniform_rows(const Lay& L, int s0, int W,
+// distance between the slots of vertically adjacent sources.
+template <typename T, bool KAHAN, class LL, int J, typename Lay, typename Idx>
+__device__ __forceinline__ void uniform_rows(const Lay& L, Idx s0, Idx W,
                                              T (&tot)[4], T (&comp)[4]) {
   constexpr LL ll{};
   if constexpr (J <= ll.jmax()) {
@@ -437,10 +440,11 @@ __device__ __forceinline__ void uniform_rows(const Lay& L, int s0, int W,
 // A uniform window's gather: the compile-time rows, then rows jmax+1 .. R,
 // which hold no landing (their pair sums are zero, added as the scan adds
 // them).
-template <typename T, bool KAHAN, int C1, int NX, int NY, typename Lay>
-__device__ __forceinline__ void uniform_gather(const Lay& L, int s0, int W,
-                                            int R, T (&tot)[4],
-                                            T (&comp)[4]) {
+template <typename T, bool KAHAN, int C1, int NX, int NY, typename Lay,
+          typename Idx>
+__device__ __forceinline__ void uniform_gather(const Lay& L, Idx s0, Idx W,
+                                               int R, T (&tot)[4],
+                                               T (&comp)[4]) {
   using LL = RowLandingList<C1, NX, NY>;
   uniform_rows<T, KAHAN, LL, 0>(L, s0, W, tot, comp);
   for (int j = LL{}.jmax() + 1; j <= R; ++j) {
@@ -468,6 +472,109 @@ __device__ __forceinline__ T ld(const void* p, long long i) {
   return reinterpret_cast<const T*>(p)[i];
 }
 
+// Step 3 of a step launch (all NT threads of the block call it): write the
+// destination's new moments (tot; valid: the thread has a destination at
+// (dx, dy)), reduce a conservative reach for the next step and, when asked,
+// the block's FP64 partial totals; the last block to finish combines the
+// partials in a fixed order and publishes reach and totals.
+template <typename T, int DIM, int NT>
+__device__ __forceinline__ void step_finish(const StepArgs& a, bool valid,
+                                            int dx, int dy,
+                                            const T (&tot)[4]) {
+  __shared__ double red_sum[4][NT / 32];
+  __shared__ int red_reach[NT / 32];
+  __shared__ int is_last;
+  const int tid = threadIdx.x;
+  int my_reach = 0;
+  if (valid) {
+    const long long o = (long long)dy * a.nx + dx;
+    reinterpret_cast<T*>(a.out[0])[o] = tot[0];
+    reinterpret_cast<T*>(a.out[1])[o] = tot[1];
+    if (DIM == 2) reinterpret_cast<T*>(a.out[2])[o] = tot[2];
+    reinterpret_cast<T*>(a.out[3])[o] = tot[3];
+    my_reach = reach_bound((double)tot[0], (double)tot[1],
+                           DIM == 2 ? (double)tot[2] : 0.0, (double)tot[3],
+                           (float)a.k.kreach);
+  }
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+    my_reach = max(my_reach, __shfl_xor_sync(0xffffffffu, my_reach, off));
+  double ps[4] = {0.0, 0.0, 0.0, 0.0};
+  if (a.do_cons) {
+    if (valid) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) ps[f] = (double)tot[f];
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1)
+        ps[f] += __shfl_down_sync(0xffffffffu, ps[f], off);
+  }
+  if (lane == 0) {
+    red_reach[warp] = my_reach;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) red_sum[f][warp] = ps[f];
+  }
+  __syncthreads();
+  const int nblk = a.nblocks;
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  if (tid == 0) {
+    int rb = red_reach[0];
+    double bs[4] = {red_sum[0][0], red_sum[1][0], red_sum[2][0], red_sum[3][0]};
+    for (int w = 1; w < NT / 32; ++w) {
+      rb = max(rb, red_reach[w]);
+#pragma unroll
+      for (int f = 0; f < 4; ++f) bs[f] += red_sum[f][w];
+    }
+    atomicMax(&a.scr->reach_next, rb);
+    if (a.do_cons) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) a.part[(long long)bid * 4 + f] = bs[f];
+    }
+    __threadfence();
+    unsigned done = atomicAdd(&a.scr->ticket, 1u);
+    is_last = (done == (unsigned)(nblk - 1));
+  }
+  __syncthreads();
+  if (!is_last) return;
+
+  // ---- last block: publish reach and totals (fixed order) ----
+  __threadfence();
+  if (a.do_cons) {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = tid; b < nblk; b += NT) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) s[f] += __ldcg(&a.part[(long long)b * 4 + f]);
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1)
+        s[f] += __shfl_down_sync(0xffffffffu, s[f], off);
+    if (lane == 0) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) red_sum[f][warp] = s[f];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int f = 0; f < 4; ++f) {
+        double t = red_sum[f][0];
+        for (int w = 1; w < NT / 32; ++w) t += red_sum[f][w];
+        a.scr->cons[f] = t;
+      }
+    }
+  }
+  if (tid == 0) {
+    int rn = atomicAdd(&a.scr->reach_next, 0);
+    a.scr->reach = rn;
+    a.scr->reach_next = 0;
+    a.scr->ticket = 0u;
+    __threadfence();
+  }
+}
+
 // Blocks per multiprocessor the register budget is sized for: the FP64
 // square-lattice window fills the shared memory of a multiprocessor, so one
 // block may use up to 255 registers a thread.
@@ -487,10 +594,7 @@ __global__ void __launch_bounds__(NT, (step_min_blocks<T, DIM>()))
                          : (NT % 32 == 0 && TW1 <= NT && NT % TW1 == 0),
                 "tile");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red_sum[4][NT / 32];
-  __shared__ int red_reach[NT / 32];
   __shared__ unsigned red_tmin[NT / 32], red_tmax[NT / 32];
-  __shared__ int is_last;
 
   const int tid = threadIdx.x;
   const int R = a.scr->reach;
@@ -513,11 +617,6 @@ __global__ void __launch_bounds__(NT, (step_min_blocks<T, DIM>()))
   unsigned long long my_clamps = 0;
   bool my_bad = false;
   unsigned my_tmin = 0xffffffffu, my_tmax = 0u;  // window types (2-D)
-  // FP64 square lattice with source records: copy each window source's
-  // record; a mirror image (reflecting wall) flips V and forms its packets
-  // from the flipped V as the equilibrium would (the level densities, c1 and
-  // phi depend on |V| only).  Otherwise form every source's equilibrium.
-  const bool from_rec = DIM == 2 && sizeof(T) == 8 && a.src64 != nullptr;
   for (int i = tid; i < NS; i += NT) {
     int ly = i / W;
     int lx = i - ly * W;
@@ -528,56 +627,7 @@ __global__ void __launch_bounds__(NT, (step_min_blocks<T, DIM>()))
     int gy = (DIM == 2) ? virtual_axis(a.bc_y, a.ny, sy, &fy) : 0;
     long long g = (long long)gy * a.nx + gx;
     Equil<T> q;
-    if constexpr (DIM == 2 && sizeof(T) == 8) {
-      if (from_rec) {
-        const long long n = (long long)a.nx * a.ny;
-        const double* Sr = a.src64;
-        const long long w =
-            reinterpret_cast<const long long*>(Sr + kS64Word * n)[g];
-        const int c1 = (short)(w & 0xffff);
-        const int n0 = (short)((w >> 16) & 0xffff);
-        const int n1 = (short)((w >> 32) & 0xffff);
-        if (c1 < 0) {
-          L.c1[i] = -1;
-          my_tmin = 0u;
-          continue;
-        }
-        if (!fx && !fy) {
-          L.c1[i] = (short)c1;
-          L.n0[i] = (short)n0;
-          L.n1[i] = (short)n1;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) L.wt[k * L.cap + i] = Sr[(kS64W + k) * n + g];
-          L.mass[i] = Sr[kS64Mass * n + g];
-          L.mass[L.cap + i] = Sr[(kS64Mass + 1) * n + g];
-#pragma unroll
-          for (int p = 0; p < S::NP; ++p) {
-            L.Px[p * L.cap + i] = Sr[(kS64Px + p) * n + g];
-            L.Py[p * L.cap + i] = Sr[(kS64Py + p) * n + g];
-            L.PE[p * L.cap + i] = Sr[(kS64PE + p) * n + g];
-          }
-          const unsigned wt = window_type(true, c1, n0, n1);
-          my_tmin = min(my_tmin, wt);
-          my_tmax = max(my_tmax, wt);
-          continue;
-        }
-        q.emits = true;
-        q.bad = false;
-        q.clamp = false;
-        q.c1 = c1;
-        q.V0 = Sr[kS64V * n + g];
-        q.V1 = Sr[(kS64V + 1) * n + g];
-        if (fx) q.V0 = -q.V0;
-        if (fy) q.V1 = -q.V1;
-        q.e = T(0);
-        q.d0 = T(0);
-        q.d1 = Sr[kS64Mass * n + g];
-        q.d2 = Sr[(kS64Mass + 1) * n + g];
-        q.phi = Sr[kS64Phi * n + g];
-        equil_split(q);
-      }
-    }
-    if (!from_rec) {
+    {
       T rho = ld<T>(a.in[0], g);
       T mx = ld<T>(a.in[1], g);
       T my = (DIM == 2) ? ld<T>(a.in[2], g) : T(0);
@@ -753,94 +803,7 @@ __global__ void __launch_bounds__(NT, (step_min_blocks<T, DIM>()))
   }
 
   // ---- 3. write, reach of the new state, FP64 totals ----
-  int my_reach = 0;
-  if (valid) {
-    const long long o = (long long)dy * a.nx + dx;
-    reinterpret_cast<T*>(a.out[0])[o] = tot[0];
-    reinterpret_cast<T*>(a.out[1])[o] = tot[1];
-    if (DIM == 2) reinterpret_cast<T*>(a.out[2])[o] = tot[2];
-    reinterpret_cast<T*>(a.out[3])[o] = tot[3];
-    my_reach = reach_bound((double)tot[0], (double)tot[1],
-                           DIM == 2 ? (double)tot[2] : 0.0, (double)tot[3],
-                           (float)a.k.kreach);
-  }
-  const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1)
-    my_reach = max(my_reach, __shfl_xor_sync(0xffffffffu, my_reach, off));
-  double ps[4] = {0.0, 0.0, 0.0, 0.0};
-  if (a.do_cons) {
-    if (valid) {
-#pragma unroll
-      for (int f = 0; f < 4; ++f) ps[f] = (double)tot[f];
-    }
-#pragma unroll
-    for (int f = 0; f < 4; ++f)
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1)
-        ps[f] += __shfl_down_sync(0xffffffffu, ps[f], off);
-  }
-  if (lane == 0) {
-    red_reach[warp] = my_reach;
-#pragma unroll
-    for (int f = 0; f < 4; ++f) red_sum[f][warp] = ps[f];
-  }
-  __syncthreads();
-  const int nblk = a.nblocks;
-  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-  if (tid == 0) {
-    int rb = red_reach[0];
-    double bs[4] = {red_sum[0][0], red_sum[1][0], red_sum[2][0], red_sum[3][0]};
-    for (int w = 1; w < NT / 32; ++w) {
-      rb = max(rb, red_reach[w]);
-#pragma unroll
-      for (int f = 0; f < 4; ++f) bs[f] += red_sum[f][w];
-    }
-    atomicMax(&a.scr->reach_next, rb);
-    if (a.do_cons) {
-#pragma unroll
-      for (int f = 0; f < 4; ++f) a.part[(long long)bid * 4 + f] = bs[f];
-    }
-    __threadfence();
-    unsigned done = atomicAdd(&a.scr->ticket, 1u);
-    is_last = (done == (unsigned)(nblk - 1));
-  }
-  __syncthreads();
-  if (!is_last) return;
-
-  // ---- last block: publish reach and totals (fixed order) ----
-  __threadfence();
-  if (a.do_cons) {
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = tid; b < nblk; b += NT) {
-#pragma unroll
-      for (int f = 0; f < 4; ++f) s[f] += __ldcg(&a.part[(long long)b * 4 + f]);
-    }
-#pragma unroll
-    for (int f = 0; f < 4; ++f)
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1)
-        s[f] += __shfl_down_sync(0xffffffffu, s[f], off);
-    if (lane == 0) {
-#pragma unroll
-      for (int f = 0; f < 4; ++f) red_sum[f][warp] = s[f];
-    }
-    __syncthreads();
-    if (tid == 0) {
-      for (int f = 0; f < 4; ++f) {
-        double t = red_sum[f][0];
-        for (int w = 1; w < NT / 32; ++w) t += red_sum[f][w];
-        a.scr->cons[f] = t;
-      }
-    }
-  }
-  if (tid == 0) {
-    int rn = atomicAdd(&a.scr->reach_next, 0);
-    a.scr->reach = rn;
-    a.scr->reach_next = 0;
-    a.scr->ticket = 0u;
-    __threadfence();
-  }
+  step_finish<T, DIM, NT>(a, valid, dx, dy, tot);
 }
 
 template <typename T, int DIM, int TXW = TileShape<DIM>::TX>
