@@ -396,50 +396,96 @@ struct RowLandingList {
 
 // Landings I .. E-1 of one row into the row sums r (the scan's expressions:
 // corner weight (eq 29) times the packet's mass, momentum and energy).
-// srow: the slot of the row's source at a_x = 0.
-template <typename T, class LL, int I, int E, typename Lay, typename Idx>
+// srow: the slot of the row's source at a_x = 0.  ASSIGN: the first landing
+// of the row sets r instead of adding to a zero.
+template <typename T, class LL, int I, int E, bool ASSIGN, typename Lay,
+          typename Idx>
 __device__ __forceinline__ void row_range(const Lay& L, Idx srow, T (&r)[4]) {
   if constexpr (I < E) {
     constexpr LL ll{};
     constexpr RowLanding q = ll.v[I];
+    constexpr bool first = I == 0 || ll.v[I - 1].j != q.j ||
+                           ll.v[I - 1].side != q.side;
     const Idx s = srow + q.ax;
     const T al = L.wt[q.k * L.cap + s];
-    r[0] = r[0] + al * L.mass[(q.p >> 2) * L.cap + s];
-    r[1] = r[1] + al * L.Px[q.p * L.cap + s];
-    r[2] = r[2] + al * L.Py[q.p * L.cap + s];
-    r[3] = r[3] + al * L.PE[q.p * L.cap + s];
-    row_range<T, LL, I + 1, E>(L, srow, r);
+    const T m = L.mass[(q.p >> 2) * L.cap + s];
+    const T px = L.Px[q.p * L.cap + s];
+    const T py = L.Py[q.p * L.cap + s];
+    const T pe = L.PE[q.p * L.cap + s];
+    if constexpr (ASSIGN && first) {
+      r[0] = al * m;
+      r[1] = al * px;
+      r[2] = al * py;
+      r[3] = al * pe;
+    } else {
+      r[0] = r[0] + al * m;
+      r[1] = r[1] + al * px;
+      r[2] = r[2] + al * py;
+      r[3] = r[3] + al * pe;
+    }
+    row_range<T, LL, I + 1, E, ASSIGN>(L, srow, r);
   }
 }
 
 // Rows J .. jmax of a uniform window; s0: the destination's slot, W: the
 // distance between the slots of vertically adjacent sources.
+//
+// Compensated (KAHAN): the scan's sums operation for operation.  Plain: a
+// row sum starts from its first term instead of zero, a row without
+// landings adds nothing, and rows beyond jmax are not visited.  That can
+// only change the sign of a zero row or pair sum, and the destination's
+// total, which starts at +0 and is never -0 under round-to-nearest,
+// absorbs it: total + (+0) and total + (-0) are the same number.  So the
+// totals stay bit-identical with the scan's.
 template <typename T, bool KAHAN, class LL, int J, typename Lay, typename Idx>
 __device__ __forceinline__ void uniform_rows(const Lay& L, Idx s0, Idx W,
                                              T (&tot)[4], T (&comp)[4]) {
   constexpr LL ll{};
   if constexpr (J <= ll.jmax()) {
-    T pair[4];
-    {
-      T r[4] = {T(0), T(0), T(0), T(0)};
-      row_range<T, LL, ll.begin(J, 0), ll.end(J, 0)>(L, s0 - J * W, r);
+    constexpr int b0 = ll.begin(J, 0), e0 = ll.end(J, 0);
+    constexpr int b1 = J > 0 ? ll.begin(J, 1) : 0, e1 = J > 0 ? ll.end(J, 1) : 0;
+    if constexpr (KAHAN) {
+      T pair[4];
+      {
+        T r[4] = {T(0), T(0), T(0), T(0)};
+        row_range<T, LL, b0, e0, false>(L, s0 - J * W, r);
 #pragma unroll
-      for (int f = 0; f < 4; ++f) pair[f] = r[f];
-    }
-    if constexpr (J > 0) {
-      T r[4] = {T(0), T(0), T(0), T(0)};
-      row_range<T, LL, ll.begin(J, 1), ll.end(J, 1)>(L, s0 + J * W, r);
+        for (int f = 0; f < 4; ++f) pair[f] = r[f];
+      }
+      if constexpr (J > 0) {
+        T r[4] = {T(0), T(0), T(0), T(0)};
+        row_range<T, LL, b1, e1, false>(L, s0 + J * W, r);
 #pragma unroll
-      for (int f = 0; f < 4; ++f) pair[f] = pair[f] + r[f];
+        for (int f = 0; f < 4; ++f) pair[f] = pair[f] + r[f];
+      }
+      add_pair<T, KAHAN>(tot, comp, pair);
+    } else {
+      constexpr bool has0 = b0 < e0, has1 = b1 < e1;
+      if constexpr (has0 || has1) {
+        T pair[4];
+        if constexpr (has0) row_range<T, LL, b0, e0, true>(L, s0 - J * W, pair);
+        if constexpr (has1) {
+          T r[4];
+          row_range<T, LL, b1, e1, true>(L, s0 + J * W, r);
+#pragma unroll
+          for (int f = 0; f < 4; ++f) {
+            if constexpr (has0)
+              pair[f] = pair[f] + r[f];
+            else
+              pair[f] = r[f];
+          }
+        }
+        add_pair<T, KAHAN>(tot, comp, pair);
+      }
     }
-    add_pair<T, KAHAN>(tot, comp, pair);
     uniform_rows<T, KAHAN, LL, J + 1>(L, s0, W, tot, comp);
   }
 }
 
-// A uniform window's gather: the compile-time rows, then rows jmax+1 .. R,
-// which hold no landing (their pair sums are zero, added as the scan adds
-// them).
+// A uniform window's gather: the compile-time rows, then (compensated sums
+// only) rows jmax+1 .. R, which hold no landing: their pair sums are zero,
+// added as the scan adds them, because the compensation term makes such an
+// addition change the total.
 template <typename T, bool KAHAN, int C1, int NX, int NY, typename Lay,
           typename Idx>
 __device__ __forceinline__ void uniform_gather(const Lay& L, Idx s0, Idx W,
@@ -447,11 +493,13 @@ __device__ __forceinline__ void uniform_gather(const Lay& L, Idx s0, Idx W,
                                                T (&comp)[4]) {
   using LL = RowLandingList<C1, NX, NY>;
   uniform_rows<T, KAHAN, LL, 0>(L, s0, W, tot, comp);
-  for (int j = LL{}.jmax() + 1; j <= R; ++j) {
-    T pair[4] = {T(0), T(0), T(0), T(0)};
+  if constexpr (KAHAN) {
+    for (int j = LL{}.jmax() + 1; j <= R; ++j) {
+      T pair[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-    for (int f = 0; f < 4; ++f) pair[f] = pair[f] + T(0);
-    add_pair<T, KAHAN>(tot, comp, pair);
+      for (int f = 0; f < 4; ++f) pair[f] = pair[f] + T(0);
+      add_pair<T, KAHAN>(tot, comp, pair);
+    }
   }
 }
 

@@ -63,6 +63,9 @@ def _assert_bitwise(g, o, dim):
             continue
         assert np.array_equal(g[f], o[f]), (
             f, np.max(np.abs(g[f] - o[f])), np.argmax(np.abs(g[f] - o[f])))
+        # the same bits, signs of zeros included
+        assert np.array_equal(np.asarray(g[f], np.float64).view(np.uint64),
+                              np.asarray(o[f], np.float64).view(np.uint64)), f
     np.testing.assert_allclose(g["p"], o["p"], rtol=1e-12,
                                atol=1e-12 * np.max(np.abs(o["p"])))
 
