@@ -135,10 +135,20 @@ struct Equil {
   int c1, n0, n1;
 };
 
-__device__ __forceinline__ float dev_sqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double dev_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float dev_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double dev_floor(double x) { return floor(x); }
+
+// Estimate of floor(sqrt(X)) for 0 <= X <= 2^40, within one of the exact
+// value: X rounded to FP32 and its correctly rounded FP32 square root are
+// within 1.5 * 2^-24 sqrt(X) of sqrt(X), less than 0.1 for X <= 2^40.  (The
+// FP64 square root would take a long chain of FP64 operations for the same
+// integer.)
+__device__ __forceinline__ int isqrt_estimate(double X) {
+  return (int)floorf(sqrtf((float)X));
+}
+__device__ __forceinline__ int isqrt_estimate(float X) {
+  return (int)floorf(sqrtf(X));
+}
 
 // Lattice shift n = floor(V) and split fraction f = V - n per axis (eqs
 // 23, 28, 29).
@@ -186,9 +196,9 @@ __device__ __forceinline__ Equil<T> equilibrium(T rho, T mx, T my, T rhoE,
     q.bad = true;
     return q;
   }
-  // floor(sqrt(X)) of a correctly rounded sqrt is within one of the exact
-  // integer root, so one fix-up each way settles c1^2 <= X < (c1+1)^2
-  int c1 = (int)dev_floor(dev_sqrt(X));
+  // c1 is the integer floor(sqrt(X)), fixed by c1^2 <= X < (c1+1)^2: an
+  // estimate within one of it and one exact fix-up each way give it
+  int c1 = isqrt_estimate(X);
   if ((T)((long long)(c1 + 1) * (c1 + 1)) <= X) ++c1;
   if (c1 > 0 && (T)((long long)c1 * c1) > X) --c1;
   q.c1 = c1;
