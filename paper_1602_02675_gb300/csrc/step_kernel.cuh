@@ -6,9 +6,7 @@
 //     migration reach R of the tile once (Section III.B eqs 13-15, 24-26;
 //     packets eqs 11-14, 21; split weights eq 23, 28, 29) and keeps them in
 //     shared memory; sources beyond the domain edge are the additional points
-//     of Section V.B (zero-gradient, periodic image or mirror image).  FP64
-//     on the square lattice copies them from the source records a separate
-//     pass wrote for every node (the same arithmetic, once per node);
+//     of Section V.B (zero-gradient, periodic image or mirror image);
 //  2. lets each thread gather the arrivals at its destination (eqs 6, 10,
 //     22): source rows at distance j below and above the destination are
 //     summed row by row (ascending x, packet table order, corner order) and
@@ -19,6 +17,11 @@
 //  3. writes the new moments, reduces a conservative reach for the next step
 //     and, when asked, FP64 totals; the last block to finish publishes them.
 // No floating-point atomics anywhere; every sum has a fixed order.
+//
+// An FP64 square-lattice handle steps with step2d_f64 (step_f64.cu)
+// instead: the same gather and sums, reading packets that a records pass
+// formed once per node; this kernel serves that case for
+// lbm_step_noalloc, which has no room for the records.
 #pragma once
 
 #include <cstdint>
