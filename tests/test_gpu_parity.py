@@ -137,6 +137,21 @@ def test_one_type_windows_fp64_bitwise(bcs, bands, p_over_rho):
     _assert_bitwise(g, o, 2)
 
 
+@pytest.mark.parametrize("max_reach", [0, 4])
+def test_closed_box_fp64_bitwise(max_reach):
+    """Reflecting walls on all four sides (mirror images at the corners),
+    with the default reach limit and a smaller one (the FP64 source
+    records are padded by the limit)."""
+    nx, ny = 70, 37
+    prims = I.banded_prims(nx, ny, seed=3300, u_band=(0.1, 0.8),
+                           v_band=(-0.8, -0.1), p_over_rho=1.0)
+    g = _gpu(2, nx, ny, L.REFLECTING, L.REFLECTING, prims=prims, steps=6,
+             max_reach=max_reach)
+    o = _oracle(2, nx, ny, O.REFLECTING, O.REFLECTING, prims=prims, steps=6)
+    _assert_bitwise(g, o, 2)
+    assert g["diag"]["flags"] == 0
+
+
 def test_sod_2d_paper_lattice_fp64_bitwise():
     """The paper's 400 x 4 square lattice (Section V.C) with x-only data."""
     lam = 1.0
