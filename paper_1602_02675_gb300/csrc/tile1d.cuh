@@ -293,11 +293,19 @@ __device__ void tile1d_step(const T* __restrict__ in0,
       my_reach = reach_bound((double)r, (double)x, 0.0, (double)e,
                              (float)k.kreach);
   }
+  // the item's reach: one atomic per item rather than one per warp (all
+  // items of a tube update the same word)
+  __shared__ int red_r[TW / 32];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1)
     my_reach = max(my_reach, __shfl_xor_sync(0xffffffffu, my_reach, off));
-  if ((tid & 31) == 0 && my_reach > 0) atomicMax(reach_next, my_reach);
+  if ((tid & 31) == 0) red_r[tid >> 5] = my_reach;
   __syncthreads();  // shared records are reused by the next item
+  if (tid == 0) {
+    int m = red_r[0];
+    for (int w = 1; w < TW / 32; ++w) m = max(m, red_r[w]);
+    if (m > 0) atomicMax(reach_next, m);
+  }
 }
 
 
