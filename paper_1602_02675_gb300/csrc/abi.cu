@@ -34,7 +34,7 @@ struct lbm_handle {
   TmaMap rec_map[2][2];   // TMA tensor maps of rec[b][0], rec[b][1]
   // FP64 square lattice: source records of the state being stepped,
   // rewritten before every step.
-  double* src64 = nullptr;
+  void* src = nullptr;
   Scratch* scr = nullptr;
   double* part = nullptr;
   int part_cap = 0;
@@ -215,8 +215,8 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
       h->use_rec = false;
     }
   }
-  if (ok && h->f64 && c.dim == 2)
-    ok = cudaMalloc(&h->src64, src64_bytes(h->nx, h->ny, h->r_cap)) ==
+  if (ok && c.dim == 2 && h->f64)
+    ok = cudaMalloc(&h->src, src_bytes(h->nx, h->ny, h->r_cap, esize(h))) ==
          cudaSuccess;
   ok = ok && cudaMalloc(&h->scr, sizeof(Scratch)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->part, sizeof(double) * 4 * (size_t)h->part_cap) ==
@@ -342,7 +342,7 @@ lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
   a.k = h->k;
   a.scr = h->scr;
   a.part = h->part;
-  a.src64 = h->src64;
+  a.src = h->src;
   for (int64_t s = 0; s < nsteps; ++s) {
     for (int f = 0; f < 4; ++f) {
       a.in[f] = h->buf[h->cur][f];
@@ -471,7 +471,7 @@ void lbm_destroy(lbm_handle* h) {
   for (int b = 0; b < 2; ++b)
     for (int f = 0; f < 2; ++f)
       if (h->rec[b][f]) cudaFree(h->rec[b][f]);
-  if (h->src64) cudaFree(h->src64);
+  if (h->src) cudaFree(h->src);
   if (h->scr) cudaFree(h->scr);
   if (h->part) cudaFree(h->part);
   if (h->staging) cudaFree(h->staging);

@@ -62,16 +62,17 @@ struct StepArgs {
   // Tiles resident at once (set by the launcher): a block prefetches into
   // L2 the input records of the tile that many launches ahead.
   int prefetch_ahead = 0;
-  // FP64 square lattice only: source records of the input state over the
-  // grid padded by r_cap, written by the launcher's records pass before
-  // each step (layout in step_kernel.cuh), or null.
-  double* src64 = nullptr;
+  // FP64 square lattice: source records of the input state over the grid
+  // padded by r_cap (layout in step_kernel.cuh), written by the launcher's
+  // records pass before each step, or null.
+  void* src = nullptr;
 };
 
-// Bytes of the FP64 square-lattice source records of an nx x ny grid with
-// reach limit r_cap: 31 x 8 bytes per padded node.
-inline size_t src64_bytes(int nx, int ny, int r_cap) {
-  return (size_t)(nx + 2 * r_cap) * (size_t)(ny + 2 * r_cap) * 31 * 8;
+// Bytes of the square-lattice source records of an nx x ny grid with reach
+// limit r_cap and elements of esize bytes: 30 fields of esize bytes and one
+// 8-byte word per padded node.
+inline size_t src_bytes(int nx, int ny, int r_cap, size_t esize) {
+  return (size_t)(nx + 2 * r_cap) * (size_t)(ny + 2 * r_cap) * (30 * esize + 8);
 }
 
 // Launch helpers (step kernels).

@@ -18,10 +18,10 @@
 //     and, when asked, FP64 totals; the last block to finish publishes them.
 // No floating-point atomics anywhere; every sum has a fixed order.
 //
-// An FP64 square-lattice handle steps with step2d_f64 (step_f64.cu)
-// instead: the same gather and sums, reading packets that a records pass
-// formed once per node; this kernel serves that case for
-// lbm_step_noalloc, which has no room for the records.
+// FP64 square-lattice handles step with step2d_rec (step_rec.cuh) instead:
+// the same gather and sums, reading packets that a records pass formed once
+// per source; this kernel serves that case for lbm_step_noalloc, which has
+// no room for the records.
 #pragma once
 
 #include <cstdint>
@@ -268,22 +268,22 @@ __device__ __forceinline__ void packet_fields(const Equil<T>& q, int p,
   }
 }
 
-// FP64 square-lattice source records, written for every node and every
-// additional point before each step (records2d_f64) and read by the step's
-// gather instead of forming each window source's equilibrium again.
+// Square-lattice source records (step_rec.cuh), written for every node and
+// every additional point before each step by a records pass and read by the
+// step's gather instead of forming each window source's equilibrium again.
 // Structure of arrays over the grid padded by r_cap on every side (source
-// (x, y) at (y + r_cap) * (nx + 2 r_cap) + x + r_cap), one double per
-// source each: P_x of packets 0-7, P_y of 0-7, P_E of 0-7, d1, d2, the four
-// corner weights, then one array of 64-bit words holding c1, n_x, n_y as
-// 16-bit fields (c1 = -1: the source emits nothing).
+// (x, y) at (y + r_cap) * (nx + 2 r_cap) + x + r_cap), one element of the
+// step's type per source each: P_x of packets 0-7, P_y of 0-7, P_E of 0-7,
+// d1, d2, the four corner weights, then one array of 64-bit words holding
+// c1, n_x, n_y as 16-bit fields (c1 = -1: the source emits nothing).
 enum : int {
-  kS64Px = 0,
-  kS64Py = 8,
-  kS64PE = 16,
-  kS64Mass = 24,
-  kS64W = 26,
-  kS64Word = 30,
-  kS64Arrays = 31
+  kRecPx = 0,
+  kRecPy = 8,
+  kRecPE = 16,
+  kRecMass = 24,
+  kRecW = 26,
+  kRecWord = 30,
+  kRecArrays = 31
 };
 
 // Corner weights of a square-lattice source (eq 29), in corner order
