@@ -257,6 +257,62 @@ def test_sod_2d_full_size_rows_match_oracle():
             _assert_l1(row, o, 2)
 
 
+def _cylinder_patch_oracle(N, ix, iy, h, steps, cx=0.5, cy=0.5, r=0.4):
+    """The oracle's value at node (ix, iy) of the N x N periodic cylinder
+    after `steps` steps, from a (2h+1)^2 patch around it (periodic wrap of
+    the indices).  The node's arrivals come from sources within the reach,
+    in an order fixed relative to the node, so with h at least (steps + 1)
+    reaches the patch's own (transmissive) edges cannot reach the centre
+    and the value equals the full grid's."""
+    dx = 1.0 / N
+    x = O.node_x(N, 0.0, 1.0)
+    y = 0.0 + (np.arange(N) + 0.5) * dx
+    jx = np.take(np.arange(N), np.arange(ix - h, ix + h + 1), mode="wrap")
+    jy = np.take(np.arange(N), np.arange(iy - h, iy + h + 1), mode="wrap")
+    X, Y = np.meshgrid(x[jx], y[jy])
+    r2 = (X - cx) * (X - cx) + (Y - cy) * (Y - cy)
+    w = 2 * h + 1
+    P = O.Params(dim=2, nx=w, ny=w, bc_x=O.TRANSMISSIVE, bc_y=O.TRANSMISSIVE)
+    st = O._assign(P, (r2 < r * r).ravel(), (1.0, 0.0, 0.0, 1.0),
+                   (0.125, 0.0, 0.0, 0.1), 1.0)
+    st2, _ = O.run(P, st, steps)
+    ph = O.lattice_to_physical(1.4, 1.0, st2)
+    c = h * w + h
+    return {f: ph[f][c] for f in FIELDS}
+
+
+def test_cylinder_full_size_sampled_outputs():
+    """The 8192^2 periodic cylinder at full size, two steps: sampled nodes
+    (the centre, the circle's edge, the periodic corners, seeded others)
+    against the oracle run on a patch around each.  FP64 bit for bit; the
+    FP32 register kernel and the compensated FP32 kernel within 1e-5 of the
+    field's range."""
+    N, steps, h = 8192, 2, 24
+    rng = np.random.default_rng(20263)
+    edge = int(round((0.5 + 0.4) * N - 0.5))
+    picks = [(N // 2, N // 2), (edge, N // 2), (N // 2, edge), (0, 0),
+             (N - 1, N - 1), (0, N - 1)]
+    picks += [tuple(int(v) for v in rng.integers(0, N, 2)) for _ in range(10)]
+    ref = {(ix, iy): _cylinder_patch_oracle(N, ix, iy, h, steps)
+           for ix, iy in picks}
+    riem = ((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1), 1, 0.5, 0.5, 0.4)
+    # field ranges after two steps (oracle, 512^2 and 96^2 alike)
+    span = {"rho": 0.875, "mx": 0.777, "my": 0.777, "rhoE": 2.25}
+    for prec, kahan in ((L.F64, 1), (L.F32, 0), (L.F32, 1)):
+        g = _gpu(2, N, N, L.PERIODIC, L.PERIODIC, riemann=riem, steps=steps,
+                 precision=prec, kahan=kahan)
+        assert g["diag"]["flags"] == 0
+        for (ix, iy), o in ref.items():
+            k = iy * N + ix
+            for f in FIELDS:
+                if prec == L.F64:
+                    assert g[f][k] == o[f], (prec, ix, iy, f, g[f][k], o[f])
+                else:
+                    assert abs(g[f][k] - o[f]) <= 1e-5 * span[f], (
+                        prec, kahan, ix, iy, f, g[f][k], o[f])
+        del g
+
+
 def test_conservation_periodic_gpu():
     nx, ny = 96, 40
     prims = I.random_smooth_prims(2, nx, ny, seed=44, jump=False)
