@@ -81,6 +81,32 @@ def test_batch_matches_oracle_per_tube(precision):
             assert np.all(np.abs(tot[j] - want) <= tol * scale), (j, tot[j], want)
 
 
+def test_full_batch_sampled_tubes_fp32():
+    """The benchmark's batch at full size (4096 seeded tubes of 256..16384
+    nodes, FP32 with compensated sums, the tuned tile): the six tubes the
+    oracle runs fastest, checked against the oracle run of each alone."""
+    specs = []
+    for t in I.tubes_batch(4096):
+        nsteps, lam = t.steps_and_lambda(0.2)
+        specs.append((t, nsteps, (lam / t.n) * t.n))
+    cheap = sorted(range(len(specs)),
+                   key=lambda j: specs[j][0].n * specs[j][1])[:6]
+    with _make(specs, L.F32, kahan=1) as b:
+        b.run()
+        b.sync()
+        assert b.tuning()["tile"] in (128, 256, 512)
+        got = {j: b.moments(j) for j in cheap}
+    for j in cheap:
+        t, ns, lam = specs[j]
+        o, _ = _oracle_tube(t, ns, lam)
+        for f in ("rho", "mx", "rhoE"):
+            rng = o[f].max() - o[f].min()
+            err = np.mean(np.abs(got[j][f] - o[f])) / rng
+            if err > 1e-5:
+                floor = _oracle_fp32_storage_error(t, ns, lam)[f]
+                assert err <= 4.0 * floor, (j, f, err, floor)
+
+
 @pytest.mark.parametrize("precision", [L.F32, L.F64])
 def test_tube_alone_equals_tube_in_the_mix(precision):
     specs = _tubes(16, seed=5)
