@@ -26,6 +26,7 @@
 
 #include <cstdint>
 
+#include "fp32_arith.cuh"
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -533,6 +534,21 @@ __device__ __forceinline__ T ld(const void* p, long long i) {
   return reinterpret_cast<const T*>(p)[i];
 }
 
+// Warp 0 of a block: lane 8 f + w takes warp w's compensated partial of
+// field f (NW <= 8 warps, the rest zero) and the xor 4, 2, 1 exchanges
+// combine them in a fixed pairing; lanes 8 f return field f.
+template <int NW>
+__device__ __forceinline__ Sum2 combine_warps_f2(const float2 (&red)[4][NW],
+                                                 int lane) {
+  static_assert(NW <= 8, "one lane per (field, warp)");
+  const int w = lane & 7;
+  const float2 h = w < NW ? red[lane >> 3][w] : make_float2(0.f, 0.f);
+  Sum2 b{h.x, h.y};
+#pragma unroll
+  for (int off = 4; off > 0; off >>= 1) b = sum2_add(b, sum2_shfl_xor(b, off));
+  return b;
+}
+
 // Step 3 of a step launch (all NT threads of the block call it): write the
 // destination's new moments (tot; valid: the thread has a destination at
 // (dx, dy)), reduce a conservative reach for the next step and, when asked,
@@ -543,6 +559,7 @@ __device__ __forceinline__ void step_finish(const StepArgs& a, bool valid,
                                             int dx, int dy,
                                             const T (&tot)[4]) {
   __shared__ double red_sum[4][NT / 32];
+  __shared__ float2 red_f2[4][NT / 32];
   __shared__ int red_reach[NT / 32];
   __shared__ int is_last;
   const int tid = threadIdx.x;
@@ -553,46 +570,81 @@ __device__ __forceinline__ void step_finish(const StepArgs& a, bool valid,
     reinterpret_cast<T*>(a.out[1])[o] = tot[1];
     if (DIM == 2) reinterpret_cast<T*>(a.out[2])[o] = tot[2];
     reinterpret_cast<T*>(a.out[3])[o] = tot[3];
-    my_reach = reach_bound((double)tot[0], (double)tot[1],
-                           DIM == 2 ? (double)tot[2] : 0.0, (double)tot[3],
-                           (float)a.k.kreach);
+    if constexpr (sizeof(T) == sizeof(float))
+      my_reach = reach_bound_f32(tot[0], tot[1], DIM == 2 ? tot[2] : 0.0f,
+                                 tot[3], (float)a.k.kreach);
+    else
+      my_reach = reach_bound((double)tot[0], (double)tot[1],
+                             DIM == 2 ? (double)tot[2] : 0.0, (double)tot[3],
+                             (float)a.k.kreach);
   }
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1)
     my_reach = max(my_reach, __shfl_xor_sync(0xffffffffu, my_reach, off));
-  double ps[4] = {0.0, 0.0, 0.0, 0.0};
   if (a.do_cons) {
-    if (valid) {
+    if constexpr (sizeof(T) == sizeof(float)) {
+      // FP32: compensated FP32 sums (the FP64 pipe is 1/64 of FP32 on this
+      // GPU), per warp here and over the warps below
+      Sum2 p4[4];
 #pragma unroll
-      for (int f = 0; f < 4; ++f) ps[f] = (double)tot[f];
+      for (int f = 0; f < 4; ++f) p4[f] = Sum2{valid ? (float)tot[f] : 0.0f, 0.0f};
+      const Sum2 k = warp_sum2_fields(p4, lane);
+      if ((lane & 7) == 0) red_f2[lane >> 3][warp] = make_float2(k.hi, k.lo);
+    } else {
+      double ps[4] = {0.0, 0.0, 0.0, 0.0};
+      if (valid) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) ps[f] = (double)tot[f];
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+          ps[f] += __shfl_down_sync(0xffffffffu, ps[f], off);
+      if (lane == 0) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) red_sum[f][warp] = ps[f];
+      }
     }
-#pragma unroll
-    for (int f = 0; f < 4; ++f)
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1)
-        ps[f] += __shfl_down_sync(0xffffffffu, ps[f], off);
   }
-  if (lane == 0) {
-    red_reach[warp] = my_reach;
-#pragma unroll
-    for (int f = 0; f < 4; ++f) red_sum[f][warp] = ps[f];
-  }
+  if (lane == 0) red_reach[warp] = my_reach;
   __syncthreads();
   const int nblk = a.nblocks;
   const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  double bs[4] = {0.0, 0.0, 0.0, 0.0};
+  float2 bf[4];  // FP32: the block's compensated partials (hi, lo)
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (warp == 0 && a.do_cons) {
+      const Sum2 b = combine_warps_f2<NT / 32>(red_f2, lane);
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        bf[f] = make_float2(__shfl_sync(0xffffffffu, b.hi, 8 * f),
+                            __shfl_sync(0xffffffffu, b.lo, 8 * f));
+    }
+  }
   if (tid == 0) {
     int rb = red_reach[0];
-    double bs[4] = {red_sum[0][0], red_sum[1][0], red_sum[2][0], red_sum[3][0]};
+    if constexpr (sizeof(T) != sizeof(float)) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) bs[f] = red_sum[f][0];
+    }
     for (int w = 1; w < NT / 32; ++w) {
       rb = max(rb, red_reach[w]);
+      if constexpr (sizeof(T) != sizeof(float)) {
 #pragma unroll
-      for (int f = 0; f < 4; ++f) bs[f] += red_sum[f][w];
+        for (int f = 0; f < 4; ++f) bs[f] += red_sum[f][w];
+      }
     }
     atomicMax(&a.scr->reach_next, rb);
     if (a.do_cons) {
 #pragma unroll
-      for (int f = 0; f < 4; ++f) a.part[(long long)bid * 4 + f] = bs[f];
+      for (int f = 0; f < 4; ++f) {
+        if constexpr (sizeof(T) == sizeof(float))
+          reinterpret_cast<float2*>(a.part)[(long long)bid * 4 + f] = bf[f];
+        else
+          a.part[(long long)bid * 4 + f] = bs[f];
+      }
     }
     __threadfence();
     unsigned done = atomicAdd(&a.scr->ticket, 1u);
@@ -603,7 +655,28 @@ __device__ __forceinline__ void step_finish(const StepArgs& a, bool valid,
 
   // ---- last block: publish reach and totals (fixed order) ----
   __threadfence();
-  if (a.do_cons) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (a.do_cons) {
+      // the blocks' (hi, lo) partials in compensated FP32 sums, each
+      // thread a fixed strided set, then the warps and the block as above
+      Sum2 s4[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+      for (int b = tid; b < nblk; b += NT) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const float2 v =
+              __ldcg(&reinterpret_cast<const float2*>(a.part)[(long long)b * 4 + f]);
+          s4[f] = sum2_add(s4[f], Sum2{v.x, v.y});
+        }
+      }
+      const Sum2 k = warp_sum2_fields(s4, lane);
+      if ((lane & 7) == 0) red_f2[lane >> 3][warp] = make_float2(k.hi, k.lo);
+      __syncthreads();
+      if (warp == 0) {
+        const Sum2 b = combine_warps_f2<NT / 32>(red_f2, lane);
+        if ((lane & 7) == 0) a.scr->cons[lane >> 3] = (double)b.hi + (double)b.lo;
+      }
+    }
+  } else if (a.do_cons) {
     double s[4] = {0.0, 0.0, 0.0, 0.0};
     for (int b = tid; b < nblk; b += NT) {
 #pragma unroll
