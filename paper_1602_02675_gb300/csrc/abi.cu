@@ -161,6 +161,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
   h->k.kphi = 1.0 - 0.5 * D * (c.gamma - 1.0);
   h->k.b1 = (c.dim == 1) ? 2.0 : 4.0;
   h->k.kreach = h->k.kq / (1.0 - h->k.theta);
+  h->k.set_fp32_copies();
   h->r_cap = c.max_reach > 0 ? c.max_reach : (c.dim == 1 ? 64 : 6);
   h->smem = step_smem_bytes(c.dim, h->f64, h->r_cap);
   int dev = 0;

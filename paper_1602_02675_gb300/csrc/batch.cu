@@ -468,6 +468,7 @@ lbm_status lbm_batch_create(int32_t precision, double gamma, double theta,
   b->k.kphi = 1.0 - 0.5 * 1.0 * (gamma - 1.0);
   b->k.b1 = 2.0;
   b->k.kreach = b->k.kq / (1.0 - theta);
+  b->k.set_fp32_copies();
   b->smem = step_smem_bytes(1, b->f64, b->r_cap);
 
   // sort by decreasing step count (stable: ties keep the caller's order)

@@ -32,6 +32,17 @@ struct EqConst {
   double kphi;   // 1 - D/2 (gamma - 1)     (eq 15)
   double b1;     // directions per level: 2 (1-D), 4 (square lattice)
   double kreach; // D (gamma - 1) / (1 - b0 theta): X = kreach * e
+  // the same constants rounded to FP32 once on the host (set_fp32_copies),
+  // so that FP32 kernels convert nothing on the GPU's slow FP64 pipe
+  float theta_f, kq_f, kphi_f, b1_f, kreach_f;
+
+  void set_fp32_copies() {
+    theta_f = (float)theta;
+    kq_f = (float)kq;
+    kphi_f = (float)kphi;
+    b1_f = (float)b1;
+    kreach_f = (float)kreach;
+  }
 };
 
 struct StepArgs {

@@ -143,6 +143,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_noalloc_desc* d,
   k.kphi = 1.0 - 0.5 * D * (d->gamma - 1.0);
   k.b1 = d->dim == 1 ? 2.0 : 4.0;
   k.kreach = k.kq / (1.0 - k.theta);
+  k.set_fp32_copies();
 
   // the array keeps the previous call's contents: start from zero
   e = cudaMemsetAsync(scr, 0, kHeader, s);

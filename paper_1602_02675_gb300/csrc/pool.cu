@@ -231,6 +231,7 @@ lbm_status lbm_pool_create(int32_t precision, double gamma, double theta,
   p->k.kphi = 1.0 - 0.5 * (gamma - 1.0);
   p->k.b1 = 2.0;
   p->k.kreach = p->k.kq / (1.0 - theta);
+  p->k.set_fp32_copies();
   p->capacity = capacity_nodes;
   p->max_slots = max_slots;
   p->smem = step_smem_bytes(1, p->f64, p->r_cap);

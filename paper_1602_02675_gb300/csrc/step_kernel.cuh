@@ -142,6 +142,20 @@ struct Equil {
 __device__ __forceinline__ float dev_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double dev_floor(double x) { return floor(x); }
 
+// A constant of the equilibrium in the step's type: FP64 kernels take the
+// double, FP32 kernels the copy rounded to FP32 on the host (the same value
+// a conversion on the GPU gives).
+template <typename T>
+__device__ __forceinline__ T eq_const(double d, float f);
+template <>
+__device__ __forceinline__ double eq_const<double>(double d, float) {
+  return d;
+}
+template <>
+__device__ __forceinline__ float eq_const<float>(double, float f) {
+  return f;
+}
+
 // Estimate of floor(sqrt(X)) for 0 <= X <= 2^40, within one of the exact
 // value: X rounded to FP32 and its correctly rounded FP32 square root are
 // within 1.5 * 2^-24 sqrt(X) of sqrt(X), less than 0.1 for X <= 2^40.  (The
@@ -191,9 +205,9 @@ __device__ __forceinline__ Equil<T> equilibrium(T rho, T mx, T my, T rhoE,
     q.clamp = true;
   }
   q.e = e;
-  T d0 = (DIM == 1) ? T(k.theta) * rho : T(0);
+  T d0 = (DIM == 1) ? eq_const<T>(k.theta, k.theta_f) * rho : T(0);
   T rho_p = rho - T(1) * d0;
-  T Q = T(k.kq) * rho * e;
+  T Q = eq_const<T>(k.kq, k.kq_f) * rho * e;
   T X = Q / rho_p;
   // X beyond 2^40 would mean c1 > 2^20: far past any supported reach
   if (!isfinite(X) || !(X >= T(0)) || X > T(1099511627776.0)) {
@@ -208,7 +222,7 @@ __device__ __forceinline__ Equil<T> equilibrium(T rho, T mx, T my, T rhoE,
   q.c1 = c1;
   T c1sq = (T)(c1 * c1);
   T c2sq = (T)((c1 + 1) * (c1 + 1));
-  T den = T(k.b1) * (c2sq - c1sq);
+  T den = eq_const<T>(k.b1, k.b1_f) * (c2sq - c1sq);
   q.d0 = d0;
   q.d1 = (c2sq * rho_p - Q) / den;
   q.d2 = (Q - c1sq * rho_p) / den;
@@ -216,9 +230,9 @@ __device__ __forceinline__ Equil<T> equilibrium(T rho, T mx, T my, T rhoE,
     // eq 15 as e - (D/2)(gamma-1) e: the packets then carry exactly
     // rho e = rho phi + Q/2 up to unbiased rounding; with the FP32-rounded
     // constants kphi + kq/2 != 1 and every step would add a fixed bias
-    q.phi = e - T(0.5) * (T(k.kq) * e);
+    q.phi = e - T(0.5) * (eq_const<T>(k.kq, k.kq_f) * e);
   } else {
-    q.phi = T(k.kphi) * e;
+    q.phi = eq_const<T>(k.kphi, k.kphi_f) * e;
   }
   equil_split(q);
   q.emits = true;
@@ -572,7 +586,7 @@ __device__ __forceinline__ void step_finish(const StepArgs& a, bool valid,
     reinterpret_cast<T*>(a.out[3])[o] = tot[3];
     if constexpr (sizeof(T) == sizeof(float))
       my_reach = reach_bound_f32(tot[0], tot[1], DIM == 2 ? tot[2] : 0.0f,
-                                 tot[3], (float)a.k.kreach);
+                                 tot[3], a.k.kreach_f);
     else
       my_reach = reach_bound((double)tot[0], (double)tot[1],
                              DIM == 2 ? (double)tot[2] : 0.0, (double)tot[3],

@@ -36,7 +36,7 @@ __device__ __forceinline__ Equil<float> equilibrium_1d_f32(float rho, float mx,
   const float e_raw = rhoE * inv - 0.5f * (q.V0 * q.V0);
   const float e = fmaxf(e_raw, 0.0f);
   q.e = e;
-  const float X = (float)k.kreach * e;
+  const float X = k.kreach_f * e;
   const bool finite_in = fabsf(rho + mx + rhoE) <= 3.0e38f;
   q.bad = !finite_in || rho < 0.0f || (rho > 0.0f && rho < 1.17549435e-38f) ||
           !(X <= 1099511627776.0f);
@@ -47,11 +47,11 @@ __device__ __forceinline__ Equil<float> equilibrium_1d_f32(float rho, float mx,
   const float c2f = c1f + 1.0f;
   const float c1sq = c1f * c1f, c2sq = c2f * c2f;
   const float den = 2.0f * (c2sq - c1sq);
-  q.d0 = (float)k.theta * rho;
+  q.d0 = k.theta_f * rho;
   const float rho_p = rho - q.d0;
   q.d1 = div_markstein(rho_p * (c2sq - X), den, rcp_nr(den));
   q.d2 = 0.5f * rho_p - q.d1;
-  q.phi = e - 0.5f * ((float)k.kq * e);
+  q.phi = e - 0.5f * (k.kq_f * e);
   const float fl = floorf(q.V0);
   q.n0 = (int)fl;
   q.f0 = q.V0 - fl;
@@ -235,7 +235,7 @@ __device__ void tile1d_step(const T* __restrict__ in0,
     o1[o] = T(0) + x;
     o2[o] = T(0) + e;
     if constexpr (sizeof(T) == sizeof(float))
-      my_reach = reach_bound_f32(r, x, 0.0f, e, (float)k.kreach);
+      my_reach = reach_bound_f32(r, x, 0.0f, e, k.kreach_f);
     else
       my_reach = reach_bound((double)r, (double)x, 0.0, (double)e,
                              (float)k.kreach);
@@ -288,7 +288,7 @@ __device__ void tile1d_step(const T* __restrict__ in0,
     o1[o] = T(0) + x;
     o2[o] = T(0) + e;
     if constexpr (sizeof(T) == sizeof(float))
-      my_reach = reach_bound_f32(r, x, 0.0f, e, (float)k.kreach);
+      my_reach = reach_bound_f32(r, x, 0.0f, e, k.kreach_f);
     else
       my_reach = reach_bound((double)r, (double)x, 0.0, (double)e,
                              (float)k.kreach);
