@@ -329,6 +329,27 @@ def test_conservation_periodic_gpu():
         assert np.all(np.abs(t1 - t0) <= tol * scale), (prec, (t1 - t0) / scale)
 
 
+@pytest.mark.parametrize("n", [1000, 5000, 200000])
+def test_conservation_periodic_1d_gpu(n):
+    """Periodic 1-D tubes (16-, 32- and 256-node tiles): the device totals
+    of mass and energy do not drift, and equal the sums of the state read
+    back (FP32: compensated FP32 sums of the nodes; FP64: FP64 sums)."""
+    prims = I.random_smooth_prims(1, n, 1, seed=45 + n, jump=False)
+    for prec, tol, kahan in ((L.F64, 1e-13, 1), (L.F32, 1e-6, 1),
+                             (L.F32, 1e-6, 0)):
+        cfg = L.make_config(1, n, precision=prec, bc_x=L.PERIODIC, kahan=kahan)
+        with L.Solver(cfg) as s:
+            s.set_primitives(*prims)
+            t0 = s.conservation()
+            s.step(100)
+            t1 = s.conservation()
+            m = s.moments()
+        scale = np.array([t0[0], t0[0], 1.0, t0[3]])
+        assert np.all(np.abs(t1 - t0) <= tol * scale), (prec, (t1 - t0) / scale)
+        rel = 1e-12 if prec == L.F64 else 1e-9
+        assert abs(t1[0] - np.sum(m["rho"])) <= rel * t1[0], (prec, kahan)
+
+
 def test_restart_bitwise():
     """Checkpoint through lbm_moments / lbm_set_moments: n then m steps
     equal n + m steps (FP64, lambda = 1 so the unit conversion is exact)."""
