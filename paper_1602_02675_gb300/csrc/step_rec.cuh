@@ -6,8 +6,8 @@
 // are those of step_kernel.cuh, so the FP64 instance (built with
 // -fmad=false) is bit-identical with the oracle.  Used by FP64 handles; in
 // FP32 the records' traffic (30 fields per source written and read) costs
-// more than forming the equilibria in every tile (measured: 0.368 against
-// 0.331 ms per step on the 4096 x 512 tube with compensated sums).
+// more than forming the equilibria in every tile (measured 11 % slower on
+// the 4096 x 512 tube with compensated sums).
 #pragma once
 
 #include "step_kernel.cuh"
