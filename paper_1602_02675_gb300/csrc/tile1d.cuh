@@ -128,6 +128,40 @@ __device__ __forceinline__ void land1(const Lay& L, int base, T& r, T& x,
   }
 }
 
+// The same landing for FP32 with compensated sums, mass and momentum as one
+// pair in the packed FP32 instructions, each half rounding exactly as the
+// scalar form of the units that use it (built without contraction): y =
+// al m - c, t = s + y, c = (t - s) - y.
+template <int N, int C1, int I, typename Lay>
+__device__ __forceinline__ void land1_k2(const Lay& L, int base, float2& rx,
+                                         float& e, float2& crx, float& ce) {
+  constexpr Landings1<N, C1> list{};
+  constexpr Landing1 q = list.v[I];
+  constexpr int lev = q.p == 0 ? 0 : (q.p <= 2 ? 1 : 2);
+  const int s = base + q.delta;
+  const float fx0 = L.f0[s];
+  const float al = q.k == 0 ? 1.0f - fx0 : fx0;
+  const float2 a2 = make_float2(al, al);
+  const float2 v2 = make_float2(L.mass[lev * L.cap + s], L.Px[q.p * L.cap + s]);
+  const float2 y = __fadd2_rn(__fmul2_rn(a2, v2), make_float2(-crx.x, -crx.y));
+  const float2 t = __fadd2_rn(rx, y);
+  const float2 d = __fadd2_rn(t, make_float2(-rx.x, -rx.y));
+  crx = __fadd2_rn(d, make_float2(-y.x, -y.y));
+  rx = t;
+  const float ye = al * L.PE[q.p * L.cap + s] - ce;
+  const float te = e + ye;
+  ce = (te - e) - ye;
+  e = te;
+}
+
+template <int N, int C1, typename Lay, int... I>
+__device__ __forceinline__ void land1_k2_all(const Lay& L, int base,
+                                             float2& rx, float& e, float2& crx,
+                                             float& ce,
+                                             std::integer_sequence<int, I...>) {
+  (land1_k2<N, C1, I>(L, base, rx, e, crx, ce), ...);
+}
+
 template <typename T, bool KAHAN, int N, int C1, typename Lay, int... I>
 __device__ __forceinline__ void land1_all(const Lay& L, int base, T& r, T& x,
                                           T& e, T& cr, T& cx_, T& ce,
@@ -139,8 +173,18 @@ template <typename T, bool KAHAN, int N, int C1, typename Lay>
 __device__ __forceinline__ void fast_gather1(const Lay& L, int base, T& r,
                                              T& x, T& e, T& cr, T& cx_,
                                              T& ce) {
-  land1_all<T, KAHAN, N, C1>(L, base, r, x, e, cr, cx_, ce,
-                             std::make_integer_sequence<int, 10>{});
+  if constexpr (KAHAN && sizeof(T) == sizeof(float)) {
+    float2 rx = make_float2(r, x), crx = make_float2(cr, cx_);
+    land1_k2_all<N, C1>(L, base, rx, e, crx, ce,
+                        std::make_integer_sequence<int, 10>{});
+    r = rx.x;
+    x = rx.y;
+    cr = crx.x;
+    cx_ = crx.y;
+  } else {
+    land1_all<T, KAHAN, N, C1>(L, base, r, x, e, cr, cx_, ce,
+                               std::make_integer_sequence<int, 10>{});
+  }
 }
 
 template <typename T, bool KAHAN, int TW = kTile1d>
