@@ -40,6 +40,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -114,7 +115,8 @@ def steps_and_lambda(t_end, dx):
 class Clocks:
     def __init__(self, gpu_index: int):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(),
+                                 f"lbm_bench_clocks_{os.getpid()}.csv")
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -127,6 +129,11 @@ class Clocks:
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            try:
+                self.f.close()
+                os.remove(self.path)
+            except Exception:
+                pass
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -138,9 +145,14 @@ class Clocks:
             self.proc.kill()
         self.f.close()
         sm, smax, reasons = [], [], set()
+        lines = open(self.path).read().splitlines()
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
                  "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
