@@ -40,7 +40,6 @@ import math
 import os
 import statistics
 import subprocess
-import tempfile
 import sys
 import time
 
@@ -113,27 +112,31 @@ def steps_and_lambda(t_end, dx):
 # clocks sampled during the timed region
 # --------------------------------------------------------------------------
 class Clocks:
+    """nvidia-smi samples (every 20 ms) collected from its output pipe by a
+    reader thread while the timed region runs."""
+
     def __init__(self, gpu_index: int):
+        import threading
         self.proc = None
-        self.path = os.path.join(tempfile.gettempdir(),
-                                 f"lbm_bench_clocks_{os.getpid()}.csv")
+        self.lines = []
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
                  "--format=csv,noheader,nounits", "-lms", "20"],
-                stdout=self.f, stderr=subprocess.DEVNULL)
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
-            try:
-                self.f.close()
-                os.remove(self.path)
-            except Exception:
-                pass
+            return
+
+        def read():
+            for line in self.proc.stdout:
+                self.lines.append(line)
+
+        self.reader = threading.Thread(target=read, daemon=True)
+        self.reader.start()
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -143,16 +146,11 @@ class Clocks:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        self.f.close()
+        self.reader.join(timeout=5)
         sm, smax, reasons = [], [], set()
-        lines = open(self.path).read().splitlines()
-        try:
-            os.remove(self.path)
-        except OSError:
-            pass
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
                  "sw_power_cap"]
-        for line in lines:
+        for line in list(self.lines):
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
