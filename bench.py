@@ -292,6 +292,15 @@ def run_ours(args, rank, world):
         "fp64": {"value": v64, "unit": "node-updates/s", "steps": k64,
                  "ms_per_step": round(mean64, 5),
                  "hbm_frac": round((16 * 4 * N) / (mean64 / 1e3) / 1e9 / peak, 4),
+                 # FP64 on this GPU is bound by its FP64 pipe: the arrivals'
+                 # 256 flop per node update against the measured FP64 rate
+                 "roofline": ({"bound": "alu",
+                               "achieved": round(v64 * 256 / 1e12, 4),
+                               "peak": round(peak64 / 1e12, 4),
+                               "unit": "TFLOP/s",
+                               "frac": round(v64 * 256 / peak64, 4),
+                               "peak_kind": "measured (lbm_measure_fma_peak)"}
+                              if args.precision == "both" else None),
                  "parity": "bit-exact with the FP64 oracle (tests)"},
         "e2e": e2e,
         "roofline": roof,
