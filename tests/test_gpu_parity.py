@@ -137,6 +137,28 @@ def test_one_type_windows_fp64_bitwise(bcs, bands, p_over_rho):
     _assert_bitwise(g, o, 2)
 
 
+@pytest.mark.parametrize("bcs", [(L.PERIODIC, L.PERIODIC),
+                                 (L.TRANSMISSIVE, L.REFLECTING)])
+@pytest.mark.parametrize("bands,p_over_rho", [
+    (((1.1, 1.6), (-0.4, 0.4)), 3.0),    # n_x = 1, c1 = 2: reach 5
+    (((-1.6, -1.1), (1.1, 1.6)), 1.0)])  # n_x = -2, n_y = 1
+def test_fast_flow_parity(bcs, bands, p_over_rho):
+    """Lattice velocities beyond one node per step (shifts outside the
+    compile-time landing lists, reach up to 5 of the 6 the records and
+    windows hold): FP64 bit for bit, the FP32 kernels within 1e-5 of
+    range."""
+    nx, ny = 60, 36
+    prims = I.banded_prims(nx, ny, seed=3400, u_band=bands[0],
+                           v_band=bands[1], p_over_rho=p_over_rho)
+    o = _oracle(2, nx, ny, *bcs, prims=prims, steps=4)
+    g = _gpu(2, nx, ny, *bcs, prims=prims, steps=4)
+    _assert_bitwise(g, o, 2)
+    for kahan in (0, 1):
+        g = _gpu(2, nx, ny, *bcs, prims=prims, steps=4, precision=L.F32,
+                 kahan=kahan)
+        _assert_l1(g, o, 2)
+
+
 @pytest.mark.parametrize("max_reach", [0, 4])
 def test_closed_box_fp64_bitwise(max_reach):
     """Reflecting walls on all four sides (mirror images at the corners),
