@@ -90,7 +90,8 @@ typedef struct {
   double dt;          /* physical time step; lambda = dt/dx */
   int32_t max_reach;  /* largest migration reach R (lattice cells) a step
                          may meet; 0 picks the default (1-D 64, 2-D 6).
-                         Shared memory per block grows with it.  A step
+                         Shared memory per block grows with it (F64 2-D:
+                         the padding of the source records instead).  A step
                          that meets a larger R leaves the state untouched
                          and reports LBM_EREACH at the next waiting call. */
   int32_t kahan;      /* F32 only: 1 = compensated (Kahan) summation of

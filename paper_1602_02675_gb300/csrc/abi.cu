@@ -163,7 +163,9 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
   h->k.kreach = h->k.kq / (1.0 - h->k.theta);
   h->k.set_fp32_copies();
   h->r_cap = c.max_reach > 0 ? c.max_reach : (c.dim == 1 ? 64 : 6);
-  h->smem = step_smem_bytes(c.dim, h->f64, h->r_cap);
+  // the FP64 square-lattice step gathers from source records and needs no
+  // shared-memory window; every other step holds its window there
+  h->smem = (h->f64 && c.dim == 2) ? 0 : step_smem_bytes(c.dim, h->f64, h->r_cap);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   int optin = 0;

@@ -159,6 +159,22 @@ def test_fast_flow_parity(bcs, bands, p_over_rho):
         _assert_l1(g, o, 2)
 
 
+def test_fp32_reach_limit_beyond_register_window():
+    """max_reach 8 exceeds the register kernel's fixed window (reach 6), so
+    the FP32 handle without compensated sums steps with the exact-order
+    kernel instead; same results within the FP32 bar, and FP64 with the
+    same limit (records padded by 8) bit for bit."""
+    nx, ny = 70, 40
+    prims = I.random_smooth_prims(2, nx, ny, seed=3500)
+    bcs = (L.PERIODIC, L.REFLECTING)
+    o = _oracle(2, nx, ny, *bcs, prims=prims, steps=5)
+    g = _gpu(2, nx, ny, *bcs, prims=prims, steps=5, precision=L.F32,
+             kahan=0, max_reach=8)
+    _assert_l1(g, o, 2)
+    g = _gpu(2, nx, ny, *bcs, prims=prims, steps=5, max_reach=8)
+    _assert_bitwise(g, o, 2)
+
+
 @pytest.mark.parametrize("max_reach", [0, 4])
 def test_closed_box_fp64_bitwise(max_reach):
     """Reflecting walls on all four sides (mirror images at the corners),
