@@ -432,6 +432,34 @@ def test_errors_are_reported():
         assert e.value.status == L.EREACH
 
 
+@pytest.mark.parametrize("prec,kahan", [(L.F64, 1), (L.F32, 1), (L.F32, 0)])
+def test_errors_are_reported_2d(prec, kahan):
+    """Square lattice, every step path (FP64 records pass and gather, FP32
+    exact-order kernel, FP32 register kernel): a negative density is
+    LBM_ESTATE; a reach beyond max_reach is LBM_EREACH."""
+    n = 40
+    N = n * n
+    cfg = L.make_config(2, n, n, precision=prec, kahan=kahan,
+                        bc_x=L.PERIODIC, bc_y=L.PERIODIC)
+    with L.Solver(cfg) as s:
+        rho = np.ones(N)
+        rho[123] = -1.0
+        with pytest.raises(L.LbmError) as e:
+            s.set_primitives(rho, np.zeros(N), np.zeros(N), np.ones(N))
+            s.step(1)
+            s.moments()
+        assert e.value.status == L.ESTATE
+    # c1 = 1 at rest gives reach 3: a limit of 2 is exceeded
+    cfg = L.make_config(2, n, n, precision=prec, kahan=kahan,
+                        bc_x=L.PERIODIC, bc_y=L.PERIODIC, max_reach=2)
+    with L.Solver(cfg) as s:
+        s.set_primitives(np.ones(N), np.zeros(N), np.zeros(N), np.ones(N))
+        s.step(1)
+        with pytest.raises(L.LbmError) as e:
+            s.synchronize()
+        assert e.value.status == L.EREACH
+
+
 def test_uniform_state_stays_uniform_bitwise():
     n = 64
     for dim in (1, 2):
