@@ -175,6 +175,28 @@ def test_fp32_reach_limit_beyond_register_window():
     _assert_bitwise(g, o, 2)
 
 
+def test_vacuum_nodes_2d():
+    """Nodes with zero density emit nothing (they only receive): FP64 bit
+    for bit with the oracle, FP32 kernels within 1e-5 of range."""
+    nx, ny = 70, 33
+    rho, u, v, p = I.random_smooth_prims(2, nx, ny, seed=3600, jump=False)
+    rng = np.random.default_rng(3601)
+    empty = rng.choice(nx * ny, 60, replace=False)
+    rho = rho.copy()
+    p = p.copy()
+    rho[empty] = 0.0
+    p[empty] = 0.0
+    prims = (rho, u, v, p)
+    bcs = (L.TRANSMISSIVE, L.REFLECTING)
+    o = _oracle(2, nx, ny, *bcs, prims=prims, steps=3)
+    g = _gpu(2, nx, ny, *bcs, prims=prims, steps=3)
+    _assert_bitwise(g, o, 2)
+    for kahan in (0, 1):
+        g = _gpu(2, nx, ny, *bcs, prims=prims, steps=3, precision=L.F32,
+                 kahan=kahan)
+        _assert_l1(g, o, 2)
+
+
 @pytest.mark.parametrize("max_reach", [0, 4])
 def test_closed_box_fp64_bitwise(max_reach):
     """Reflecting walls on all four sides (mirror images at the corners),
