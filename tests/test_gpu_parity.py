@@ -238,6 +238,35 @@ def test_lambda_not_one_fp64_bitwise():
     _assert_bitwise(g, o, 1)
 
 
+TORO1 = ((1.0, 0.75, 1.0), (0.125, 0.0, 0.1), 0, 0.3, 0.5, 0.0)
+
+
+@pytest.mark.parametrize("riem", [SOD, TORO1])
+def test_lambda_half_fp64_bitwise(riem):
+    """lambda = 0.5 (the oracle's conversion is pinned there by the
+    conservation laws and the exact Riemann solution): a 1-D tube with a
+    moving left state, 160 steps, and the same jump on a 2-D lattice between
+    reflecting walls, through the GPU's own unit conversions."""
+    g = _gpu(1, 400, 1, L.TRANSMISSIVE, 0, riemann=riem, steps=160, lam=0.5)
+    o = _oracle(1, 400, 1, O.TRANSMISSIVE, 0, riemann=riem, steps=160,
+                lam=0.5)
+    _assert_bitwise(g, o, 1)
+    r2 = ((riem[0][0], riem[0][1], 0.0, riem[0][2]),
+          (riem[1][0], riem[1][1], 0.0, riem[1][2])) + riem[2:]
+    g = _gpu(2, 96, 6, L.TRANSMISSIVE, L.REFLECTING, riemann=r2, steps=40,
+             lam=0.5)
+    o = _oracle(2, 96, 6, O.TRANSMISSIVE, O.REFLECTING, riemann=r2, steps=40,
+                lam=0.5)
+    _assert_bitwise(g, o, 2)
+    prims = I.random_smooth_prims(2, 40, 24, seed=77)
+    for prec, kahan in ((L.F32, 0), (L.F32, 1)):
+        g = _gpu(2, 40, 24, L.PERIODIC, L.PERIODIC, prims=prims, steps=8,
+                 lam=0.5, precision=prec, kahan=kahan)
+        o = _oracle(2, 40, 24, O.PERIODIC, O.PERIODIC, prims=prims, steps=8,
+                    lam=0.5)
+        _assert_l1(g, o, 2)
+
+
 @pytest.mark.parametrize("kahan", [1, 0])
 def test_sod_1d_fp32_l1(kahan):
     g = _gpu(1, 1000, 1, L.TRANSMISSIVE, 0, riemann=SOD, steps=200,
