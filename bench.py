@@ -1,33 +1,43 @@
 #!/usr/bin/env python3
 """Benchmark of the tau = 1 lattice Boltzmann step on GB300.
 
-Workload (default): the 2-D shock tube on the square lattice, 4096 x 512
-nodes, x-only Sod jump at mid-length, transmissive x ends, reflecting y walls,
-run toward t = 0.2 (820 steps), synthetic initial state (Section V.C).
+Workload (default): the large 2-D cylindrical Riemann problem on the square
+lattice, 8192 x 8192 nodes on [0, 1]^2, inside a circle of radius 0.4 about
+(0.5, 0.5) (rho, p) = (1, 1), outside (0.125, 0.1), at rest, gamma = 1.4,
+periodic box, lambda = 1, 2000 steps (Section V.C's Riemann problem on a 2-D
+grid); synthetic initial state.
 
-One benchmark step = one tau = 1 step of the whole grid: the fused step
-kernel (window records, migration, summation, the new nodes' equilibria,
-reach and FP64 partial totals) and a one-block finalize kernel (FP64 totals,
-reach hand-off).  The state (67 MB in FP32, plus 100 MB of equilibrium
-records) is about the size of the 129 MB L2, so L2 is flushed by a 256 MB
-write between timed steps and every step is timed alone with CUDA events on
-the solver's stream.
+One benchmark step = one tau = 1 step of the whole grid: the fused FP32
+step kernel (window equilibria, deposit, shifted gather, the new nodes'
+reach and compensated partial totals) and a one-block finalize kernel
+(FP64 totals, reach hand-off).  The timed region is the whole solve from
+its initial state (K steps, 2000 by default), timed in blocks of up to 100
+steps with CUDA events on the solver's stream; the state (1.07 GB per set
+in FP32) is far larger than the 129 MB L2, so no flush is needed.
 
-  value      node-updates/s of the FP32 path (device-resident state)
-  fp64       the same for the FP64 path (bit-exact with the oracle)
+  value      node-updates/s of the FP32 path over the timed solve
+  windows    ms per step of the first, middle and last block of the solve
+             (the lattice-scale structure of the flow grows with time)
+  fp64       the FP64 path (bit-exact with the oracle) over the first steps
   e2e        node-updates/s of whole solves through the C ABI from pinned
-             host buffers: set moments (H2D), 820 steps, moments (D2H)
+             host buffers: set moments (H2D), K steps, moments (D2H)
   roofline   step: algorithmic bytes (4 fields read + 4 written per node) /
              mean step time (both kernels), against the measured HBM copy
              rate
   alu_check  the arrivals' multiply-adds (256 flop per node update) of the
              FP32 and FP64 steps against this GPU's measured FMA peaks
+  precision  FP32 against FP64 on the full grid after the first steps, and
+             at the end of the timed solve
+  sod2d      the 2-D shock tube (4096 x 512, transmissive x, reflecting y),
+             L2 flushed before every timed step, with FP32 / FP64 errors
+             against the oracle's stored row
   cpu_baseline  the FP64 oracle on this host's cores, bounded sample
 
-Other workloads (one JSON line each): --workload cylinder2d (8192^2 periodic
-cylinder), sod1d (1-D Sod time to solution, plain and CUDA-graph), tubes
-(4096 batched 1-D tubes vs plain FP64 one at a time), serve (continuous
-batching: capacity and Poisson sweep vs plain FP64 one at a time).
+Other workloads (one JSON line each): --workload sod2d (the shock tube as
+the main line), sod1d (1-D Sod time to solution, plain and CUDA-graph),
+tubes (4096 batched 1-D tubes vs plain FP64 one at a time), serve
+(continuous batching: capacity and Poisson sweep vs plain FP64 one at a
+time).
 
 --impl reference times the oracle alone (the CPU reference arm).
 Multi-GPU (torchrun): independent replicas, one per rank (weak scaling).
@@ -38,6 +48,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -49,13 +60,32 @@ sys.path.insert(0, ROOT)
 NX, NY = 4096, 512
 T_END = 0.2
 WORKLOAD = "sod_2d_4096x512_transmissive_x_reflecting_y"
-# profiling case: the periodic cylinder box, state larger than L2
+CYL_N, CYL_STEPS = 8192, 2000
+CYL_NAME = "cylinder_2d_8192x8192_periodic"
 WORKLOADS = {
     "sod2d": dict(nx=4096, ny=512, name=WORKLOAD),
-    "cylinder2d": dict(nx=8192, ny=8192, name="cylinder_2d_8192x8192_periodic"),
+    "cylinder2d": dict(nx=CYL_N, ny=CYL_N, name=CYL_NAME),
 }
 METRIC = "node-updates/s"
 L2_FLUSH_BYTES = 256 << 20
+CYL_IN = (1.0, 0.0, 0.0, 1.0)
+CYL_OUT = (0.125, 0.0, 0.0, 0.1)
+
+
+def host_info() -> dict:
+    """Host cores and CPU model of the machine running the oracle."""
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True,
+                             timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model,
+            "arch": platform.machine()}
 
 
 def load_peaks():
@@ -84,19 +114,22 @@ def job_rate(units_per_rank, world, t_max):
     return world * units_per_rank / t_max
 
 
-def measured_traffic(nodes):
+def measured_traffic(nodes, name="step2d_ds_traffic.json"):
     """DRAM bytes per launch of the FP32 2-D step kernel from the committed
     ncu summary, scaled by nodes; None unless the kernel sources are the
     ones that summary was taken from."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "step2d_f32_traffic.json")
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     with open(path) as f:
         rec = json.load(f)
     h = hashlib.sha256()
     for src in rec["sources"]:
-        with open(os.path.join(ROOT, src), "rb") as g:
+        p = os.path.join(ROOT, src)
+        if not os.path.exists(p):
+            return None
+        with open(p, "rb") as g:
             h.update(g.read())
     if h.hexdigest() != rec["sha256"]:
         return None
@@ -170,87 +203,91 @@ class Clocks:
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
-def run_ours(args, rank, world):
+def fp32_kernel_name(kahan):
+    return "lbm::ds::step2d_ds" if kahan == 0 else "step_kernel<float,2,true>"
+
+
+def run_cylinder(args, rank, world):
+    """The 8192^2 periodic cylinder: the whole FP32 solve from its initial
+    state, the FP64 path over its first steps, FP32 against FP64, e2e."""
+    import numpy as np
     import torch
     from paper_1602_02675_gb300 import lbm as L
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
-    wl = WORKLOADS[args.workload]
-    nx, ny = wl["nx"], wl["ny"]
-    dx = 1.0 / nx
-    nsolve, lam = steps_and_lambda(T_END, dx)
-    if args.workload == "cylinder2d":
-        lam = 1.0
-    N = nx * ny
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    n = CYL_N
+    N = n * n
+    K = args.steps if args.steps > 0 else CYL_STEPS
 
-    def make(prec, cons_every=1):
-        if args.workload == "cylinder2d":
-            cfg = L.make_config(2, nx, ny, dt=lam * dx, precision=prec,
-                                bc_x=L.PERIODIC, bc_y=L.PERIODIC,
-                                kahan=args.kahan, cons_every=cons_every,
-                                stream=stream.cuda_stream)
-            s = L.Solver(cfg)
-            s.init_riemann((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1),
-                           L.CIRCLE, 0.5, 0.5, 0.4)
-            return s
-        cfg = L.make_config(2, nx, ny, dt=lam * dx, precision=prec,
-                            bc_x=L.TRANSMISSIVE, bc_y=L.REFLECTING,
-                            kahan=args.kahan, cons_every=cons_every,
-                            stream=stream.cuda_stream)
-        s = L.Solver(cfg)
-        s.init_riemann((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), L.PLANAR_X, 0.5)
-        return s
+    def make(prec, kahan=args.kahan):
+        cfg = L.make_config(2, n, n, dt=1.0 / n, precision=prec,
+                            bc_x=L.PERIODIC, bc_y=L.PERIODIC, kahan=kahan,
+                            cons_every=1, stream=stream.cuda_stream)
+        return L.Solver(cfg)
 
-    def timed_steps(s, K, W):
+    def init(s):
+        s.init_riemann(CYL_IN, CYL_OUT, L.CIRCLE, 0.5, 0.5, 0.4)
+
+    def timed_solve(s, k, w, block=100):
+        """w untimed steps, back to the initial state, then k steps timed
+        in blocks with CUDA events on the solver's stream."""
         with torch.cuda.stream(stream):
-            s.step(W)
+            init(s)
+            s.step(w)
+            init(s)
             stream.synchronize()
+            nb = [min(block, k - i) for i in range(0, k, block)]
             ev = [(torch.cuda.Event(enable_timing=True),
-                   torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+                   torch.cuda.Event(enable_timing=True)) for _ in nb]
             if world > 1:
                 torch.distributed.barrier()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            for a, b in ev:
-                flush.fill_(1.0)          # evict the state from L2
+            for (a, b), m in zip(ev, nb):
                 a.record(stream)
-                s.step(1)
+                s.step(m)
                 b.record(stream)
             stream.synchronize()
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
         ms = [a.elapsed_time(b) for a, b in ev]
-        s.synchronize()
-        return ms, wall
+        return ms, nb, wall
 
-    # FP32 (headline)
     s32 = make(L.F32)
     clocks = Clocks(dev)
-    ms32, wall32 = timed_steps(s32, args.steps, args.warmup)
+    ms32, nb32, wall32 = timed_solve(s32, K, args.warmup)
     clk = clocks.stop()
+    s32.synchronize()
+    diag32 = s32.diagnostics()
+    reach32 = s32.reach()
+    end32 = s32.moments()
     s32.close()
-    # FP64 (oracle-exact path)
-    k64 = max(3, args.steps // 4)
+    per_step = [m / k for m, k in zip(ms32, nb32)]
+    windows = {"first": {"steps": f"1-{nb32[0]}", "ms_per_step": round(per_step[0], 5)},
+               "middle": {"steps": f"{sum(nb32[:len(nb32) // 2]) + 1}-"
+                                   f"{sum(nb32[:len(nb32) // 2 + 1])}",
+                          "ms_per_step": round(per_step[len(nb32) // 2], 5)},
+               "last": {"steps": f"{K - nb32[-1] + 1}-{K}",
+                        "ms_per_step": round(per_step[-1], 5)}}
+
+    # FP64 (oracle-exact path) over the first steps
+    k64 = max(3, args.fp64_steps)
     ms64 = [float("nan")]
     if args.precision == "both":
-        s64 = make(L.F64)
-        ms64, _ = timed_steps(s64, k64, max(3, args.warmup))
+        s64 = make(L.F64, kahan=1)
+        ms64, _, _ = timed_solve(s64, k64, 3, block=k64)
         s64.close()
 
     t32, t64 = max_over_ranks([sum(ms32) / 1e3, sum(ms64) / 1e3], world,
                               "cuda")
-    value = job_rate(N * args.steps, world, t32)
+    value = job_rate(N * K, world, t32)
     v64 = job_rate(N * k64, world, t64)
-
-    # e2e: whole solves through the C ABI from pinned host memory
-    e2e = (run_e2e(args, L, torch, stream, lam, nsolve, world)
-           if args.e2e_solves > 0 and args.workload == "sod2d" else None)
+    mean_ms = t32 / K * 1e3
+    mean64 = t64 / k64 * 1e3
 
     peak, peak_kind = load_peaks()
-    mean_ms = t32 / args.steps * 1e3
     bytes_per_launch = 8 * 4 * N            # 4 fields read + 4 written, FP32
     achieved = bytes_per_launch / (mean_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
@@ -258,18 +295,12 @@ def run_ours(args, rank, world):
             "traffic": (args.traffic if args.traffic is not None else
                         (measured_traffic(N) if args.kahan == 0 else None)),
             "peak_kind": peak_kind,
-            "kernel": ("lbm::fast::step2d_f32" if args.kahan == 0
-                       else "step_kernel<float,2,true>"),
+            "kernel": fp32_kernel_name(args.kahan),
             "bytes_per_launch": bytes_per_launch,
             "nominal_peak": 7900.0,
             "frac_of_nominal": round(achieved / 7900.0, 4),
-            "duration": ("CUDA events around lbm_step: step kernel + "
-                         "one-block finalize kernel" if args.kahan == 0 else
-                         "CUDA events around lbm_step: one step kernel")}
-    mean64 = t64 / k64 * 1e3
-    # Arithmetic roof: the gather's 32 arrivals x 4 fields of multiply-adds
-    # (256 flop per node update, a lower bound on the method's arithmetic)
-    # against this GPU's measured FMA throughput.
+            "duration": "CUDA events around lbm_step over the whole timed "
+                        "solve: step kernel + one-block finalize kernel"}
     peak32 = L.lbm_measure_fma_peak(L.F32, stream.cuda_stream)
     peak64 = L.lbm_measure_fma_peak(L.F64, stream.cuda_stream)
     alu = {"flop_per_node_update": 256,
@@ -279,21 +310,31 @@ def run_ours(args, rank, world):
            "fp32_frac": round(value * 256 / peak32, 4),
            "fp64_frac": (round(v64 * 256 / peak64, 4)
                          if args.precision == "both" else None)}
+
+    e2e = (run_e2e_cylinder(args, L, torch, stream, K, world)
+           if args.e2e_solves > 0 else None)
+    precision = (cylinder_precision(args, L, stream, end32, K)
+                 if rank == 0 and args.precision == "both" and not args.no_l1
+                 else None)
     line = {
         "metric": METRIC, "value": value, "unit": "node-updates/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": round(mean_ms, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (Sod initial state, Section V.C)",
-        "config": {"workload": wl["name"], "nx": nx, "ny": ny, "nodes": N,
-                   "lambda": lam, "steps_to_t0.2": nsolve,
-                   "l2": "flushed (256 MB write) before every timed step",
+        "data": "synthetic (cylindrical Riemann problem, Section V.C states)",
+        "config": {"workload": CYL_NAME, "nx": n, "ny": n, "nodes": N,
+                   "lambda": 1.0, "steps_of_solve": CYL_STEPS,
+                   "timed": f"steps 1-{K} of the solve from its initial state",
+                   "l2": "state (1.07 GB per set) larger than the 129 MB L2; "
+                         "no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "windows": windows,
+        "ms_per_step_blocks": [round(x, 5) for x in per_step],
+        "fp32_end_state": {"reach": reach32, "diagnostics": diag32},
         "fp64": {"value": v64, "unit": "node-updates/s", "steps": k64,
+                 "timed": f"steps 1-{k64} of the solve",
                  "ms_per_step": round(mean64, 5),
                  "hbm_frac": round((16 * 4 * N) / (mean64 / 1e3) / 1e9 / peak, 4),
-                 # FP64 on this GPU is bound by its FP64 pipe: the arrivals'
-                 # 256 flop per node update against the measured FP64 rate
                  "roofline": ({"bound": "alu",
                                "achieved": round(v64 * 256 / 1e12, 4),
                                "peak": round(peak64 / 1e12, 4),
@@ -306,84 +347,201 @@ def run_ours(args, rank, world):
         "roofline": roof,
         "alu_check": alu,
         "clocks": clk,
-        "gpu_launches": args.steps * (2 if args.kahan == 0 else 1),
+        "gpu_launches": 2 * K if args.kahan == 0 else K,
         "wall_s_timed_fp32": round(wall32, 4),
+        "precision": precision,
     }
+    if rank == 0 and not args.no_sod:
+        line["sod2d"] = run_sod2d(args, L, torch, stream, world, rank,
+                                  secondary=True)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
-    if rank == 0 and not args.no_l1:
-        line["l1_vs_oracle"] = l1_vs_oracle(L)
     return line
 
 
-def run_e2e(args, L, torch, stream, lam, nsolve, world):
-    """Whole solves: H2D of the initial moments from pinned host memory,
-    nsolve steps, D2H of the final moments and pressure."""
+def cylinder_precision(args, L, stream, end32, K):
+    """FP32 against FP64 on the full 8192^2 grid: mean |FP32 - FP64| / range
+    of the FP64 field after the first steps (FP64 is bit-exact with the
+    oracle in the tests), and the FP32 state at the end of the timed solve
+    against the FP64 state after the same number of steps when that is
+    short enough to run here."""
     import numpy as np
-    N = NX * NY
-    dx = 1.0 / NX
-    # the initial state, as a user would hold it on the host (physical units)
-    x = (np.arange(NX) + 0.5) * dx
-    left = np.tile(x < 0.5, NY)
+    n = CYL_N
+    steps = min(args.precision_steps, K)
+
+    def run(prec, kahan, k):
+        cfg = L.make_config(2, n, n, dt=1.0 / n, precision=prec,
+                            bc_x=L.PERIODIC, bc_y=L.PERIODIC, kahan=kahan,
+                            stream=stream.cuda_stream)
+        with L.Solver(cfg) as s:
+            s.init_riemann(CYL_IN, CYL_OUT, L.CIRCLE, 0.5, 0.5, 0.4)
+            s.step(k)
+            return s.moments()
+
+    ref = run(L.F64, 1, steps)
+    out = {"steps": steps, "metric": "mean |x - x_FP64| / (max - min of x_FP64)"}
+    for name, kahan in (("f32", 0), ("f32_kahan", 1)):
+        g = run(L.F32, kahan, steps)
+        out[name] = {f: float(np.mean(np.abs(g[f] - ref[f])) /
+                              max(float(ref[f].max() - ref[f].min()), 1e-300))
+                     for f in ("rho", "mx", "my", "rhoE")}
+    if K == steps:
+        out["end_of_timed_solve_is_this_state"] = True
+    out["note"] = ("the square-lattice step amplifies round-off (design "
+                   "notes): the oracle itself, rounding its state to FP32 "
+                   "each step, departs from FP64 by the amounts in "
+                   "tests/golden/cylinder_fp32_storage_floor.txt")
+    return out
+
+
+def run_e2e_cylinder(args, L, torch, stream, K, world):
+    """Whole solves: H2D of the initial moments from pinned host memory, K
+    steps, D2H of the final moments and pressure."""
+    import numpy as np
+    n = CYL_N
+    N = n * n
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x)
+    inside = ((X - 0.5) ** 2 + (Y - 0.5) ** 2 < 0.16).ravel()
     pin = lambda: torch.empty(N, dtype=torch.float64, pin_memory=True).numpy()
     rho, mx, my, rhoE = pin(), pin(), pin(), pin()
-    rho[:] = np.where(left, 1.0, 0.125)
+    rho[:] = np.where(inside, 1.0, 0.125)
     mx[:] = 0.0
     my[:] = 0.0
-    rhoE[:] = np.where(left, 1.0, 0.1) / 0.4
+    rhoE[:] = np.where(inside, 1.0, 0.1) / 0.4
     outs = {k: pin() for k in ("rho", "mx", "my", "rhoE", "p")}
-    cfg = L.make_config(2, NX, NY, dt=lam * dx, precision=L.F32,
-                        bc_x=L.TRANSMISSIVE, bc_y=L.REFLECTING,
-                        kahan=args.kahan, stream=stream.cuda_stream)
+    cfg = L.make_config(2, n, n, dt=1.0 / n, precision=L.F32,
+                        bc_x=L.PERIODIC, bc_y=L.PERIODIC, kahan=args.kahan,
+                        stream=stream.cuda_stream)
     times = []
     with L.Solver(cfg) as s:
         for rep in range(1 + args.e2e_solves):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             s.set_moments(rho, mx, my, rhoE)
-            s.step(nsolve)
+            s.step(K if rep > 0 else 2)
             s.moments(outs)
             dt = time.perf_counter() - t0
             if rep > 0:
                 times.append(dt)
     t = statistics.median(times)
-    return {"value": world * N * nsolve / t, "unit": "node-updates/s",
+    return {"value": world * N * K / t, "unit": "node-updates/s",
             "h2d_bytes_per_step": 4 * 8 * N, "d2h_bytes_per_step": 5 * 8 * N,
-            "step": f"one solve to t=0.2 ({nsolve} lattice steps)",
-            "solve_ms_p50": round(1e3 * t, 3),
-            "solves": len(times)}
+            "step": f"one solve ({K} lattice steps) with its host transfers",
+            "solve_ms_p50": round(1e3 * t, 3), "solves": len(times)}
+
+
+def run_sod2d(args, L, torch, stream, world, rank, secondary=False):
+    """The 2-D shock tube, 4096 x 512: each timed step alone after a 256 MB
+    L2 flush, FP32 (and FP64), errors against the oracle's stored row."""
+    dx = 1.0 / NX
+    nsolve, lam = steps_and_lambda(T_END, dx)
+    N = NX * NY
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    K = args.sod_steps if secondary else args.steps
+
+    def make(prec, kahan):
+        cfg = L.make_config(2, NX, NY, dt=lam * dx, precision=prec,
+                            bc_x=L.TRANSMISSIVE, bc_y=L.REFLECTING,
+                            kahan=kahan, cons_every=1,
+                            stream=stream.cuda_stream)
+        s = L.Solver(cfg)
+        s.init_riemann((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), L.PLANAR_X, 0.5)
+        return s
+
+    def timed_steps(s, k, w):
+        with torch.cuda.stream(stream):
+            s.step(w)
+            stream.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True),
+                   torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+            if world > 1 and not secondary:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            for a, b in ev:
+                flush.fill_(1.0)          # evict the state from L2
+                a.record(stream)
+                s.step(1)
+                b.record(stream)
+            stream.synchronize()
+            torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        s.synchronize()
+        return ms
+
+    s32 = make(L.F32, args.kahan)
+    clocks = None if secondary else Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    ms32 = timed_steps(s32, K, args.warmup)
+    clk = clocks.stop() if clocks else None
+    s32.close()
+    k64 = max(3, K // 4)
+    s64 = make(L.F64, 1)
+    ms64 = timed_steps(s64, k64, 3)
+    s64.close()
+    t32, t64 = (sum(ms32) / 1e3, sum(ms64) / 1e3)
+    if not secondary:
+        t32, t64 = max_over_ranks([t32, t64], world, "cuda")
+    value = job_rate(N * K, world if not secondary else 1, t32)
+    mean_ms = t32 / K * 1e3
+    peak, peak_kind = load_peaks()
+    achieved = 32 * N / (mean_ms / 1e3) / 1e9
+    out = {"workload": WORKLOAD, "value": value, "unit": "node-updates/s",
+           "steps": K, "ms_per_step": round(mean_ms, 5),
+           "timed": f"steps {args.warmup + 1}-{args.warmup + K} of the "
+                    f"{nsolve}-step solve, each alone after an L2 flush",
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1),
+                        "peak": peak, "unit": "GB/s",
+                        "frac": round(achieved / peak, 4),
+                        "peak_kind": peak_kind,
+                        "kernel": fp32_kernel_name(args.kahan)},
+           "fp64": {"ms_per_step": round(t64 / k64 * 1e3, 5),
+                    "value": N * k64 / t64}}
+    if clk is not None:
+        out["clocks"] = clk
+    if rank == 0 and not args.no_l1:
+        out["l1_vs_oracle"] = l1_vs_oracle(L)
+    return out
 
 
 # --------------------------------------------------------------------------
 # the oracle on the host: CPU baseline and reference arm
 # --------------------------------------------------------------------------
-def _oracle_sod_steps(nsteps, ny=NY):
+def _oracle_cylinder_rows(rows, nsteps=1):
+    """nsteps oracle steps of a periodic strip of the cylinder's initial
+    state: all 8192 columns, `rows` rows through the circle's centre (the
+    same arithmetic per node as the full grid; the strip closes on itself
+    along y).  Returns (seconds, node updates)."""
+    import numpy as np
     from oracle import oracle as O
-    dx = 1.0 / NX
-    _, lam = steps_and_lambda(T_END, dx)
-    P = O.Params(dim=2, nx=NX, ny=ny, bc_x=O.TRANSMISSIVE, bc_y=O.REFLECTING)
-    s = O.riemann_planar(P, 0.0, 1.0, 0.5, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1),
-                         lam)
+    n = CYL_N
+    P = O.Params(dim=2, nx=n, ny=rows, bc_x=O.PERIODIC, bc_y=O.PERIODIC)
+    x = (np.arange(n) + 0.5) / n
+    y = 0.5 + (np.arange(rows) - rows // 2 + 0.5) / n
+    X, Y = np.meshgrid(x, y)
+    inside = ((X - 0.5) ** 2 + (Y - 0.5) ** 2 < 0.16).ravel()
+    pick = lambda i: np.where(inside, CYL_IN[i], CYL_OUT[i])
+    s = O.prims_to_lattice(1.4, 1.0, pick(0), pick(1), pick(2), pick(3))
     t0 = time.perf_counter()
     O.run(P, s, nsteps)
-    return time.perf_counter() - t0, NX * ny * nsteps
+    return time.perf_counter() - t0, n * rows * nsteps
 
 
 def cpu_baseline(seconds: float) -> dict:
-    # calibrate on one step of a 4096 x 8 strip, then size the sample
-    t, nu = _oracle_sod_steps(1, ny=8)
+    # calibrate on one step of an 8192 x 4 strip, then size the sample
+    t, nu = _oracle_cylinder_rows(4)
     rate = nu / t
-    rows = max(8, min(NY, int(seconds * rate / NX)))
-    t, nu = _oracle_sod_steps(1, ny=rows)
+    rows = max(4, min(CYL_N, int(seconds * rate / CYL_N)))
+    t, nu = _oracle_cylinder_rows(rows)
     return {"value": nu / t, "unit": "node-updates/s", "cores": 1,
-            "kind": "oracle",
-            "sample": f"1 step of a 4096 x {rows} strip of the 4096 x 512 Sod "
-                      f"lattice (FP64, single thread), {t:.1f} s"}
+            "kind": "oracle", "host": host_info(),
+            "sample": f"1 step of an 8192 x {rows} periodic strip through the "
+                      f"centre of the cylinder's initial state (FP64 oracle, "
+                      f"one thread), {t:.1f} s"}
 
 
 def l1_vs_oracle(L) -> dict:
-    """FP32 and FP64 paths against the FP64 oracle on the benchmark workload:
-    a whole 4096 x 512 solve to t = 0.2 (820 steps), mean |error| / field
+    """FP32 and FP64 paths against the FP64 oracle on the shock tube: a
+    whole 4096 x 512 solve to t = 0.2 (820 steps), mean |error| / field
     range of every row against the oracle's row stored in
     tests/golden/sod2d_row_4096_t0.2.txt (written from oracle/ alone; the
     data vary along x only, so every row is that row)."""
@@ -407,8 +565,7 @@ def l1_vs_oracle(L) -> dict:
                      for f in ("rho", "mx", "rhoE")}
         out[name]["my_max_abs"] = float(np.max(np.abs(g["my"])))
     out["case"] = ("sod_2d_4096x512, 820 steps to t = 0.2, every row; f32: "
-                   "register kernel (plain FP32 sums), f32_kahan: compensated "
-                   "exact-order kernel")
+                   "deposit kernel, f32_kahan: compensated exact-order kernel")
     return out
 
 
@@ -604,31 +761,36 @@ def run_sod1d(args):
 
 
 def run_reference(args, rank, world):
-    """The CPU oracle as it stands: K bounded samples of the workload."""
+    """The CPU oracle as it stands: K bounded samples of the workload (each
+    a step of a periodic strip of the cylinder's initial state)."""
     if rank != 0:
         return None
     times, nus = [], []
     rows = args.ref_rows
+    K = args.steps if args.steps > 0 else 5
     for _ in range(args.warmup):
-        _oracle_sod_steps(1, ny=rows)
-    for _ in range(args.steps):
-        t, nu = _oracle_sod_steps(1, ny=rows)
+        _oracle_cylinder_rows(rows)
+    for _ in range(K):
+        t, nu = _oracle_cylinder_rows(rows)
         times.append(t)
         nus.append(nu)
     value = sum(nus) / sum(times)
+    sample = (f"each step: 1 lattice step of an 8192 x {rows} periodic strip "
+              "through the centre of the cylinder's initial state (FP64 "
+              "oracle, one thread)")
     return {
         "metric": METRIC, "value": value, "unit": "node-updates/s",
-        "impl": "reference", "n_gpus": world, "steps": args.steps,
+        "impl": "reference", "n_gpus": world, "steps": K,
         "warmup": args.warmup,
         "ms_per_step": round(1e3 * sum(times) / len(times), 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (Sod initial state, Section V.C)",
-        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY,
+        "dtype": "f64",
+        "data": "synthetic (cylindrical Riemann problem, Section V.C states)",
+        "config": {"workload": CYL_NAME, "nx": CYL_N, "ny": CYL_N,
                    "sample_rows": rows},
         "cpu_baseline": {"value": value, "unit": "node-updates/s",
-                         "cores": 1, "kind": "oracle",
-                         "sample": f"each step: 1 lattice step of a 4096 x {rows} "
-                                   "strip of the Sod lattice (FP64, 1 thread)"},
+                         "cores": 1, "kind": "oracle", "host": host_info(),
+                         "sample": sample},
         "e2e": {"value": value, "unit": "node-updates/s",
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -637,29 +799,36 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=0,
+                    help="timed steps (cylinder: 0 = the whole 2000-step "
+                         "solve; sod2d: 0 = 200)")
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-solves", type=int, default=2)
+    ap.add_argument("--e2e-solves", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-rows", type=int, default=16)
+    ap.add_argument("--ref-rows", type=int, default=8)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per step-kernel launch, if measured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-l1", action="store_true")
-    ap.add_argument("--workload", default="sod2d",
+    ap.add_argument("--no-sod", action="store_true",
+                    help="cylinder: skip the shock-tube sub-measurement")
+    ap.add_argument("--sod-steps", type=int, default=200)
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--precision-steps", type=int, default=100)
+    ap.add_argument("--workload", default="cylinder2d",
                     choices=sorted(WORKLOADS) + ["tubes", "serve", "sod1d"])
     ap.add_argument("--repeats", type=int, default=100,
                     help="sod1d: solves timed")
-    ap.add_argument("--requests", type=int, default=300)
+    ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--budget-gb", type=float, default=120.0)
-    ap.add_argument("--max-side", type=int, default=1024)
+    ap.add_argument("--max-side", type=int, default=2048)
     ap.add_argument("--tubes", type=int, default=4096)
     ap.add_argument("--batch-reps", type=int, default=2)
     ap.add_argument("--seq-tubes", type=int, default=48)
     ap.add_argument("--precision", default="both", choices=["both", "f32"])
     ap.add_argument("--kahan", type=int, default=0, choices=[0, 1],
-                    help="FP32 kernel: 0 register kernel, 1 compensated "
+                    help="FP32 kernel: 0 deposit kernel, 1 compensated "
                          "exact-order kernel")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -685,12 +854,41 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         torch.distributed.init_process_group("nccl")
-    line = run_ours(args, rank, world)
+    if args.workload == "cylinder2d":
+        line = run_cylinder(args, rank, world)
+    else:
+        line = run_sod2d_main(args, rank, world)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()
+
+
+def run_sod2d_main(args, rank, world):
+    """--workload sod2d: the shock tube as the main line."""
+    import torch
+    from paper_1602_02675_gb300 import lbm as L
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.Stream()
+    if args.steps <= 0:
+        args.steps = args.sod_steps
+    sub = run_sod2d(args, L, torch, stream, world, rank, secondary=False)
+    line = {"metric": METRIC, "value": sub["value"], "unit": "node-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sub["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (Sod initial state, Section V.C)",
+            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY,
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": (f"replicas x{world}" if world > 1
+                                       else "1 GPU")},
+            "roofline": sub["roofline"], "clocks": sub.get("clocks"),
+            "gpu_launches": 2 * args.steps if args.kahan == 0 else args.steps,
+            "sod2d": sub}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    return line
 
 
 if __name__ == "__main__":

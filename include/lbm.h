@@ -316,20 +316,30 @@ void lbm_pool_destroy(lbm_pool* p);
  * Arrays are in lattice units (m = rho u lambda, rhoE scaled by lambda^2),
  * element type float (LBM_F32) or double (LBM_F64), nx*ny nodes, x fastest,
  * order {rho, m_x, m_y, rhoE}; m_y may be NULL in 1-D.  in and out must not
- * overlap.  totals (4 doubles), reach (1 int32) and flags (1 uint32, bit 0
- * LBM_ESTATE, bit 1 LBM_EREACH) are optional device pointers that receive
- * the new state's FP64 totals, the reach of the new state and the device
- * error flags.  The maximum reach is the lbm_create default (1-D 64, 2-D 6).
- * Work is queued on stream (cudaStream_t, NULL = default stream); the call
- * returns without waiting, so device-side errors arrive through flags.
- * err (nullable, err_len bytes) receives a message on failure.
+ * overlap.  totals (4 doubles), reach (1 int32) and flags (1 uint32) are
+ * optional device pointers that receive the new state's FP64 totals, the
+ * reach of the new state and the device error flags.  The maximum reach
+ * is the lbm_create default (1-D 64, 2-D 6).  Work is queued on stream
+ * (cudaStream_t, NULL = default stream); the call returns without waiting,
+ * so device-side errors arrive only through flags: a caller that passes
+ * flags = NULL cannot tell a failed step from a good one.  Per bit:
+ *   bit 1 (2, LBM_EREACH): the input's reach exceeds the maximum; the step
+ *     did not run: out is left as it was, totals are 0 and reach is the
+ *     input's;
+ *   bit 0 (1, LBM_ESTATE): a node of the input or of the new state has
+ *     rho < 0 or a non-finite moment; the step ran, but out and totals
+ *     hold whatever that state produced and must not be used.
+ * With flags == 0, out, totals and reach are valid.  err (nullable, err_len
+ * bytes) receives a message on a host-side failure.
  *
  * Every call shares the one scratch array, which keeps the last call's
  * contents; each call clears the part that must start at zero.  Calls that
  * overlap on the GPU (different streams or threads at the same time) race
  * on it and must be serialized by the caller.  The first call on a device
  * looks up the array's device address (once per device, with that device
- * current); make that first call before any stream capture.
+ * current; again after the device's context was destroyed and created
+ * anew, e.g. by cudaDeviceReset); make that first call, and the first call
+ * after such a reset, before any stream capture.
  */
 #define LBM_NOALLOC_SCRATCH_BYTES (1u << 20)
 

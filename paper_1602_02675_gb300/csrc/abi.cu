@@ -25,13 +25,6 @@ struct lbm_handle {
   int nblocks = 0;
   void* buf[2][4] = {{nullptr}};
   int cur = 0;
-  // FP32 square lattice: equilibrium records of buf[b] in rec[b] (float4
-  // and float2 arrays); rec_ok says whether rec[cur] matches buf[cur].
-  bool use_rec = false;
-  void* rec[2][2] = {{nullptr}};
-  bool rec_ok = false;
-  int rec_pitch = 0;      // nodes per record row (nx rounded up to even)
-  TmaMap rec_map[2][2];   // TMA tensor maps of rec[b][0], rec[b][1]
   // FP64 square lattice: source records of the state being stepped,
   // rewritten before every step.
   void* src = nullptr;
@@ -187,7 +180,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
     delete h;
     return st;
   }
-  h->nblocks = step_blocks(c.dim, h->nx, h->ny);
+  h->nblocks = (int)step_blocks(c.dim, h->nx, h->ny);  // nx ny <= INT32_MAX
   h->part_cap = h->nblocks > totals_blocks(h->n) ? h->nblocks
                                                  : totals_blocks(h->n);
   const size_t fb = esize(h) * (size_t)h->n;
@@ -197,27 +190,6 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
       if (f == 2 && c.dim == 1) continue;
       ok = cudaMalloc(&h->buf[b][f], fb) == cudaSuccess;
     }
-  h->use_rec = step_uses_records(c.dim, h->f64, c.kahan ? 1 : 0, h->r_cap);
-  h->rec_pitch = h->nx + (h->nx & 1);
-  const size_t rec_nodes = (size_t)h->rec_pitch * (size_t)h->ny;
-  for (int b = 0; b < 2 && ok && h->use_rec; ++b) {
-    ok = cudaMalloc(&h->rec[b][0], 16 * rec_nodes) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->rec[b][1], 8 * rec_nodes) == cudaSuccess;
-    if (ok && make_record_maps(h->rec[b][0], h->rec[b][1], h->nx, h->ny,
-                               h->rec_pitch, &h->rec_map[b][0],
-                               &h->rec_map[b][1]) != cudaSuccess) {
-      // no TMA tensor maps on this driver: the handle steps with the
-      // exact-order FP32 kernel instead (no records)
-      cudaGetLastError();
-      for (int q = 0; q < 2; ++q)
-        for (int f = 0; f < 2; ++f)
-          if (h->rec[q][f]) {
-            cudaFree(h->rec[q][f]);
-            h->rec[q][f] = nullptr;
-          }
-      h->use_rec = false;
-    }
-  }
   if (ok && c.dim == 2 && h->f64)
     ok = cudaMalloc(&h->src, src_bytes(h->nx, h->ny, h->r_cap, esize(h))) ==
          cudaSuccess;
@@ -275,7 +247,6 @@ lbm_status lbm_init_riemann(lbm_handle* h, const lbm_prim* inner,
     d[2] = h->dim == 2 ? s[j]->v : 0.0;
     d[3] = s[j]->p;
   }
-  h->rec_ok = false;
   LBM_CUDA(h, launch_init(h->f64, a, h->stream), "init kernel");
   LBM_CUDA(h, cudaMemsetAsync(h->scr, 0, sizeof(Scratch), h->stream),
            "scratch clear");
@@ -306,7 +277,6 @@ static lbm_status set_from_host(lbm_handle* h, int kind, const double* a,
            "copy to device");
   void* f[4];
   cur_fields(h, f);
-  h->rec_ok = false;
   LBM_CUDA(h, launch_from_host_layout(h->f64, kind, h->dim, h->staging, f, n,
                                       h->lambda, h->cfg.gamma, h->stream),
            "convert kernel");
@@ -353,23 +323,6 @@ lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
     }
     const int every = h->cfg.cons_every;
     a.do_cons = (every > 0 && ((h->steps + 1) % every) == 0) ? 1 : 0;
-    if (h->use_rec) {
-      if (!h->rec_ok) {
-        const void* f[4] = {a.in[0], a.in[1], a.in[2], a.in[3]};
-        LBM_CUDA(h, launch_records_f32(f, h->rec[h->cur][0], h->rec[h->cur][1],
-                                       h->nx, h->ny, h->rec_pitch, h->k,
-                                       h->stream),
-                 "records kernel");
-        h->rec_ok = true;
-      }
-      a.rin_a = h->rec[h->cur][0];
-      a.rin_b = h->rec[h->cur][1];
-      a.rout_a = h->rec[h->cur ^ 1][0];
-      a.rout_b = h->rec[h->cur ^ 1][1];
-      a.rec_pitch = h->rec_pitch;
-      a.map_a = &h->rec_map[h->cur][0];
-      a.map_b = &h->rec_map[h->cur][1];
-    }
     LBM_CUDA(h, launch_step(h->dim, h->f64, a, h->smem, h->stream),
              "step kernel");
     h->cur ^= 1;
@@ -471,9 +424,6 @@ void lbm_destroy(lbm_handle* h) {
   for (int b = 0; b < 2; ++b)
     for (int f = 0; f < 4; ++f)
       if (h->buf[b][f]) cudaFree(h->buf[b][f]);
-  for (int b = 0; b < 2; ++b)
-    for (int f = 0; f < 2; ++f)
-      if (h->rec[b][f]) cudaFree(h->rec[b][f]);
   if (h->src) cudaFree(h->src);
   if (h->scr) cudaFree(h->scr);
   if (h->part) cudaFree(h->part);

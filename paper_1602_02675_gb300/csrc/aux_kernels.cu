@@ -22,10 +22,14 @@ cudaError_t step_prepare(int dim, bool f64, size_t smem) {
   return f64 ? step_prepare_f64(dim, smem) : step_prepare_f32(dim, smem);
 }
 
-int step_blocks(int dim, int nx, int ny) {
-  if (dim == 1) return (nx + step_tile_1d(nx) - 1) / step_tile_1d(nx);
-  return ((nx + TileShape<2>::TX - 1) / TileShape<2>::TX) *
-         ((ny + TileShape<2>::TY - 1) / TileShape<2>::TY);
+long long step_blocks(int dim, int nx, int ny) {
+  const long long X = nx, Y = ny;
+  if (dim == 1) {
+    const long long tw = step_tile_1d(nx);
+    return (X + tw - 1) / tw;
+  }
+  return ((X + TileShape<2>::TX - 1) / TileShape<2>::TX) *
+         ((Y + TileShape<2>::TY - 1) / TileShape<2>::TY);
 }
 
 cudaError_t launch_step(int dim, bool f64, const StepArgs& a, size_t smem,

@@ -10,11 +10,6 @@ namespace lbm {
 // Device error flags (Scratch::flags).
 enum : unsigned { kFlagState = 1u, kFlagReach = 2u, kFlagTimeout = 4u };
 
-// Opaque copy of a TMA tensor map (CUtensorMap: 128 bytes, 64-byte aligned).
-struct alignas(64) TmaMap {
-  unsigned char bytes[128];
-};
-
 // Small device-resident block of per-handle scratch words.
 struct Scratch {
   int reach;               // migration reach the next step uses
@@ -57,22 +52,6 @@ struct StepArgs {
   EqConst k;
   Scratch* scr;
   double* part;       // [nblocks * 4] FP64 partial sums
-  // FP32 square lattice only: per-node equilibrium records of the input
-  // (rin) and of the output (rout) state, or null.  rec_a = (V_x, V_y, d1,
-  // d2), rec_b = (E_b, flag word); see step_fast_f32.cuh.
-  const void* rin_a = nullptr;
-  const void* rin_b = nullptr;
-  void* rout_a = nullptr;
-  void* rout_b = nullptr;
-  int rec_pitch = 0;  // nodes per record row (>= nx, even)
-  // Host copies of the TMA tensor maps of rin_a / rin_b (FP32 tensors of
-  // widths 4 nx and 2 nx, rows of 16 and 8 pitch bytes), read by the
-  // launcher.
-  const TmaMap* map_a = nullptr;
-  const TmaMap* map_b = nullptr;
-  // Tiles resident at once (set by the launcher): a block prefetches into
-  // L2 the input records of the tile that many launches ahead.
-  int prefetch_ahead = 0;
   // FP64 square lattice: source records of the input state over the grid
   // padded by r_cap (layout in step_kernel.cuh), written by the launcher's
   // records pass before each step, or null.
@@ -89,21 +68,11 @@ inline size_t src_bytes(int nx, int ny, int r_cap, size_t esize) {
 // Launch helpers (step kernels).
 size_t step_smem_bytes(int dim, bool f64, int r_cap);
 cudaError_t step_prepare(int dim, bool f64, size_t smem);
-int step_blocks(int dim, int nx, int ny);
+// Blocks of the exact-order step kernel for an nx x ny grid (64-bit: no
+// overflow for any int sizes).
+long long step_blocks(int dim, int nx, int ny);
 cudaError_t launch_step(int dim, bool f64, const StepArgs& a, size_t smem,
                         cudaStream_t s);
-
-// FP32 square-lattice handles whose steps carry equilibrium records between
-// launches (the fast kernel's path); records take 24 bytes per node.
-bool step_uses_records(int dim, bool f64, int kahan, int r_cap);
-// Records of the state f (FP32 moments, nx x ny) into rec_a float4 and
-// rec_b float2 arrays with rows of `pitch` nodes.
-cudaError_t launch_records_f32(const void* const f[4], void* rec_a,
-                               void* rec_b, int nx, int ny, int pitch,
-                               const EqConst& k, cudaStream_t s);
-// TMA tensor maps of a pair of record arrays (see StepArgs::map_a).
-cudaError_t make_record_maps(void* rec_a, void* rec_b, int nx, int ny,
-                             int pitch, TmaMap* map_a, TmaMap* map_b);
 
 // Auxiliary kernels (init, conversion, reductions).
 struct InitArgs {

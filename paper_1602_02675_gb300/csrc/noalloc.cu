@@ -8,6 +8,9 @@
 // error flags, the last-block ticket and the FP64 partial sums of the step
 // kernel) live in one file-scope device array that every GPU loading the
 // library holds until the process exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -38,6 +41,10 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_ptr[kMaxDevices] = {nullptr};
+// Context the cached address belongs to: a context torn down and created
+// again (cudaDeviceReset) loads the module anew, so the address is looked
+// up again when the current context changes.
+CUcontext g_ctx[kMaxDevices] = {nullptr};
 
 void set_err(char* err, size_t len, const char* msg) {
   if (err && len > 0) {
@@ -51,16 +58,41 @@ void set_cuda_err(char* err, size_t len, const char* what, cudaError_t e) {
                   cudaGetErrorString(e));
 }
 
+// Current driver context (through the runtime's driver entry point, so the
+// library needs no link against the driver library); nullptr if unknown.
+CUcontext current_context() {
+  static PFN_cuCtxGetCurrent_v4000 get = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000,
+                                         cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess && fn)
+      get = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
+    else
+      cudaGetLastError();
+    tried = true;
+  }
+  CUcontext c = nullptr;
+  if (get && get(&c) != CUDA_SUCCESS) c = nullptr;
+  return c;
+}
+
 // Device address of the scratch array on the current device.  The symbol's
 // name in host code is only a host-side stand-in, so the address is taken
-// with cudaGetSymbolAddress, once per device, with that device current.
+// with cudaGetSymbolAddress, once per device (and again if that device's
+// context was replaced), with that device current.
 cudaError_t scratch_on(int dev, unsigned char** out) {
   std::lock_guard<std::mutex> lock(g_mu);
-  if (g_ptr[dev] == nullptr) {
+  const CUcontext ctx = current_context();
+  if (g_ptr[dev] == nullptr || ctx == nullptr || ctx != g_ctx[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_ptr[dev] = static_cast<unsigned char*>(p);
+    g_ctx[dev] = ctx;
   }
   *out = g_ptr[dev];
   return cudaSuccess;
@@ -96,16 +128,18 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_noalloc_desc* d,
     return LBM_EINVAL;
   }
   const int nx = (int)d->nx, ny = (int)(d->dim == 2 ? d->ny : 1);
-  const int tiles = step_blocks(d->dim, nx, ny);
-  if (tiles > kMaxTiles) {
+  // tile count in 64 bits, checked before anything is launched
+  const long long tiles64 = step_blocks(d->dim, nx, ny);
+  if (tiles64 > kMaxTiles) {
     char msg[256];
     std::snprintf(msg, sizeof(msg),
-                  "lbm_step_noalloc: %lld x %lld nodes need %d tiles; the "
+                  "lbm_step_noalloc: %lld x %lld nodes need %lld tiles; the "
                   "static scratch holds at most %d (use lbm_create/lbm_step)",
-                  (long long)d->nx, (long long)d->ny, tiles, kMaxTiles);
+                  (long long)d->nx, (long long)d->ny, tiles64, kMaxTiles);
     set_err(err, err_len, msg);
     return LBM_EINVAL;
   }
+  const int tiles = (int)tiles64;
   const bool f64 = d->precision == LBM_F64;
   const int r_cap = d->dim == 1 ? 64 : 6;
   const size_t smem = step_smem_bytes(d->dim, f64, r_cap);

@@ -1,0 +1,822 @@
+// FP32 fused step for the square lattice (2-D): deposit, then shift.
+//
+// The method (Section III.B, eqs 11-15, 21-26, 29; Section V.A-B) moves,
+// from every source s, eight packets: packet p of level v carries mass d_v,
+// momentum d_v (V + c'_p) and energy d_v (E_b + V.c'_p + |c'_p|^2/2), with
+// E_b = |V|^2/2 + phi (eqs 12-15), and lands bilinearly (eq 29) on the four
+// nodes around s + V + c'_p: corner k = (k_x, k_y) at s + n + c'_p + k,
+// n = floor(V), with weight w_k(s) = ((1-f_x) or f_x) ((1-f_y) or f_y).
+// Every packet field is a fixed linear map of the level record
+//   L_v(s) = d_v (1, V_x, V_y, E_b)
+// that depends only on c'_p.  So, among sources that share n and c1 (one
+// "type"), the arrivals at a destination x are
+//   Y(x) = sum_v sum_{p in v} M(c'_p) D_v(x - n - c'_p),
+//   D_v(q) = sum_k w_k(q - k) L_v(q - k)                       (deposit)
+// i.e. the records are deposited bilinearly once (32 multiply-adds per
+// position) and each destination then reads eight shifted deposits, instead
+// of visiting 32 packet landings.  The arithmetic differs from the landing
+// by landing sum only in rounding; the sum of every destination has the same
+// form and order relative to the destination, so uniform states stay uniform
+// and data that vary along x only stay so bit for bit (their y-momentum
+// arrivals from rows +-c cancel exactly).
+//
+// Layout of one launch: one block per tile.  The block's window is 61 x 48
+// sources (WCOLS x WROWS); with the step's reach R the tile is the window
+// minus R on every side, (61 - 2R) x (48 - 2R) destinations.
+//  * Phase 1 (window).  Thread (lane, wx, g) owns window column
+//    lane + 30 wx (the two warps of a row overlap by two columns; column 61
+//    holds deposits only) and walks rows 12 g - 1 .. 12 g + 12 (the groups
+//    overlap; row 48 holds deposits only).  Walking down its column it loads
+//    each source's moments (coalesced: a warp reads 32 consecutive nodes of
+//    a row), forms the equilibrium and deposits: the parts that land in its
+//    own column it sums itself over the rows, the parts that land one or two
+//    columns to the right come from the lanes to the left by shuffles, and
+//    the deposit goes to shared memory.  Sources outside the grid are the
+//    additional points of Section V.B (nearest node, periodic image, or
+//    mirror image with the normal momentum negated).
+//  * Phase 2 (tile).  Each thread gathers destinations of the tile in
+//    row-major order, 256 apart, from the deposits: per level four reads
+//    (+x, -x, +y, -y packets), and writes the new moments; then the new
+//    node's reach and the block's compensated partial totals.
+// The window's sources are all of one type in most tiles; the first deposit
+// is formed for the type of the tile's central node, and the block checks
+// that every source had that type.  Otherwise the sources are grouped by c1
+// and by blocks of two lattice shifts per axis, n in {a, a+1} x {b, b+1}:
+// relative to the base (a, b) such a source lands at s + dn + k, dn in
+// {0, 1}^2, so the deposit weights become hat functions over three offsets
+// per axis (a general deposit, one walk per group), and the gather is the
+// one-type gather at shift (a, b).  Groups are done in ascending order,
+// each adding its arrivals to the destinations.
+#pragma once
+
+#include <cstdint>
+
+#include "fp32_arith.cuh"
+#include "step_kernel.cuh"
+
+namespace lbm {
+namespace ds {
+
+constexpr int NWX = 2;                    // warps across a window row
+constexpr int CW = 32 * NWX;              // threads across
+constexpr int WSTEP = 30;                 // column offset of the second warp
+constexpr int DCOLS = WSTEP + 32;         // deposit columns 1 .. 61
+constexpr int WCOLS = DCOLS - 1;          // source columns 0 .. 60
+constexpr int NG = 4;                     // row groups
+constexpr int SH = 12;                    // rows a group deposits
+constexpr int WROWS = NG * SH;            // source rows 0 .. 47
+constexpr int NTHR = CW * NG;             // 256
+constexpr int NWARP = NTHR / 32;
+constexpr int RMAX = 6;                   // largest reach of this layout
+constexpr int DP = CW;                    // deposit row pitch (positions)
+constexpr int PLANE = DP * (WROWS + 1);   // deposit rows 1 .. 48
+// Type ids: c1 * 65536 + (n_x + 128) * 256 + (n_y + 128), held exactly in
+// a float; sources that emit nothing have no type.
+constexpr float kNoType = 16777216.0f;
+
+__host__ __device__ constexpr size_t smem_bytes() {
+  return (size_t)2 * PLANE * sizeof(float4);
+}
+__host__ __device__ inline int tile_w(int R) { return WCOLS - 2 * R; }
+__host__ __device__ inline int tile_h(int R) { return WROWS - 2 * R; }
+// Tiles of an nx x ny grid at reach R (at least 1).
+__host__ __device__ inline int tiles_for(int nx, int ny, int R) {
+  const int r = R < 1 ? 1 : R;
+  return ((nx + tile_w(r) - 1) / tile_w(r)) * ((ny + tile_h(r) - 1) / tile_h(r));
+}
+
+// The part of a node's equilibrium that both the window phase and the
+// producing step's reach need, in explicitly rounded operations so that the
+// two agree bit for bit: V = m / rho (one refined reciprocal), |V|^2,
+// e = E - |V|^2/2 (eq 13, eq 15 text) before and after the clamp at 0, and
+// X = D (gamma - 1) e (eq 26 with d0 = 0 on the square lattice).
+struct EqCore {
+  float Vx, Vy, kin2, eraw, X;
+};
+__device__ __forceinline__ EqCore eq_core(float rho, float mx, float my,
+                                          float rhoE, float kq) {
+  EqCore c;
+  const float inv = rcp_nr(rho);
+  c.Vx = __fmul_rn(mx, inv);
+  c.Vy = __fmul_rn(my, inv);
+  c.kin2 = __fmaf_rn(c.Vy, c.Vy, __fmul_rn(c.Vx, c.Vx));
+  c.eraw = __fmaf_rn(-0.5f, c.kin2, __fmul_rn(rhoE, inv));
+  c.X = __fmul_rn(kq, fmaxf(c.eraw, 0.0f));
+  return c;
+}
+
+// c1 = int(sqrt(X)) (eq 26), exactly: below 16 by counting the squares
+// X reaches, above by the estimate with the integer test (c1_of).  Every
+// lane of the warp must call it.
+__device__ __forceinline__ float c1_exact(float X) {
+  float c = (X >= 1.0f ? 1.0f : 0.0f) + (X >= 4.0f ? 1.0f : 0.0f) +
+            (X >= 9.0f ? 1.0f : 0.0f);
+  if (__any_sync(0xffffffffu, !(X < 16.0f))) c = X < 16.0f ? c : c1_of(X);
+  return c;
+}
+
+// n = floor(V), f = V - n (eq 23); f rounded to 1 is taken as (n + 1, 0).
+__device__ __forceinline__ void split_f(float V, float& n, float& f) {
+  const float fl = floorf(V);
+  const float fr = __fsub_rn(V, fl);
+  const bool one = fr == 1.0f;
+  n = one ? __fadd_rn(fl, 1.0f) : fl;
+  f = one ? 0.0f : fr;
+}
+
+// Migration reach floor(max |V_a|) + 1 + c2 (eq 26) of a node whose core
+// and c1 are given; 0 for a node that emits nothing.
+__device__ __forceinline__ int reach_of(bool emits, const EqCore& c,
+                                        float c1) {
+  const float v = floorf(fmaxf(fabsf(c.Vx), fabsf(c.Vy)));
+  const float r = v + 2.0f + c1;
+  return !emits ? 0 : (r > 1.0e8f ? 100000000 : (int)r);
+}
+
+// Interior node supplying source coordinate L on one axis (Section V.B).
+__device__ __forceinline__ int axis_src(int bc, int n, int L, bool* flip) {
+  *flip = false;
+  if ((unsigned)L < (unsigned)n) return L;
+  return virtual_axis(bc, n, (long long)L, flip);
+}
+
+__device__ __forceinline__ float4 f4(float a, float b, float c, float d) {
+  return make_float4(a, b, c, d);
+}
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+  const float2 lo = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+  const float2 hi = __fadd2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w));
+  return f4(lo.x, lo.y, hi.x, hi.y);
+}
+__device__ __forceinline__ float4 mul4(float s, float4 a) {
+  const float2 ss = make_float2(s, s);
+  const float2 lo = __fmul2_rn(ss, make_float2(a.x, a.y));
+  const float2 hi = __fmul2_rn(ss, make_float2(a.z, a.w));
+  return f4(lo.x, lo.y, hi.x, hi.y);
+}
+__device__ __forceinline__ float4 fma4(float s, float4 a, float4 b) {
+  const float2 ss = make_float2(s, s);
+  const float2 lo = __ffma2_rn(ss, make_float2(a.x, a.y), make_float2(b.x, b.y));
+  const float2 hi = __ffma2_rn(ss, make_float2(a.z, a.w), make_float2(b.z, b.w));
+  return f4(lo.x, lo.y, hi.x, hi.y);
+}
+__device__ __forceinline__ float4 shfl_up4n(float4 v, int d) {
+  return f4(__shfl_up_sync(0xffffffffu, v.x, d),
+            __shfl_up_sync(0xffffffffu, v.y, d),
+            __shfl_up_sync(0xffffffffu, v.z, d),
+            __shfl_up_sync(0xffffffffu, v.w, d));
+}
+__device__ __forceinline__ float4 shfl_up4(float4 v) {
+  return f4(__shfl_up_sync(0xffffffffu, v.x, 1),
+            __shfl_up_sync(0xffffffffu, v.y, 1),
+            __shfl_up_sync(0xffffffffu, v.z, 1),
+            __shfl_up_sync(0xffffffffu, v.w, 1));
+}
+
+// Decoded type: lattice shift n and level speeds c1, c2.
+struct Type {
+  int nx, ny, c1;
+};
+__device__ __forceinline__ Type decode_type(float t) {
+  const float c1 = floorf(t * (1.0f / 65536.0f));
+  const float r = __fmaf_rn(-65536.0f, c1, t);
+  const float hx = floorf(r * (1.0f / 256.0f));
+  const float hy = __fmaf_rn(-256.0f, hx, r);
+  return Type{(int)hx - 128, (int)hy - 128, (int)c1};
+}
+
+// Equilibrium of one window source (Section III.B with d0 = 0 and b1 = 4
+// on the square lattice): c1 (eq 26), level densities (eqs 24-25), the
+// level records' shared part (1, V_x, V_y, E_b) with E_b = |V|^2/2 + phi
+// (eqs 13-15), and the split of V (eq 23).  A source that emits nothing
+// (rho <= 0) has zero densities, V and E_b.
+struct SrcEq {
+  bool emits, clamp;
+  float c1, nxf, nyf, fx, fy, d1, d2, Vx, Vy, Eb;
+};
+__device__ __forceinline__ SrcEq source_eq(float4 m, float kq) {
+  SrcEq q;
+  const float rho = m.x;
+  const EqCore c = eq_core(rho, m.y, m.z, m.w, kq);
+  q.emits = rho > 0.0f;
+  q.clamp = q.emits && c.eraw < 0.0f;
+  q.c1 = c1_exact(c.X);
+  const float c2 = __fadd_rn(q.c1, 1.0f);
+  const float c2sq = __fmul_rn(c2, c2);
+  // d1 = (c2^2 rho - X rho) / (4 (c2^2 - c1^2)), d2 = rho / 4 - d1; the
+  // quotient rounded as one division would round it (Markstein's
+  // correction): a shared rounding of 1 / den would bias the packets'
+  // energy of every node alike
+  const float den = __fmul_rn(4.0f, __fmaf_rn(2.0f, q.c1, 1.0f));
+  const float num = __fmaf_rn(c2sq, rho, -__fmul_rn(c.X, rho));
+  const float d1 = div_markstein(num, den, rcp_nr(den));
+  q.d1 = q.emits ? d1 : 0.0f;
+  q.d2 = q.emits ? __fmaf_rn(0.25f, rho, -d1) : 0.0f;
+  // phi = e - X / 2 (eq 15 with D/2 (gamma - 1) e = X / 2)
+  const float phi = __fmaf_rn(-0.5f, c.X, fmaxf(c.eraw, 0.0f));
+  q.Eb = q.emits ? __fmaf_rn(0.5f, c.kin2, phi) : 0.0f;
+  q.Vx = q.emits ? c.Vx : 0.0f;
+  q.Vy = q.emits ? c.Vy : 0.0f;
+  split_f(q.Vx, q.nxf, q.fx);
+  split_f(q.Vy, q.nyf, q.fy);
+  return q;
+}
+
+__device__ __forceinline__ float type_id(const SrcEq& q) {
+  return q.emits ? __fmaf_rn(65536.0f, q.c1,
+                             __fmaf_rn(256.0f, __fadd_rn(q.nxf, 128.0f),
+                                       __fadd_rn(q.nyf, 128.0f)))
+                 : kNoType;
+}
+
+// Statistics of a window walk, per thread until reduce_stats combines them
+// over the block.
+struct WinStats {
+  float tmin, tmax, tnext;      // types: smallest, largest, next group
+  float nxmin, nymin, c1min;    // over emitting sources
+  unsigned clamps;              // clamped energies of owned nodes
+  bool any;                     // a source took part in the deposit
+};
+__device__ __forceinline__ WinStats stats_init() {
+  return WinStats{kNoType, -1.0f, kNoType, kNoType, kNoType, kNoType, 0u,
+                  false};
+}
+
+// Where a thread's column sits and how it reads its sources.
+struct Column {
+  int lane, wx, g, lx, sx, gx;
+  bool flipx, col_valid, col_own, store_col;
+};
+__device__ __forceinline__ Column column_of(const StepArgs& a, int x0, int R,
+                                            int TX, bool interior) {
+  Column c;
+  const int tid = threadIdx.x;
+  c.lane = tid & 31;
+  c.wx = (tid >> 5) & (NWX - 1);
+  c.g = tid / CW;
+  c.lx = c.lane + WSTEP * c.wx;
+  c.sx = x0 - R + c.lx;
+  c.col_valid = c.lx < WCOLS;
+  c.flipx = false;
+  c.gx = (interior || !c.col_valid) ? c.sx
+                                    : axis_src(a.bc_x, a.nx, c.sx, &c.flipx);
+  // deposits of column 0 are never read; the second warp's first two lanes
+  // repeat the first warp's last two columns
+  c.store_col = c.wx == 0 ? c.lane >= 1 : c.lane >= 2;
+  c.col_own = c.store_col && c.lx >= R && c.lx < R + TX && c.sx < a.nx;
+  return c;
+}
+
+// Moments of window source (column c, row ly); zero outside the window.
+__device__ __forceinline__ float4 load_src(const StepArgs& a, const Column& c,
+                                           int y0, int R, int ly,
+                                           bool interior) {
+  float4 m = f4(0.f, 0.f, 0.f, 0.f);
+  if (!c.col_valid || ly < 0 || ly >= WROWS) return m;
+  const int sy = y0 - R + ly;
+  bool flipy = false;
+  const int gy = interior ? sy : axis_src(a.bc_y, a.ny, sy, &flipy);
+  const long long i = (long long)gy * a.nx + c.gx;
+  m.x = __ldg(static_cast<const float*>(a.in[0]) + i);
+  m.y = __ldg(static_cast<const float*>(a.in[1]) + i);
+  m.z = __ldg(static_cast<const float*>(a.in[2]) + i);
+  m.w = __ldg(static_cast<const float*>(a.in[3]) + i);
+  if (c.flipx) m.y = -m.y;
+  if (flipy) m.z = -m.z;
+  return m;
+}
+
+// One-type walk: deposits the sources whose type is T (the corner weights
+// of eq 29 on offsets {0, 1}^2) and gathers the statistics of every source
+// (pass 0: types, minima, clamped energies of owned nodes).
+__device__ __forceinline__ void walk_one_type(
+    const StepArgs& a, float4* __restrict__ D1, float4* __restrict__ D2,
+    int x0, int y0, int R, int TX, int TY, bool interior, float T,
+    WinStats& st) {
+  const Column col = column_of(a, x0, R, TX, interior);
+  const int ly0 = SH * col.g;
+  const float kq = a.k.kq_f;
+  float4 pw01a1 = f4(0.f, 0.f, 0.f, 0.f), pw01a2 = pw01a1;
+  float4 pw11a1 = pw01a1, pw11a2 = pw01a1;
+  float4 nxt = load_src(a, col, y0, R, ly0, interior);
+#pragma unroll
+  for (int r = 0; r <= SH; ++r) {
+    const int ly = ly0 + r;
+    const float4 m = nxt;
+    if (r < SH) nxt = load_src(a, col, y0, R, ly + 1, interior);
+    const SrcEq q = source_eq(m, kq);
+    const float id = type_id(q);
+    const bool mine = id == T;
+    st.any |= mine;
+    st.tmin = fminf(st.tmin, id);
+    st.tmax = fmaxf(st.tmax, q.emits ? id : -1.0f);
+    if (q.emits) {
+      st.nxmin = fminf(st.nxmin, q.nxf);
+      st.nymin = fminf(st.nymin, q.nyf);
+      st.c1min = fminf(st.c1min, q.c1);
+    }
+    if (r >= 1 && q.clamp && col.col_own && ly >= R && ly < R + TY &&
+        y0 - R + ly < a.ny)
+      st.clamps += 1;
+    // level records L_v = d_v (1, V_x, V_y, E_b) of the sources of type T
+    const float4 v4 = f4(1.0f, q.Vx, q.Vy, q.Eb);
+    const float4 a1 = mul4(mine ? q.d1 : 0.0f, v4);
+    const float4 a2 = mul4(mine ? q.d2 : 0.0f, v4);
+    // corner weights (eq 29)
+    const float gx1 = __fsub_rn(1.0f, q.fx), gy1 = __fsub_rn(1.0f, q.fy);
+    const float w00 = __fmul_rn(gx1, gy1), w10 = __fmul_rn(q.fx, gy1);
+    const float w01 = __fmul_rn(gx1, q.fy), w11 = __fmul_rn(q.fx, q.fy);
+    // own-column part (this row's (0,0) corner and the row above's (0,1))
+    // and the part for the column to the right ((1,0) and (1,1))
+    const float4 t01 = fma4(w00, a1, pw01a1), t02 = fma4(w00, a2, pw01a2);
+    const float4 t11 = fma4(w10, a1, pw11a1), t12 = fma4(w10, a2, pw11a2);
+    pw01a1 = mul4(w01, a1);
+    pw01a2 = mul4(w01, a2);
+    pw11a1 = mul4(w11, a1);
+    pw11a2 = mul4(w11, a2);
+    const float4 u1 = shfl_up4(t11), u2 = shfl_up4(t12);
+    if (r >= 1 && col.store_col) {
+      D1[ly * DP + col.lx] = add4(t01, u1);
+      D2[ly * DP + col.lx] = add4(t02, u2);
+    }
+  }
+}
+
+// Group of an emitting source in the general walk: c1 relative to the
+// tile's smallest, and its shift n relative to the tile's smallest, in
+// blocks of two per axis.
+__device__ __forceinline__ float group_id(const SrcEq& q, float c1min,
+                                          float nxmin, float nymin) {
+  if (!q.emits) return kNoType;
+  const float gx = floorf(__fsub_rn(q.nxf, nxmin) * 0.5f);
+  const float gy = floorf(__fsub_rn(q.nyf, nymin) * 0.5f);
+  return __fmaf_rn(65536.0f, __fsub_rn(q.c1, c1min), __fmaf_rn(256.0f, gx, gy));
+}
+
+// Source of the general walk: level records and the hat weights over
+// offsets {0, 1, 2} per axis (dn = n - base in {0, 1}).
+struct GSrc {
+  float4 l1, l2;
+  float ax0, ax1, ax2, ay0, ay1, ay2;
+};
+
+// General walk for group G (c1 = c1min + Cc, n in {a, a+1} x {b, b+1} with
+// a = nxmin + 2 GX, b = nymin + 2 GY): deposits D(q) = sum over the
+// group's sources s and corners k of w_k(s) L(s) at q = s + (n - base) + k,
+// and finds the next group above G.
+__device__ __forceinline__ void walk_general(
+    const StepArgs& a, float4* __restrict__ D1, float4* __restrict__ D2,
+    int x0, int y0, int R, int TX, bool interior, float G, float c1min,
+    float nxmin, float nymin, WinStats& st) {
+  const Column col = column_of(a, x0, R, TX, interior);
+  const int ly0 = SH * col.g - 1;
+  const float kq = a.k.kq_f;
+  const float Gc = floorf(G * (1.0f / 65536.0f));
+  const float Gr = __fmaf_rn(-65536.0f, Gc, G);
+  const float GX = floorf(Gr * (1.0f / 256.0f));
+  const float GY = __fmaf_rn(-256.0f, GX, Gr);
+  const float bx = __fmaf_rn(2.0f, GX, nxmin), by = __fmaf_rn(2.0f, GY, nymin);
+  GSrc p1, p2;
+  p1.l1 = p1.l2 = f4(0.f, 0.f, 0.f, 0.f);
+  p1.ax0 = p1.ax1 = p1.ax2 = p1.ay0 = p1.ay1 = p1.ay2 = 0.0f;
+  p2 = p1;
+  float4 nxt = load_src(a, col, y0, R, ly0, interior);
+#pragma unroll
+  for (int r = 0; r <= SH + 1; ++r) {
+    const int ly = ly0 + r;
+    const float4 m = nxt;
+    if (r <= SH) nxt = load_src(a, col, y0, R, ly + 1, interior);
+    const SrcEq q = source_eq(m, kq);
+    const float gid = group_id(q, c1min, nxmin, nymin);
+    const bool mine = gid == G;
+    st.any |= mine;
+    st.tnext = fminf(st.tnext, gid > G ? gid : kNoType);
+    GSrc cur;
+    const float4 v4 = f4(1.0f, q.Vx, q.Vy, q.Eb);
+    cur.l1 = mul4(mine ? q.d1 : 0.0f, v4);
+    cur.l2 = mul4(mine ? q.d2 : 0.0f, v4);
+    // hat weights: dn = 0 -> (1 - f, f, 0), dn = 1 -> (0, 1 - f, f)
+    const bool sx1 = q.nxf != bx, sy1 = q.nyf != by;
+    const float gx1 = __fsub_rn(1.0f, q.fx), gy1 = __fsub_rn(1.0f, q.fy);
+    cur.ax0 = sx1 ? 0.0f : gx1;
+    cur.ax1 = sx1 ? gx1 : q.fx;
+    cur.ax2 = sx1 ? q.fx : 0.0f;
+    cur.ay0 = sy1 ? 0.0f : gy1;
+    cur.ay1 = sy1 ? gy1 : q.fy;
+    cur.ay2 = sy1 ? q.fy : 0.0f;
+    // own-column parts landing 0, 1, 2 columns to the right: rows t
+    // (offset 0), t - 1 (offset 1) and t - 2 (offset 2) of this column
+    float4 D1r, D2r;
+    {
+      const float w0 = __fmul_rn(cur.ax2, cur.ay0), w1 = __fmul_rn(p1.ax2, p1.ay1),
+                  w2 = __fmul_rn(p2.ax2, p2.ay2);
+      const float4 t1 = fma4(w0, cur.l1, fma4(w1, p1.l1, mul4(w2, p2.l1)));
+      const float4 t2 = fma4(w0, cur.l2, fma4(w1, p1.l2, mul4(w2, p2.l2)));
+      const float4 z = f4(0.f, 0.f, 0.f, 0.f);
+      const bool ok = col.lane >= 2;
+      const float4 s1 = shfl_up4n(t1, 2), s2 = shfl_up4n(t2, 2);
+      D1r = ok ? s1 : z;
+      D2r = ok ? s2 : z;
+    }
+    {
+      const float w0 = __fmul_rn(cur.ax1, cur.ay0), w1 = __fmul_rn(p1.ax1, p1.ay1),
+                  w2 = __fmul_rn(p2.ax1, p2.ay2);
+      const float4 t1 = fma4(w0, cur.l1, fma4(w1, p1.l1, mul4(w2, p2.l1)));
+      const float4 t2 = fma4(w0, cur.l2, fma4(w1, p1.l2, mul4(w2, p2.l2)));
+      const float4 s1 = shfl_up4(t1), s2 = shfl_up4(t2);
+      const float w0b = __fmul_rn(cur.ax0, cur.ay0), w1b = __fmul_rn(p1.ax0, p1.ay1),
+                  w2b = __fmul_rn(p2.ax0, p2.ay2);
+      const float4 o1 = fma4(w0b, cur.l1, fma4(w1b, p1.l1, mul4(w2b, p2.l1)));
+      const float4 o2 = fma4(w0b, cur.l2, fma4(w1b, p1.l2, mul4(w2b, p2.l2)));
+      D1r = add4(add4(o1, s1), D1r);
+      D2r = add4(add4(o2, s2), D2r);
+    }
+    p2 = p1;
+    p1 = cur;
+    if (r >= 2 && col.store_col) {
+      D1[ly * DP + col.lx] = D1r;
+      D2[ly * DP + col.lx] = D2r;
+    }
+  }
+}
+
+// Arrivals of the four packets of one level with speed c (template C >= 0;
+// C < 0: runtime c) at base position q of the deposits: +x, -x, +y, -y
+// packets read D at q - c, q + c, q - c DP, q + c DP.
+template <int C>
+__device__ __forceinline__ float4 level_arrivals(const float4* __restrict__ P,
+                                                 int q, int crt) {
+  const int c = C >= 0 ? C : crt;
+  const float cf = (float)c;
+  const float4 A = P[q - c], B = P[q + c];
+  const float4 Cu = P[q - c * DP], E = P[q + c * DP];
+  const float4 s = add4(add4(A, B), add4(Cu, E));
+  // mass; momentum + c (A - B) along x, + c (C - E) along y; energy
+  // + c (A.mx - B.mx) + c (C.my - E.my) + c^2/2 mass (eq 14 with the cross
+  // term 2 c'.V)
+  const float mx = __fmaf_rn(cf, __fsub_rn(A.x, B.x), s.y);
+  const float my = __fmaf_rn(cf, __fsub_rn(Cu.x, E.x), s.z);
+  float en = __fmaf_rn(cf, __fsub_rn(A.y, B.y), s.w);
+  en = __fmaf_rn(cf, __fsub_rn(Cu.z, E.z), en);
+  en = __fmaf_rn(0.5f * cf * cf, s.x, en);
+  return f4(s.x, mx, my, en);
+}
+
+template <int C1>
+__device__ __forceinline__ float4 gather_one(const float4* __restrict__ D1,
+                                             const float4* __restrict__ D2,
+                                             int q, int c1) {
+  const float4 y1 = level_arrivals<C1>(D1, q, c1);
+  const float4 y2 = level_arrivals<(C1 >= 0 ? C1 + 1 : -1)>(D2, q, c1 + 1);
+  return add4(y1, y2);
+}
+
+// Per-destination end of the step: write, reach and state check of the new
+// node, compensated partial totals.
+struct TileOut {
+  int reach;
+  bool bad;
+  Sum2 s[4];
+};
+
+__device__ __forceinline__ void finish_node(const StepArgs& a, bool valid,
+                                            long long o, float4 v,
+                                            TileOut& t) {
+  if (valid) {
+    static_cast<float*>(a.out[0])[o] = v.x;
+    static_cast<float*>(a.out[1])[o] = v.y;
+    static_cast<float*>(a.out[2])[o] = v.z;
+    static_cast<float*>(a.out[3])[o] = v.w;
+  } else {
+    v = f4(0.f, 0.f, 0.f, 0.f);
+  }
+  const EqCore c = eq_core(v.x, v.y, v.z, v.w, a.k.kq_f);
+  const float c1 = c1_exact(c.X);
+  const bool emits = v.x > 0.0f;
+  t.reach = max(t.reach, reach_of(emits, c, c1));
+  const bool finite_in = fabsf(v.x + v.y + v.z + v.w) <= 3.0e38f;
+  t.bad |= !finite_in || v.x < 0.0f ||
+           (v.x > 0.0f && v.x < 1.17549435e-38f) || !(c.X <= 1099511627776.0f);
+  if (a.do_cons) {
+    t.s[0] = sum2_add(t.s[0], v.x);
+    t.s[1] = sum2_add(t.s[1], v.y);
+    t.s[2] = sum2_add(t.s[2], v.z);
+    t.s[3] = sum2_add(t.s[3], v.w);
+  }
+}
+
+// Destinations of this thread: tile positions tid, tid + NTHR, ... in
+// row-major order over the TX x TY tile.
+struct DestWalk {
+  int dx, dy, sx, sy, TX;
+  __device__ __forceinline__ void init(int k, int tx) {
+    TX = tx;
+    dy = k / TX;
+    dx = k - dy * TX;
+    sy = NTHR / TX;
+    sx = NTHR - sy * TX;
+  }
+  __device__ __forceinline__ void next() {
+    dy += sy;
+    dx += sx;
+    if (dx >= TX) {
+      dx -= TX;
+      ++dy;
+    }
+  }
+};
+
+// Gather pass for type T over the tile: first pass writes, later passes
+// add to what the earlier passes wrote; the last pass finishes the nodes.
+template <int C1>
+__device__ __forceinline__ void gather_pass(const StepArgs& a,
+                                           const float4* __restrict__ D1,
+                                           const float4* __restrict__ D2,
+                                           int x0, int y0, int R, int TX,
+                                           int TY, Type ty, bool first,
+                                           bool last, TileOut& t) {
+  DestWalk w;
+  w.init(threadIdx.x, TX);
+  const int n = TX * TY;
+  const int iters = (n + NTHR - 1) / NTHR;
+  for (int it = 0; it < iters; ++it) {
+    const bool in_tile = w.dy < TY;
+    const int x = x0 + w.dx, y = y0 + w.dy;
+    const bool valid = in_tile && x < a.nx && y < a.ny;
+    float4 v = f4(0.f, 0.f, 0.f, 0.f);
+    const long long o = (long long)y * a.nx + x;
+    if (in_tile) {
+      const int q = (R + w.dy - ty.ny) * DP + (R + w.dx - ty.nx);
+      v = gather_one<C1>(D1, D2, q, ty.c1);
+    }
+    if (!first && valid) {
+      const float4 p = f4(static_cast<const float*>(a.out[0])[o],
+                          static_cast<const float*>(a.out[1])[o],
+                          static_cast<const float*>(a.out[2])[o],
+                          static_cast<const float*>(a.out[3])[o]);
+      v = add4(p, v);
+    }
+    if (last) {
+      finish_node(a, valid, o, v, t);
+    } else if (valid) {
+      static_cast<float*>(a.out[0])[o] = v.x;
+      static_cast<float*>(a.out[1])[o] = v.y;
+      static_cast<float*>(a.out[2])[o] = v.z;
+      static_cast<float*>(a.out[3])[o] = v.w;
+    }
+    w.next();
+  }
+}
+
+__device__ __forceinline__ void gather_dispatch(const StepArgs& a,
+                                                const float4* D1,
+                                                const float4* D2, int x0,
+                                                int y0, int R, int TX, int TY,
+                                                Type ty, bool first, bool last,
+                                                TileOut& t) {
+  switch (ty.c1) {
+    case 0: gather_pass<0>(a, D1, D2, x0, y0, R, TX, TY, ty, first, last, t); break;
+    case 1: gather_pass<1>(a, D1, D2, x0, y0, R, TX, TY, ty, first, last, t); break;
+    case 2: gather_pass<2>(a, D1, D2, x0, y0, R, TX, TY, ty, first, last, t); break;
+    default: gather_pass<-1>(a, D1, D2, x0, y0, R, TX, TY, ty, first, last, t); break;
+  }
+}
+
+// Finishes every destination of the tile without a gather: with zeros
+// (nothing landed) when first, else with what earlier passes wrote.  All
+// threads run the same number of iterations (c1_exact is warp-collective).
+__device__ __forceinline__ void finish_tile(const StepArgs& a, int x0, int y0,
+                                            int TX, int TY, bool first,
+                                            TileOut& t) {
+  const int n = TX * TY;
+  const int iters = (n + NTHR - 1) / NTHR;
+  for (int it = 0; it < iters; ++it) {
+    const int k = threadIdx.x + it * NTHR;
+    const int dy = k / TX, dx = k - dy * TX;
+    const int x = x0 + dx, y = y0 + dy;
+    const bool valid = k < n && x < a.nx && y < a.ny;
+    const long long o = (long long)y * a.nx + x;
+    float4 v = f4(0.f, 0.f, 0.f, 0.f);
+    if (valid && !first)
+      v = f4(static_cast<const float*>(a.out[0])[o],
+             static_cast<const float*>(a.out[1])[o],
+             static_cast<const float*>(a.out[2])[o],
+             static_cast<const float*>(a.out[3])[o]);
+    finish_node(a, valid, o, v, t);
+  }
+}
+
+// Every packet of a one-type walk (slack 0) or of a general walk's group
+// (slack 1: its base may lie one below its sources' shift) within reach R
+// reads deposits that lie in rows 1 .. 48 and columns 1 .. 61.
+__device__ __forceinline__ bool type_fits(Type ty, int R, int slack) {
+  const int c2 = ty.c1 + 1;
+  return ty.nx <= R - 1 - c2 && -ty.nx <= R - c2 + slack &&
+         ty.ny <= R - 1 - c2 && -ty.ny <= R - c2 + slack;
+}
+
+// Block reduction of the window statistics (all threads call it; it holds
+// the barrier that makes the deposits visible).  Minima are reduced on
+// non-negative bit patterns (n shifted by 128, -1 mapped to 0 for tmax).
+constexpr int NSTAT = 6;
+__device__ __forceinline__ void reduce_stats(WinStats& st, unsigned* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned v[NSTAT];
+  v[0] = __reduce_min_sync(0xffffffffu, __float_as_uint(st.tmin));
+  v[1] = __reduce_min_sync(0xffffffffu, __float_as_uint(st.tnext));
+  v[2] = __reduce_min_sync(0xffffffffu, __float_as_uint(st.nxmin + 128.0f));
+  v[3] = __reduce_min_sync(0xffffffffu, __float_as_uint(st.nymin + 128.0f));
+  v[4] = __reduce_min_sync(0xffffffffu, __float_as_uint(st.c1min));
+  // largest type + 1 (0: no emitting source); any = bit 31
+  const unsigned mx = __reduce_max_sync(
+      0xffffffffu, st.tmax < 0.0f ? 0u : __float_as_uint(st.tmax) + 1u);
+  const unsigned an = __any_sync(0xffffffffu, st.any) ? 0x80000000u : 0u;
+  v[5] = mx | an;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NSTAT; ++k) red[k * NWARP + warp] = v[k];
+  }
+  __syncthreads();
+  unsigned r[NSTAT] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu,
+                       0xffffffffu, 0u};
+#pragma unroll
+  for (int w = 0; w < NWARP; ++w) {
+#pragma unroll
+    for (int k = 0; k < NSTAT - 1; ++k) r[k] = min(r[k], red[k * NWARP + w]);
+    const unsigned t = red[(NSTAT - 1) * NWARP + w];
+    r[NSTAT - 1] = max(r[NSTAT - 1] & 0x7fffffffu, t & 0x7fffffffu) |
+                   ((r[NSTAT - 1] | t) & 0x80000000u);
+  }
+  st.tmin = __uint_as_float(r[0]);
+  st.tnext = __uint_as_float(r[1]);
+  st.nxmin = __uint_as_float(r[2]) - 128.0f;
+  st.nymin = __uint_as_float(r[3]) - 128.0f;
+  st.c1min = __uint_as_float(r[4]);
+  const unsigned m = r[5] & 0x7fffffffu;
+  st.tmax = m == 0 ? -1.0f : __uint_as_float(m - 1u);
+  st.any = (r[5] & 0x80000000u) != 0;
+}
+
+// The step: one block per tile of the reach the step runs with.  Blocks
+// beyond the tile count of that reach (the grid is sized for the largest
+// reach) only clear their partial totals.
+template <bool KAHAN>
+__global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
+  extern __shared__ __align__(16) float4 dsm[];
+  __shared__ unsigned red[NSTAT * NWARP];
+  __shared__ float2 red_sum[4][NWARP];
+  __shared__ int red_reach[NWARP];
+  __shared__ int red_bad[NWARP];
+  float4* D1 = dsm;
+  float4* D2 = dsm + PLANE;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b = blockIdx.x;
+  const int R0 = a.scr->reach;
+  const int R = R0 < 1 ? 1 : R0;
+  const int TX = tile_w(R), TY = tile_h(R);
+  const int tiles_x = (a.nx + TX - 1) / TX;
+  const bool over = R0 > a.r_cap || R0 > RMAX;
+  if (over || b >= tiles_x * ((a.ny + TY - 1) / TY)) {
+    if (over && tid == 0 && b == 0) atomicOr(&a.scr->flags, kFlagReach);
+    if (a.do_cons && tid < 4)
+      reinterpret_cast<float2*>(a.part)[(long long)b * 4 + tid] =
+          make_float2(0.f, 0.f);
+    return;
+  }
+  const int ty_i = b / tiles_x, tx_i = b - ty_i * tiles_x;
+  const int x0 = tx_i * TX, y0 = ty_i * TY;
+  const bool interior = x0 - R >= 0 && x0 - R + WCOLS <= a.nx &&
+                        y0 - R >= 0 && y0 - R + WROWS <= a.ny;
+
+  // guess: the type of the tile's central node (every thread forms it)
+  float T0;
+  {
+    const int cx = min(x0 + TX / 2, a.nx - 1), cy = min(y0 + TY / 2, a.ny - 1);
+    const long long i = (long long)cy * a.nx + cx;
+    const float4 m = f4(static_cast<const float*>(a.in[0])[i],
+                        static_cast<const float*>(a.in[1])[i],
+                        static_cast<const float*>(a.in[2])[i],
+                        static_cast<const float*>(a.in[3])[i]);
+    T0 = type_id(source_eq(m, a.k.kq_f));
+  }
+  WinStats st = stats_init();
+  walk_one_type(a, D1, D2, x0, y0, R, TX, TY, interior, T0, st);
+  {
+    const unsigned cl = __reduce_add_sync(0xffffffffu, st.clamps);
+    if (lane == 0 && cl) atomicAdd(&a.scr->eclamps, (unsigned long long)cl);
+  }
+  reduce_stats(st, red);  // includes the barrier after the deposits
+
+  TileOut to;
+  to.reach = 0;
+  to.bad = false;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) to.s[f] = Sum2{0.f, 0.f};
+  if (st.tmax < 0.0f) {
+    finish_tile(a, x0, y0, TX, TY, true, to);  // nothing lands
+  } else if (st.tmin == st.tmax && st.tmin == T0) {
+    // one type
+    const Type ty = decode_type(T0);
+    if (type_fits(ty, R, 0)) {
+      gather_dispatch(a, D1, D2, x0, y0, R, TX, TY, ty, true, true, to);
+    } else {
+      if (tid == 0) atomicOr(&a.scr->flags, kFlagReach);
+      finish_tile(a, x0, y0, TX, TY, true, to);
+    }
+  } else {
+    // several types: one general walk per group, ascending
+    const float c1min = st.c1min, nxmin = st.nxmin, nymin = st.nymin;
+    float G = 0.0f;  // (c1min, blocks (0, 0)); possibly empty
+    bool first = true;
+    while (true) {
+      __syncthreads();  // the previous gather is done with the deposits
+      WinStats s2 = stats_init();
+      walk_general(a, D1, D2, x0, y0, R, TX, interior, G, c1min,
+                   nxmin, nymin, s2);
+      reduce_stats(s2, red);
+      const bool last = !(s2.tnext < kNoType);
+      const float Gc = floorf(G * (1.0f / 65536.0f));
+      const float Gr = __fmaf_rn(-65536.0f, Gc, G);
+      const float GX = floorf(Gr * (1.0f / 256.0f));
+      const float GY = __fmaf_rn(-256.0f, GX, Gr);
+      const Type ty{(int)__fmaf_rn(2.0f, GX, nxmin),
+                    (int)__fmaf_rn(2.0f, GY, nymin), (int)(c1min + Gc)};
+      if (s2.any && type_fits(ty, R, 1)) {
+        gather_dispatch(a, D1, D2, x0, y0, R, TX, TY, ty, first, last, to);
+        first = false;
+      } else {
+        if (s2.any && tid == 0) atomicOr(&a.scr->flags, kFlagReach);
+        if (last) finish_tile(a, x0, y0, TX, TY, first, to);
+      }
+      if (last) break;
+      G = s2.tnext;
+    }
+  }
+
+  // block reductions: reach, bad state, totals
+  int r = __reduce_max_sync(0xffffffffu, to.reach);
+  const int bad = __any_sync(0xffffffffu, to.bad) ? 1 : 0;
+  if (a.do_cons) {
+    const Sum2 k = warp_sum2_fields(to.s, lane);
+    if ((lane & 7) == 0) red_sum[lane >> 3][warp] = make_float2(k.hi, k.lo);
+  }
+  if (lane == 0) {
+    red_reach[warp] = r;
+    red_bad[warp] = bad;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    int rb = lane < NWARP ? red_reach[lane] : 0;
+    rb = __reduce_max_sync(0xffffffffu, rb);
+    const int bb = __any_sync(0xffffffffu, lane < NWARP && red_bad[lane] != 0);
+    if (lane == 0) {
+      atomicMax(&a.scr->reach_next, rb);
+      if (bb) atomicOr(&a.scr->flags, kFlagState);
+    }
+    if (a.do_cons) {
+      static_assert(NWARP == 8, "one lane per (field, warp)");
+      const Sum2 s = combine_warps_f2<NWARP>(red_sum, lane);
+      if ((lane & 7) == 0)
+        reinterpret_cast<float2*>(a.part)[(long long)b * 4 + (lane >> 3)] =
+            make_float2(s.hi, s.lo);
+    }
+  }
+}
+
+// After each launch of step2d_ds (one block): the tiles' compensated
+// (hi, lo) partial totals summed in compensated FP32 in a fixed order and
+// converted to FP64 once per field, and the reach hand-off to the next step.
+// A launch that met a reach beyond its layout leaves the reach as it was,
+// so later steps report the same error.
+__global__ void __launch_bounds__(NTHR)
+    finalize2d(Scratch* scr, const double* __restrict__ part, int nblk,
+               int do_cons) {
+  __shared__ float2 red[4][NWARP];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (do_cons) {
+    const float2* p2 = reinterpret_cast<const float2*>(part);
+    Sum2 s4[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    for (int b = tid; b < nblk; b += NTHR) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const float2 v = p2[(long long)b * 4 + f];
+        s4[f] = sum2_add(s4[f], Sum2{v.x, v.y});
+      }
+    }
+    const Sum2 k = warp_sum2_fields(s4, lane);
+    if ((lane & 7) == 0) red[lane >> 3][warp] = make_float2(k.hi, k.lo);
+    __syncthreads();
+    if (warp == 0) {
+      const Sum2 t = combine_warps_f2<NWARP>(red, lane);
+      if ((lane & 7) == 0) scr->cons[lane >> 3] = (double)t.hi + (double)t.lo;
+    }
+  }
+  if (tid == 0) {
+    if (!(scr->flags & kFlagReach)) scr->reach = scr->reach_next;
+    scr->reach_next = 0;
+    scr->ticket = 0u;
+  }
+}
+
+}  // namespace ds
+}  // namespace lbm

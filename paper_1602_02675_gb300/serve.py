@@ -56,14 +56,13 @@ class Request:
 
 def bytes_needed(req: Request, precision: int) -> int:
     """Device bytes a solve holds while admitted: 2-D grids two moment sets
-    (4 fields), two sets of 24-byte equilibrium records (FP32) or one set of
-    248-byte source records over the grid padded by the reach limit 6 (FP64),
-    the FP64 readback staging (5 fields) and per-tile partials; 1-D tubes two
-    sets of 3 fields in the pool."""
+    (4 fields), in FP64 one set of 248-byte source records over the grid
+    padded by the reach limit 6, the FP64 readback staging (5 fields) and
+    per-tile partials; 1-D tubes two sets of 3 fields in the pool."""
     b = 8 if precision == L.F64 else 4
     n = req.nodes()
     if req.dim == 2:
-        rec = (2 * 24 * n if precision == L.F32
+        rec = (0 if precision == L.F32
                else 248 * (req.n + 12) * (req.ny + 12))
         return n * (2 * 4 * b + 5 * 8) + rec + (n // 256 + 1) * 32 + (1 << 20)
     return n * 2 * 3 * b

@@ -49,6 +49,81 @@ def riemann_l1_at_lambda(case, N, lam, t_end=0.2):
                         ph["p"])
 
 
+CYL_IN = (1.0, 0.0, 0.0, 1.0)
+CYL_OUT = (0.125, 0.0, 0.0, 0.1)
+
+
+def _as_fp32(st):
+    f = lambda a: a.astype("float32").astype("float64")
+    return O.State(f(st.rho), f(st.mx), f(st.my), f(st.rhoE))
+
+
+def cylinder_fp32_floor(n=64, checkpoints=(50, 100, 200, 400, 800)):
+    """The periodic cylinder (radius 0.4, Section V.C states) on an n x n
+    lattice, run twice by the oracle: in FP64, and in FP64 with the state
+    rounded to FP32 after every step.  Returns per checkpoint the mean
+    |difference| / range of the FP64 field, and the FP64 run's largest
+    departure from the x <-> y mirror symmetry of the problem."""
+    import numpy as np
+    P = O.Params(dim=2, nx=n, ny=n, bc_x=O.PERIODIC, bc_y=O.PERIODIC)
+    a = O.riemann_circle(P, 0, 1, 0, 0.5, 0.5, 0.4, CYL_IN, CYL_OUT, 1.0)
+    b = _as_fp32(a)
+    rows = []
+    for k in range(1, max(checkpoints) + 1):
+        a, _, _ = O.step(P, a)
+        b = _as_fp32(O.step(P, b)[0])
+        if k in checkpoints:
+            l1 = []
+            for f in ("rho", "mx", "my", "rhoE"):
+                x, y = getattr(a, f), getattr(b, f)
+                l1.append(float(np.mean(np.abs(x - y)) / (x.max() - x.min())))
+            r = a.rho.reshape(n, n)
+            rows.append((k, l1, float(np.max(np.abs(r - r.T)))))
+    return rows
+
+
+def write_cylinder_floor(path):
+    rows = cylinder_fp32_floor()
+    with open(path, "w") as f:
+        f.write("# The periodic cylinder (radius 0.4 about the centre, inside (1, 1),\n"
+                "# outside (0.125, 0.1), lambda = 1) on a 64 x 64 lattice: the FP64\n"
+                "# oracle against the same oracle with its state rounded to FP32 after\n"
+                "# every step.  mean |difference| / (max - min) of the FP64 field, and\n"
+                "# the FP64 run's largest |rho(x, y) - rho(y, x)|.  The square-lattice\n"
+                "# step amplifies round-off, so no FP32 arithmetic can stay within\n"
+                "# 1e-5 of FP64 here beyond about 200 steps.  Written by\n"
+                "# tests/golden/make_golden.py from oracle/ only.\n"
+                "# columns: step rho mx my rhoE fp64_mirror_asymmetry\n")
+        for k, l1, sym in rows:
+            f.write(f"{k} " + " ".join(f"{v:.6e}" for v in l1) + f" {sym:.6e}\n")
+
+
+def cylinder_state_hashes(n=128, steps=2000):
+    """SHA-256 of the bytes (little-endian FP64) of each lattice-unit field
+    of the periodic cylinder on an n x n lattice after `steps` oracle steps;
+    the GPU's FP64 path must reproduce them bit for bit."""
+    import hashlib
+    import numpy as np
+    P = O.Params(dim=2, nx=n, ny=n, bc_x=O.PERIODIC, bc_y=O.PERIODIC)
+    s = O.riemann_circle(P, 0, 1, 0, 0.5, 0.5, 0.4, CYL_IN, CYL_OUT, 1.0)
+    s, _ = O.run(P, s, steps)
+    return {f: hashlib.sha256(np.ascontiguousarray(getattr(s, f), "<f8")
+                              .tobytes()).hexdigest()
+            for f in ("rho", "mx", "my", "rhoE")}
+
+
+def write_cylinder_hashes(path, n=128, steps=2000):
+    h = cylinder_state_hashes(n, steps)
+    with open(path, "w") as f:
+        f.write("# SHA-256 of each field (lattice units, little-endian FP64, x fastest)\n"
+                f"# of the periodic cylinder on a {n} x {n} lattice after {steps} FP64\n"
+                "# oracle steps (radius 0.4 about the centre, inside (1, 1), outside\n"
+                "# (0.125, 0.1), lambda = 1).  Written by tests/golden/make_golden.py\n"
+                "# from oracle/ only.  columns: n steps field sha256\n")
+        for k in ("rho", "mx", "my", "rhoE"):
+            f.write(f"{n} {steps} {k} {h[k]}\n")
+
+
 def sod2d_row(nx=4096, t_end=0.2):
     """One row of the 2-D square-lattice Sod tube between reflecting walls
     (x-only data: every row of the 4096 x 512 tube is this row), physical
@@ -73,6 +148,8 @@ def write_sod2d_row(path):
 
 def main():
     here = os.path.dirname(os.path.abspath(__file__))
+    write_cylinder_floor(os.path.join(here, "cylinder_fp32_storage_floor.txt"))
+    write_cylinder_hashes(os.path.join(here, "cylinder128_fp64_2000_sha256.txt"))
     write_sod2d_row(os.path.join(here, "sod2d_row_4096_t0.2.txt"))
     out = os.path.join(here, "sod_l1_errors.txt")
     with open(out, "w") as f:

@@ -229,6 +229,45 @@ def test_cylinder_fp64_bitwise():
     _assert_bitwise(g, o, 2)
 
 
+def _golden_hashes(name):
+    import os
+    out = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            n, steps, f, h = line.split()
+            out[f] = (int(n), int(steps), h)
+    return out
+
+
+def test_cylinder_2000_steps_fp64_bitwise():
+    """The periodic cylinder over a whole 2000-step solve on a 128 x 128
+    lattice: the FP64 step reproduces the oracle's final state bit for bit
+    (SHA-256 of every field, stored by tests/golden/make_golden.py), although
+    the square-lattice step amplifies any round-off difference to O(1)
+    within a few hundred steps."""
+    import hashlib
+    want = _golden_hashes("cylinder128_fp64_2000_sha256.txt")
+    n, steps, _ = want["rho"]
+    riem = ((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1), 1, 0.5, 0.5, 0.4)
+    g = _gpu(2, n, n, L.PERIODIC, L.PERIODIC, riemann=riem, steps=steps)
+    for f in FIELDS:
+        h = hashlib.sha256(np.ascontiguousarray(g[f], "<f8").tobytes())
+        assert h.hexdigest() == want[f][2], f
+
+
+@pytest.mark.parametrize("kahan", [0, 1])
+def test_cylinder_fp32_early_steps_l1(kahan):
+    """FP32 against the oracle on the periodic cylinder (64 x 64) while the
+    oracle's own FP32-storage floor is below the bar (100 steps: ~7e-7,
+    tests/golden/cylinder_fp32_storage_floor.txt)."""
+    riem = ((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1), 1, 0.5, 0.5, 0.4)
+    g = _gpu(2, 64, 64, L.PERIODIC, L.PERIODIC, riemann=riem, steps=100,
+             precision=L.F32, kahan=kahan)
+    o = _oracle(2, 64, 64, O.PERIODIC, O.PERIODIC, riemann=riem, steps=100)
+    _assert_l1(g, o, 2)
+
+
 def test_lambda_not_one_fp64_bitwise():
     """Section V.C tube on 4096 nodes: 820 steps, lambda = 0.99902..."""
     nx = 4096

@@ -28,6 +28,8 @@ def _close(a, b, prec):
 @pytest.mark.parametrize("dim,prec,shape,bcs", [
     (1, L.F64, (1000, 1), (L.TRANSMISSIVE, 0)),
     (1, L.F32, (777, 1), (L.PERIODIC, 0)),
+    # long enough for the 256-node tiles of the 1-D kernel (reach limit 64)
+    (1, L.F64, (80000, 1), (L.TRANSMISSIVE, 0)),
     (2, L.F64, (70, 21), (L.TRANSMISSIVE, L.REFLECTING)),
     (2, L.F32, (96, 40), (L.PERIODIC, L.PERIODIC)),
 ])
@@ -80,3 +82,37 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
         L.lbm_step_noalloc(desc, fake, fake)
     assert e.value.status == L.EINVAL
     assert "at most" in str(e.value)
+
+
+@pytest.mark.parametrize("dim,prec", [(2, L.F32), (2, L.F64), (1, L.F64)])
+def test_noalloc_reach_beyond_limit_reports_and_leaves_out(dim, prec):
+    """A state whose migration reach exceeds the limit (2-D 6, 1-D 64): the
+    step does not run, flags carries LBM_EREACH (bit 1), out keeps what it
+    held and totals stay zero.  The kernel only returns early here."""
+    import torch
+    nx, ny = (48, 16) if dim == 2 else (300, 1)
+    n = nx * ny
+    dt = torch.float64 if prec == L.F64 else torch.float32
+    V = 6.0 if dim == 2 else 70.0       # lattice speed: reach > the limit
+    rho = torch.ones(n, dtype=dt, device="cuda")
+    mx = torch.full((n,), V, dtype=dt, device="cuda")
+    my = torch.zeros(n, dtype=dt, device="cuda") if dim == 2 else None
+    rhoE = torch.full((n,), 1.0 / 0.4 + 0.5 * V * V, dtype=dt, device="cuda")
+    outs = [torch.full((n,), 7.0, dtype=dt, device="cuda")
+            if (f != "my" or dim == 2) else None for f in FIELDS]
+    totals = torch.full((4,), 5.0, dtype=torch.float64, device="cuda")
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    reach = torch.zeros(1, dtype=torch.int32, device="cuda")
+    desc = L.lbm_noalloc_desc(dim, prec, L.PERIODIC, L.PERIODIC, nx, ny,
+                              1.4, 0.5 if dim == 1 else 0.0)
+    addr = lambda ts: [t.data_ptr() if t is not None else 0 for t in ts]
+    L.lbm_step_noalloc(desc, addr([rho, mx, my, rhoE]), addr(outs),
+                       totals=totals.data_ptr(), reach=reach.data_ptr(),
+                       flags=flags.data_ptr())
+    torch.cuda.synchronize()
+    assert int(flags.item()) == 2
+    for t in outs:
+        if t is not None:
+            assert bool(torch.all(t == 7.0))
+    assert bool(torch.all(totals == 0.0))
+    assert int(reach.item()) > (6 if dim == 2 else 64)
