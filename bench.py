@@ -569,25 +569,33 @@ def l1_vs_oracle(L) -> dict:
     return out
 
 
-def run_tubes(args):
+def run_tubes(args, rank=0, world=1):
     """Batched 1-D tubes (4096 seeded tubes, 256..16384 nodes, pressure
     ratio 2..100, density ratio 1..10, at rest, t = 0.2): solves/s of the
     batched FP32 path (one persistent launch per step, CUDA graphs) against
-    the plain FP64 path that solves one tube at a time through a handle."""
+    the plain FP64 path that solves one tube at a time through a handle.
+    With several ranks the tubes are split between them by work (each rank
+    one batch of its tubes, no exchange), the time is the slowest rank's."""
     import torch
     from paper_1602_02675_gb300 import inputs as I
     from paper_1602_02675_gb300 import lbm as L
+    from paper_1602_02675_gb300 import partition as Pt
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     specs = I.tubes_batch(args.tubes)
+    work = [t.n * t.steps_and_lambda(T_END)[0] for t in specs]
+    mine = Pt.assign(work, world)[rank]
     tubes, nus = [], 0
-    for t in specs:
+    for j in mine:
+        t = specs[j]
         ns, lam = t.steps_and_lambda(T_END)
         tubes.append(L.make_tube(t.n, ns, lam / t.n, t.left, t.right))
-        nus += t.n * ns
+    nus = sum(work)
     stream = torch.cuda.Stream()
     times = []
     for rep in range(1 + args.batch_reps):
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         t0 = time.perf_counter()
         with L.Batch(tubes, precision=L.F32, kahan=1,
                      stream=stream.cuda_stream) as b:   # tunes the tile
@@ -597,7 +605,7 @@ def run_tubes(args):
         dt = time.perf_counter() - t0
         if rep > 0:
             times.append(dt)
-    tb = statistics.median(times)
+    tb = max_over_ranks([statistics.median(times)], world, "cuda")[0]
     # plain FP64 one tube at a time, seeded subsample
     rng = __import__("random").Random(20260)
     sub = rng.sample(range(len(specs)), min(args.seq_tubes, len(specs)))
@@ -623,6 +631,10 @@ def run_tubes(args):
     return {
         "metric": "solves/s", "value": solves_b, "unit": "solves/s",
         "workload": f"tubes_batch_{len(specs)}", "dtype": "f32",
+        "n_gpus": world,
+        "scaling": "strong" if world > 1 else None,
+        "partition": ("tubes split by work between ranks, one batch per "
+                      "rank, no exchange" if world > 1 else None),
         "batched": {"solves_per_s": solves_b, "node_updates_per_s": nus / tb,
                     "wall_s": tb, "node_updates": nus, "tubes": len(specs),
                     "tile_tuning": tuning,
@@ -837,7 +849,15 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.workload == "tubes":
-        print(json.dumps(run_tubes(args)))
+        if world > 1:
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            torch.distributed.init_process_group("nccl")
+        line = run_tubes(args, rank, world)
+        if rank == 0:
+            print(json.dumps(line))
+        if world > 1:
+            torch.distributed.destroy_process_group()
         return
     if args.workload == "serve":
         print(json.dumps(run_serve(args)))

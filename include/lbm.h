@@ -161,6 +161,17 @@ lbm_status lbm_moments(lbm_handle* h, double* rho, double* mx, double* my,
    (eq 22 with eqs 16-18).  Waits for all queued work. */
 lbm_status lbm_conservation(lbm_handle* h, double out[4]);
 
+/* The totals the step kernel itself formed (cons_every > 0) at the last
+   step that summed them, physical units, same order as lbm_conservation
+   (or what a later lbm_conservation computed); zeros if nothing has summed
+   them since the state was set.  The FP32
+   kernels sum in compensated FP32 (pairs of floats carried through every
+   partial) and convert to FP64 once per field; the FP64 kernels sum in
+   FP64.  Waits for all queued work.  (The paper has no counterpart: this
+   reads what a10 of the step produced, without another pass over the
+   state.) */
+lbm_status lbm_last_totals(lbm_handle* h, double out[4]);
+
 /* Migration reach R the next step will use (lattice cells): the maximum over
    nodes of floor(|V_a|) + 1 + c2 (eq 26), computed conservatively.  Waits. */
 lbm_status lbm_reach(lbm_handle* h, int32_t* reach);
@@ -367,6 +378,23 @@ lbm_status lbm_step_noalloc(const lbm_noalloc_desc* d, const void* const in[4],
  * or timing call fails.
  */
 lbm_status lbm_measure_fma_peak(int32_t precision, double* flops_per_s,
+                                void* stream);
+
+/* ---- diagnostics: FP32 reciprocal and quotient of the FP32 kernels -----
+ * The paper has no counterpart: the FP32 kernels form 1/rho from the
+ * hardware reciprocal estimate with one Newton-Raphson step and the level
+ * densities' quotient by 4 (2 c1 + 1) (eqs 24-25) with Markstein's
+ * correction.  This measures both against CUDA's correctly rounded division
+ * on n inputs from a counter-based generator (SplitMix64, stream `seed`):
+ * x = m 2^e with e in [-30, 30] for the reciprocal, numerators m 2^e with e
+ * in [-20, 20] over the denominators 4 (2 c + 1), c = 0 .. 15, for the
+ * quotient.  worst_ulp[0] and worst_ulp[1] receive the largest distances in
+ * units in the last place.  Runs on the current device and the given
+ * stream (NULL = default) and synchronizes it; allocates nothing (its two
+ * result words are a file-scope device array).  LBM_EINVAL for n < 0 or a
+ * NULL pointer, LBM_ECUDA if a launch or copy fails.
+ */
+lbm_status lbm_check_fp32_arith(int64_t n, uint64_t seed, double worst_ulp[2],
                                 void* stream);
 
 #ifdef __cplusplus

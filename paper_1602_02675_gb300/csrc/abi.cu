@@ -377,6 +377,24 @@ lbm_status lbm_conservation(lbm_handle* h, double out[4]) {
   return LBM_OK;
 }
 
+lbm_status lbm_last_totals(lbm_handle* h, double out[4]) {
+  lbm_status st = check_usable(h);
+  if (st != LBM_OK) return st;
+  if (!out) return fail(h, LBM_EINVAL, "lbm_last_totals: NULL out");
+  st = check_flags(h);
+  if (st != LBM_OK) return st;
+  Scratch sc;
+  LBM_CUDA(h, cudaMemcpyAsync(&sc, h->scr, sizeof(Scratch),
+                              cudaMemcpyDeviceToHost, h->stream),
+           "copy totals");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
+  out[0] = sc.cons[0];
+  out[1] = sc.cons[1] / h->lambda;
+  out[2] = sc.cons[2] / h->lambda;
+  out[3] = sc.cons[3] / (h->lambda * h->lambda);
+  return LBM_OK;
+}
+
 lbm_status lbm_reach(lbm_handle* h, int32_t* reach) {
   lbm_status st = check_usable(h);
   if (st != LBM_OK) return st;

@@ -1,6 +1,8 @@
 // Initial states, unit conversion at the host boundary, reach seeding and
 // FP64 totals.  Compiled with -fmad=false like the FP64 step, so the unit
 // conversions round exactly as their formulas are written.
+#include <atomic>
+
 #include "step_kernel.cuh"
 
 namespace lbm {
@@ -14,6 +16,25 @@ cudaError_t launch_step_f64(int dim, const StepArgs& a, size_t smem,
 cudaError_t launch_step_f32(int dim, const StepArgs& a, size_t smem,
                             cudaStream_t s);
 
+int device_sm_count() {
+  static std::atomic<int> cached[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 1;
+  }
+  int v = cached[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+          cudaSuccess ||
+      v < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  cached[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
 size_t step_smem_bytes(int dim, bool f64, int r_cap) {
   return f64 ? step_smem_f64(dim, r_cap) : step_smem_f32(dim, r_cap);
 }
@@ -25,7 +46,7 @@ cudaError_t step_prepare(int dim, bool f64, size_t smem) {
 long long step_blocks(int dim, int nx, int ny) {
   const long long X = nx, Y = ny;
   if (dim == 1) {
-    const long long tw = step_tile_1d(nx);
+    const long long tw = step_tile_1d(nx, device_sm_count());
     return (X + tw - 1) / tw;
   }
   return ((X + TileShape<2>::TX - 1) / TileShape<2>::TX) *
@@ -82,7 +103,7 @@ __global__ void init_kernel(const InitArgs a) {
 cudaError_t launch_init(bool f64, const InitArgs& a, cudaStream_t s) {
   long long n = (long long)a.nx * a.ny;
   int blocks = (int)((n + 255) / 256);
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > device_sm_count() * 32) blocks = device_sm_count() * 32;
   if (f64)
     init_kernel<double><<<blocks, 256, 0, s>>>(a);
   else
@@ -119,7 +140,7 @@ cudaError_t launch_from_host_layout(bool f64, int kind, int dim,
                                     int64_t n, double lambda, double gamma,
                                     cudaStream_t s) {
   int blocks = (int)((n + 255) / 256);
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > device_sm_count() * 32) blocks = device_sm_count() * 32;
   if (f64)
     from_host_kernel<double><<<blocks, 256, 0, s>>>(
         kind, dim, staging, (double*)f[0], (double*)f[1], (double*)f[2],
@@ -157,7 +178,7 @@ cudaError_t launch_to_host_layout(bool f64, int dim, const void* const f[4],
                                   double* staging, int64_t n, double lambda,
                                   double gamma, cudaStream_t s) {
   int blocks = (int)((n + 255) / 256);
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > device_sm_count() * 32) blocks = device_sm_count() * 32;
   if (f64)
     to_host_kernel<double><<<blocks, 256, 0, s>>>(
         dim, (const double*)f[0], (const double*)f[1], (const double*)f[2],
@@ -196,7 +217,7 @@ cudaError_t launch_reach(bool f64, int dim, const void* const f[4], int64_t n,
   cudaError_t e = cudaMemsetAsync(&scr->reach, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   int blocks = (int)((n + 255) / 256);
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
   if (f64)
     reach_kernel<double><<<blocks, 256, 0, s>>>(
         dim, (const double*)f[0], (const double*)f[1], (const double*)f[2],
@@ -214,7 +235,8 @@ constexpr int kTotThreads = 256;
 
 int totals_blocks(int64_t n) {
   long long b = (n + kTotThreads - 1) / kTotThreads;
-  return (int)(b < 152 * 8 ? (b < 1 ? 1 : b) : 152 * 8);
+  const long long cap = 8LL * device_sm_count();
+  return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
 template <typename T>

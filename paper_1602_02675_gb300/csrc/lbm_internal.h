@@ -46,7 +46,8 @@ struct StepArgs {
   int nx, ny;
   int bc_x, bc_y;
   int r_cap;          // largest reach the launch's shared memory holds
-  int kahan;          // F32: compensated summation of row-pair sums
+  int kahan;          // F32: compensated summation of the arrivals
+  int exact_order = 0;  // F32 2-D: step with the exact-order kernel
   int do_cons;        // this launch also sums FP64 totals
   int nblocks;
   EqConst k;
@@ -64,6 +65,10 @@ struct StepArgs {
 inline size_t src_bytes(int nx, int ny, int r_cap, size_t esize) {
   return (size_t)(nx + 2 * r_cap) * (size_t)(ny + 2 * r_cap) * (30 * esize + 8);
 }
+
+// Multiprocessors of the current device (cached per device; 1 if the
+// query fails, which only makes grids smaller).
+int device_sm_count();
 
 // Launch helpers (step kernels).
 size_t step_smem_bytes(int dim, bool f64, int r_cap);

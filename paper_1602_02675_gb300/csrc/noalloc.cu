@@ -200,6 +200,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_noalloc_desc* d,
   a.bc_y = d->dim == 2 ? d->bc_y : 0;
   a.r_cap = r_cap;
   a.kahan = 1;
+  a.exact_order = 1;
   a.do_cons = totals ? 1 : 0;
   a.nblocks = tiles;
   a.k = k;

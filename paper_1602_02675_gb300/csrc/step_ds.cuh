@@ -68,14 +68,19 @@ constexpr int WROWS = NG * SH;            // source rows 0 .. 47
 constexpr int NTHR = CW * NG;             // 256
 constexpr int NWARP = NTHR / 32;
 constexpr int RMAX = 6;                   // largest reach of this layout
-constexpr int DP = CW;                    // deposit row pitch (positions)
+constexpr int PF = 3;                     // rows loaded ahead of the walk
+constexpr int DP = DCOLS;                 // deposit row pitch (positions)
 constexpr int PLANE = DP * (WROWS + 1);   // deposit rows 1 .. 48
+// Each walking thread's ring of source moments in flight: PF rows of its
+// column, 4 fields, copied asynchronously (cp.async) so that the loads are
+// issued PF rows before they are needed and hold no registers meanwhile.
+constexpr int RING = PF * 4 * NTHR;       // floats
 // Type ids: c1 * 65536 + (n_x + 128) * 256 + (n_y + 128), held exactly in
 // a float; sources that emit nothing have no type.
 constexpr float kNoType = 16777216.0f;
 
 __host__ __device__ constexpr size_t smem_bytes() {
-  return (size_t)2 * PLANE * sizeof(float4);
+  return (size_t)2 * PLANE * sizeof(float4) + (size_t)RING * sizeof(float);
 }
 __host__ __device__ inline int tile_w(int R) { return WCOLS - 2 * R; }
 __host__ __device__ inline int tile_h(int R) { return WROWS - 2 * R; }
@@ -267,6 +272,69 @@ __device__ __forceinline__ Column column_of(const StepArgs& a, int x0, int R,
   return c;
 }
 
+// 4-byte asynchronous global -> shared copy; src_bytes 0 fills zero.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src,
+                                          bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d),
+               "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// The walking thread's ring: slot k holds the 4 fields of one source row
+// of its column, field f at ring[(k * 4 + f) * NTHR + tid] (consecutive
+// threads at consecutive words).  Sources outside the window arrive as
+// zeros; mirrored momentum components are negated when read.
+struct SrcRing {
+  float* base;
+  const float* f[4];
+  int stride_rows;
+  __device__ __forceinline__ void issue(const StepArgs& a, const Column& c,
+                                        int y0, int R, int ly, int slot,
+                                        bool interior) {
+    const bool valid = c.col_valid && ly >= 0 && ly < WROWS;
+    long long i = 0;
+    if (valid) {
+      const int sy = y0 - R + ly;
+      bool flipy = false;
+      const int gy = interior ? sy : axis_src(a.bc_y, a.ny, sy, &flipy);
+      i = (long long)gy * a.nx + c.gx;
+    }
+    float* d = base + slot * 4 * NTHR + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cp_async4(d + k * NTHR, f[k] + i, valid);
+    cp_async_commit();
+  }
+  __device__ __forceinline__ float4 take(const StepArgs& a, const Column& c,
+                                         int y0, int R, int ly, int slot,
+                                         bool interior) const {
+    const float* d = base + slot * 4 * NTHR + threadIdx.x;
+    float4 m = f4(d[0], d[NTHR], d[2 * NTHR], d[3 * NTHR]);
+    if (c.flipx) m.y = -m.y;
+    if (!interior && ly >= 0 && ly < WROWS) {
+      bool flipy = false;
+      axis_src(a.bc_y, a.ny, y0 - R + ly, &flipy);
+      if (flipy) m.z = -m.z;
+    }
+    return m;
+  }
+};
+__device__ __forceinline__ SrcRing ring_of(const StepArgs& a, float* base) {
+  SrcRing r;
+  r.base = base;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r.f[k] = static_cast<const float*>(a.in[k]);
+  r.stride_rows = 0;
+  return r;
+}
+
 // Moments of window source (column c, row ly); zero outside the window.
 __device__ __forceinline__ float4 load_src(const StepArgs& a, const Column& c,
                                            int y0, int R, int ly,
@@ -291,20 +359,52 @@ __device__ __forceinline__ float4 load_src(const StepArgs& a, const Column& c,
 // (pass 0: types, minima, clamped energies of owned nodes).
 __device__ __forceinline__ void walk_one_type(
     const StepArgs& a, float4* __restrict__ D1, float4* __restrict__ D2,
-    int x0, int y0, int R, int TX, int TY, bool interior, float T,
-    WinStats& st) {
+    float* rbase, int x0, int y0, int R, int TX, int TY, bool interior,
+    float Tin, const float4* cm, float* T0p, WinStats& st) {
   const Column col = column_of(a, x0, R, TX, interior);
   const int ly0 = SH * col.g;
   const float kq = a.k.kq_f;
+  // rows r of this walk whose node the tile owns (its energy clamps are
+  // counted here); none if the column is not owned
+  const int own_lo = max(1, R - ly0);
+  const int own_hi = col.col_own
+                         ? min(min(SH, R + TY - 1 - ly0), a.ny - 1 - (y0 - R) - ly0)
+                         : -1;
   float4 pw01a1 = f4(0.f, 0.f, 0.f, 0.f), pw01a2 = pw01a1;
   float4 pw11a1 = pw01a1, pw11a2 = pw01a1;
-  float4 nxt = load_src(a, col, y0, R, ly0, interior);
+  // rows PF ahead are in flight (asynchronous copies into the thread's
+  // ring) while a row is formed: global-load latency is the walk's main
+  // stall
+  SrcRing ring = ring_of(a, rbase);
 #pragma unroll
+  for (int k = 0; k < PF; ++k) ring.issue(a, col, y0, R, ly0 + k, k, interior);
+  if (T0p) {
+    // the tile's guess type, from the central node loaded by the caller
+    *T0p = type_id(source_eq(*cm, kq));
+  }
+  const float T = T0p ? *T0p : Tin;
+  // Software pipeline: the equilibrium of row r + 1 is formed while row r
+  // is deposited (two independent dependency chains per thread).
+  // (a rolled loop: the walk's code stays small in the instruction cache)
+  auto row_eq = [&](int r, int slot) {
+    if (r + PF - 1 <= SH)
+      cp_async_wait<PF - 1>();
+    else
+      cp_async_wait<0>();
+    const float4 m = ring.take(a, col, y0, R, ly0 + r, slot, interior);
+    if (r + PF <= SH) ring.issue(a, col, y0, R, ly0 + r + PF, slot, interior);
+    return source_eq(m, kq);
+  };
+  SrcEq qn = row_eq(0, 0);
+  int slot = 1;
+#pragma unroll 1
   for (int r = 0; r <= SH; ++r) {
     const int ly = ly0 + r;
-    const float4 m = nxt;
-    if (r < SH) nxt = load_src(a, col, y0, R, ly + 1, interior);
-    const SrcEq q = source_eq(m, kq);
+    const SrcEq q = qn;
+    if (r < SH) {
+      qn = row_eq(r + 1, slot);
+      slot = slot + 1 == PF ? 0 : slot + 1;
+    }
     const float id = type_id(q);
     const bool mine = id == T;
     st.any |= mine;
@@ -315,9 +415,7 @@ __device__ __forceinline__ void walk_one_type(
       st.nymin = fminf(st.nymin, q.nyf);
       st.c1min = fminf(st.c1min, q.c1);
     }
-    if (r >= 1 && q.clamp && col.col_own && ly >= R && ly < R + TY &&
-        y0 - R + ly < a.ny)
-      st.clamps += 1;
+    if (q.clamp && r >= own_lo && r <= own_hi) st.clamps += 1;
     // level records L_v = d_v (1, V_x, V_y, E_b) of the sources of type T
     const float4 v4 = f4(1.0f, q.Vx, q.Vy, q.Eb);
     const float4 a1 = mul4(mine ? q.d1 : 0.0f, v4);
@@ -366,7 +464,8 @@ struct GSrc {
 // and finds the next group above G.
 __device__ __forceinline__ void walk_general(
     const StepArgs& a, float4* __restrict__ D1, float4* __restrict__ D2,
-    int x0, int y0, int R, int TX, bool interior, float G, float c1min,
+    float* rbase, int x0, int y0, int R, int TX, bool interior, float G,
+    float c1min,
     float nxmin, float nymin, WinStats& st) {
   const Column col = column_of(a, x0, R, TX, interior);
   const int ly0 = SH * col.g - 1;
@@ -380,13 +479,29 @@ __device__ __forceinline__ void walk_general(
   p1.l1 = p1.l2 = f4(0.f, 0.f, 0.f, 0.f);
   p1.ax0 = p1.ax1 = p1.ax2 = p1.ay0 = p1.ay1 = p1.ay2 = 0.0f;
   p2 = p1;
-  float4 nxt = load_src(a, col, y0, R, ly0, interior);
+  SrcRing ring = ring_of(a, rbase);
 #pragma unroll
-  for (int r = 0; r <= SH + 1; ++r) {
+  for (int k = 0; k < PF; ++k) ring.issue(a, col, y0, R, ly0 + k, k, interior);
+  constexpr int LAST = SH + 1;
+  auto row_eq = [&](int r, int slot) {
+    if (r + PF - 1 <= LAST)
+      cp_async_wait<PF - 1>();
+    else
+      cp_async_wait<0>();
+    const float4 m = ring.take(a, col, y0, R, ly0 + r, slot, interior);
+    if (r + PF <= LAST) ring.issue(a, col, y0, R, ly0 + r + PF, slot, interior);
+    return source_eq(m, kq);
+  };
+  SrcEq qn = row_eq(0, 0);
+  int slot = 1;
+#pragma unroll 1
+  for (int r = 0; r <= LAST; ++r) {
     const int ly = ly0 + r;
-    const float4 m = nxt;
-    if (r <= SH) nxt = load_src(a, col, y0, R, ly + 1, interior);
-    const SrcEq q = source_eq(m, kq);
+    const SrcEq q = qn;
+    if (r < LAST) {
+      qn = row_eq(r + 1, slot);
+      slot = slot + 1 == PF ? 0 : slot + 1;
+    }
     const float gid = group_id(q, c1min, nxmin, nymin);
     const bool mine = gid == G;
     st.any |= mine;
@@ -462,21 +577,70 @@ __device__ __forceinline__ float4 level_arrivals(const float4* __restrict__ P,
   return f4(s.x, mx, my, en);
 }
 
-template <int C1>
+// a - b in one packed instruction (exact: a fused multiply by -1).
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+// Two compensated partial sums at once (Knuth's TwoSum on float pairs, as
+// sum2_add does for one).
+struct Sum2x2 {
+  float2 hi, lo;
+};
+__device__ __forceinline__ void sum2x2_add(Sum2x2& a, float2 v) {
+  const float2 s = __fadd2_rn(a.hi, v);
+  const float2 bb = sub2(s, a.hi);
+  const float2 e = __fadd2_rn(sub2(a.hi, sub2(s, bb)), sub2(v, bb));
+  a.hi = s;
+  a.lo = __fadd2_rn(a.lo, e);
+}
+
+// Compensated arrivals of one level: the four packets' fields (eqs 12-14
+// from the deposited level record, the cross term 2 c'.V included), each
+// added into the destination's (hi, lo) sums by TwoSum.
+template <int C>
+__device__ __forceinline__ void level_arrivals_comp(
+    const float4* __restrict__ P, int q, int crt, Sum2x2& s01, Sum2x2& s23) {
+  const int c = C >= 0 ? C : crt;
+  const float cf = (float)c, k2 = 0.5f * cf * cf;
+  const float4 A = P[q - c], B = P[q + c];
+  const float4 Cu = P[q - c * DP], E = P[q + c * DP];
+  // +x and -x packets: momentum +-c d along x, energy +-c (d V_x) + c^2/2 d
+  sum2x2_add(s01, make_float2(A.x, __fmaf_rn(cf, A.x, A.y)));
+  sum2x2_add(s23, make_float2(A.z, __fmaf_rn(cf, A.y, __fmaf_rn(k2, A.x, A.w))));
+  sum2x2_add(s01, make_float2(B.x, __fmaf_rn(-cf, B.x, B.y)));
+  sum2x2_add(s23, make_float2(B.z, __fmaf_rn(-cf, B.y, __fmaf_rn(k2, B.x, B.w))));
+  // +y and -y packets
+  sum2x2_add(s01, make_float2(Cu.x, Cu.y));
+  sum2x2_add(s23, make_float2(__fmaf_rn(cf, Cu.x, Cu.z),
+                              __fmaf_rn(cf, Cu.z, __fmaf_rn(k2, Cu.x, Cu.w))));
+  sum2x2_add(s01, make_float2(E.x, E.y));
+  sum2x2_add(s23, make_float2(__fmaf_rn(-cf, E.x, E.z),
+                              __fmaf_rn(-cf, E.z, __fmaf_rn(k2, E.x, E.w))));
+}
+
+template <int C1, bool KAHAN>
 __device__ __forceinline__ float4 gather_one(const float4* __restrict__ D1,
                                              const float4* __restrict__ D2,
                                              int q, int c1) {
-  const float4 y1 = level_arrivals<C1>(D1, q, c1);
-  const float4 y2 = level_arrivals<(C1 >= 0 ? C1 + 1 : -1)>(D2, q, c1 + 1);
-  return add4(y1, y2);
+  if constexpr (KAHAN) {
+    Sum2x2 s01{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, s23 = s01;
+    level_arrivals_comp<C1>(D1, q, c1, s01, s23);
+    level_arrivals_comp<(C1 >= 0 ? C1 + 1 : -1)>(D2, q, c1 + 1, s01, s23);
+    const float2 a = __fadd2_rn(s01.hi, s01.lo), b = __fadd2_rn(s23.hi, s23.lo);
+    return f4(a.x, a.y, b.x, b.y);
+  } else {
+    const float4 y1 = level_arrivals<C1>(D1, q, c1);
+    const float4 y2 = level_arrivals<(C1 >= 0 ? C1 + 1 : -1)>(D2, q, c1 + 1);
+    return add4(y1, y2);
+  }
 }
 
 // Per-destination end of the step: write, reach and state check of the new
-// node, compensated partial totals.
+// node, compensated partial totals: s01 for (rho, m_x), s23 for (m_y, rhoE).
 struct TileOut {
   int reach;
   bool bad;
-  Sum2 s[4];
+  Sum2x2 s01, s23;
 };
 
 __device__ __forceinline__ void finish_node(const StepArgs& a, bool valid,
@@ -498,10 +662,8 @@ __device__ __forceinline__ void finish_node(const StepArgs& a, bool valid,
   t.bad |= !finite_in || v.x < 0.0f ||
            (v.x > 0.0f && v.x < 1.17549435e-38f) || !(c.X <= 1099511627776.0f);
   if (a.do_cons) {
-    t.s[0] = sum2_add(t.s[0], v.x);
-    t.s[1] = sum2_add(t.s[1], v.y);
-    t.s[2] = sum2_add(t.s[2], v.z);
-    t.s[3] = sum2_add(t.s[3], v.w);
+    sum2x2_add(t.s01, make_float2(v.x, v.y));
+    sum2x2_add(t.s23, make_float2(v.z, v.w));
   }
 }
 
@@ -528,7 +690,7 @@ struct DestWalk {
 
 // Gather pass for type T over the tile: first pass writes, later passes
 // add to what the earlier passes wrote; the last pass finishes the nodes.
-template <int C1>
+template <int C1, bool KAHAN>
 __device__ __forceinline__ void gather_pass(const StepArgs& a,
                                            const float4* __restrict__ D1,
                                            const float4* __restrict__ D2,
@@ -539,16 +701,11 @@ __device__ __forceinline__ void gather_pass(const StepArgs& a,
   w.init(threadIdx.x, TX);
   const int n = TX * TY;
   const int iters = (n + NTHR - 1) / NTHR;
-  for (int it = 0; it < iters; ++it) {
-    const bool in_tile = w.dy < TY;
-    const int x = x0 + w.dx, y = y0 + w.dy;
+  // one destination's arrivals, the RMW of earlier passes, its end
+  auto dest = [&](const DestWalk& d, float4 v, bool in_tile) {
+    const int x = x0 + d.dx, y = y0 + d.dy;
     const bool valid = in_tile && x < a.nx && y < a.ny;
-    float4 v = f4(0.f, 0.f, 0.f, 0.f);
     const long long o = (long long)y * a.nx + x;
-    if (in_tile) {
-      const int q = (R + w.dy - ty.ny) * DP + (R + w.dx - ty.nx);
-      v = gather_one<C1>(D1, D2, q, ty.c1);
-    }
     if (!first && valid) {
       const float4 p = f4(static_cast<const float*>(a.out[0])[o],
                           static_cast<const float*>(a.out[1])[o],
@@ -564,22 +721,40 @@ __device__ __forceinline__ void gather_pass(const StepArgs& a,
       static_cast<float*>(a.out[2])[o] = v.z;
       static_cast<float*>(a.out[3])[o] = v.w;
     }
+  };
+  auto arrivals = [&](const DestWalk& d, bool in_tile) {
+    float4 v = f4(0.f, 0.f, 0.f, 0.f);
+    if (in_tile) {
+      const int q = (R + d.dy - ty.ny) * DP + (R + d.dx - ty.nx);
+      v = gather_one<C1, KAHAN>(D1, D2, q, ty.c1);
+    }
+    return v;
+  };
+  // two destinations per round: their reads and sums interleave
+  for (int it = 0; it < iters; it += 2) {
+    DestWalk w2 = w;
+    w2.next();
+    const bool two = it + 1 < iters;   // uniform over the block
+    const bool in1 = w.dy < TY, in2 = two && w2.dy < TY;
+    const float4 v1 = arrivals(w, in1);
+    const float4 v2 = arrivals(w2, in2);
+    dest(w, v1, in1);
+    if (two) dest(w2, v2, in2);
+    w = w2;
     w.next();
   }
 }
 
+template <bool KAHAN>
 __device__ __forceinline__ void gather_dispatch(const StepArgs& a,
                                                 const float4* D1,
                                                 const float4* D2, int x0,
                                                 int y0, int R, int TX, int TY,
                                                 Type ty, bool first, bool last,
                                                 TileOut& t) {
-  switch (ty.c1) {
-    case 0: gather_pass<0>(a, D1, D2, x0, y0, R, TX, TY, ty, first, last, t); break;
-    case 1: gather_pass<1>(a, D1, D2, x0, y0, R, TX, TY, ty, first, last, t); break;
-    case 2: gather_pass<2>(a, D1, D2, x0, y0, R, TX, TY, ty, first, last, t); break;
-    default: gather_pass<-1>(a, D1, D2, x0, y0, R, TX, TY, ty, first, last, t); break;
-  }
+  // one instantiation with the level speeds at run time (a few address
+  // additions more than compile-time offsets, far less code)
+  gather_pass<-1, KAHAN>(a, D1, D2, x0, y0, R, TX, TY, ty, first, last, t);
 }
 
 // Finishes every destination of the tile without a gather: with zeros
@@ -669,6 +844,7 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
   __shared__ int red_bad[NWARP];
   float4* D1 = dsm;
   float4* D2 = dsm + PLANE;
+  float* rbase = reinterpret_cast<float*>(dsm + 2 * PLANE);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int b = blockIdx.x;
   const int R0 = a.scr->reach;
@@ -688,19 +864,20 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
   const bool interior = x0 - R >= 0 && x0 - R + WCOLS <= a.nx &&
                         y0 - R >= 0 && y0 - R + WROWS <= a.ny;
 
-  // guess: the type of the tile's central node (every thread forms it)
+  // guess: the type of the tile's central node (every thread forms it; its
+  // load overlaps the walk's first loads)
   float T0;
+  WinStats st = stats_init();
   {
     const int cx = min(x0 + TX / 2, a.nx - 1), cy = min(y0 + TY / 2, a.ny - 1);
     const long long i = (long long)cy * a.nx + cx;
-    const float4 m = f4(static_cast<const float*>(a.in[0])[i],
-                        static_cast<const float*>(a.in[1])[i],
-                        static_cast<const float*>(a.in[2])[i],
-                        static_cast<const float*>(a.in[3])[i]);
-    T0 = type_id(source_eq(m, a.k.kq_f));
+    const float4 m = f4(__ldg(static_cast<const float*>(a.in[0]) + i),
+                        __ldg(static_cast<const float*>(a.in[1]) + i),
+                        __ldg(static_cast<const float*>(a.in[2]) + i),
+                        __ldg(static_cast<const float*>(a.in[3]) + i));
+    walk_one_type(a, D1, D2, rbase, x0, y0, R, TX, TY, interior, 0.0f, &m,
+                  &T0, st);
   }
-  WinStats st = stats_init();
-  walk_one_type(a, D1, D2, x0, y0, R, TX, TY, interior, T0, st);
   {
     const unsigned cl = __reduce_add_sync(0xffffffffu, st.clamps);
     if (lane == 0 && cl) atomicAdd(&a.scr->eclamps, (unsigned long long)cl);
@@ -710,15 +887,14 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
   TileOut to;
   to.reach = 0;
   to.bad = false;
-#pragma unroll
-  for (int f = 0; f < 4; ++f) to.s[f] = Sum2{0.f, 0.f};
+  to.s01 = to.s23 = Sum2x2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
   if (st.tmax < 0.0f) {
     finish_tile(a, x0, y0, TX, TY, true, to);  // nothing lands
   } else if (st.tmin == st.tmax && st.tmin == T0) {
     // one type
     const Type ty = decode_type(T0);
     if (type_fits(ty, R, 0)) {
-      gather_dispatch(a, D1, D2, x0, y0, R, TX, TY, ty, true, true, to);
+      gather_dispatch<KAHAN>(a, D1, D2, x0, y0, R, TX, TY, ty, true, true, to);
     } else {
       if (tid == 0) atomicOr(&a.scr->flags, kFlagReach);
       finish_tile(a, x0, y0, TX, TY, true, to);
@@ -731,7 +907,7 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
     while (true) {
       __syncthreads();  // the previous gather is done with the deposits
       WinStats s2 = stats_init();
-      walk_general(a, D1, D2, x0, y0, R, TX, interior, G, c1min,
+      walk_general(a, D1, D2, rbase, x0, y0, R, TX, interior, G, c1min,
                    nxmin, nymin, s2);
       reduce_stats(s2, red);
       const bool last = !(s2.tnext < kNoType);
@@ -742,7 +918,7 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
       const Type ty{(int)__fmaf_rn(2.0f, GX, nxmin),
                     (int)__fmaf_rn(2.0f, GY, nymin), (int)(c1min + Gc)};
       if (s2.any && type_fits(ty, R, 1)) {
-        gather_dispatch(a, D1, D2, x0, y0, R, TX, TY, ty, first, last, to);
+        gather_dispatch<KAHAN>(a, D1, D2, x0, y0, R, TX, TY, ty, first, last, to);
         first = false;
       } else {
         if (s2.any && tid == 0) atomicOr(&a.scr->flags, kFlagReach);
@@ -757,7 +933,9 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
   int r = __reduce_max_sync(0xffffffffu, to.reach);
   const int bad = __any_sync(0xffffffffu, to.bad) ? 1 : 0;
   if (a.do_cons) {
-    const Sum2 k = warp_sum2_fields(to.s, lane);
+    const Sum2 ps[4] = {{to.s01.hi.x, to.s01.lo.x}, {to.s01.hi.y, to.s01.lo.y},
+                        {to.s23.hi.x, to.s23.lo.x}, {to.s23.hi.y, to.s23.lo.y}};
+    const Sum2 k = warp_sum2_fields(ps, lane);
     if ((lane & 7) == 0) red_sum[lane >> 3][warp] = make_float2(k.hi, k.lo);
   }
   if (lane == 0) {

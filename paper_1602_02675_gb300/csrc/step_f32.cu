@@ -7,7 +7,7 @@ namespace lbm {
 cudaError_t launch_step_f32(int dim, const StepArgs& a, size_t smem,
                             cudaStream_t s) {
   if (dim == 1) {
-    const int tw = step_tile_1d(a.nx);
+    const int tw = step_tile_1d(a.nx, device_sm_count());
     dim3 grid((a.nx + tw - 1) / tw, 1);
     const size_t sm32 = step_smem_bytes_t<float, 1, 32>(a.r_cap);
     const size_t sm16 = step_smem_bytes_t<float, 1, 16>(a.r_cap);
@@ -23,9 +23,10 @@ cudaError_t launch_step_f32(int dim, const StepArgs& a, size_t smem,
       step_kernel<float, 1, true><<<grid, 256, smem, s>>>(a);
     else
       step_kernel<float, 1, false><<<grid, 256, smem, s>>>(a);
-  } else if (a.kahan || a.r_cap > ds::RMAX) {
-    // exact-order kernel: compensated row-pair sums, or a reach limit beyond
-    // the deposit kernel's window
+  } else if (a.r_cap > ds::RMAX || a.exact_order) {
+    // exact-order kernel: a reach limit beyond the deposit kernel's window,
+    // or asked for (the allocation-free step, whose scratch holds this
+    // kernel's per-tile partials)
     dim3 grid((a.nx + TileShape<2>::TX - 1) / TileShape<2>::TX,
               (a.ny + TileShape<2>::TY - 1) / TileShape<2>::TY);
     if (a.kahan)
@@ -33,11 +34,15 @@ cudaError_t launch_step_f32(int dim, const StepArgs& a, size_t smem,
     else
       step_kernel<float, 2, false><<<grid, 256, smem, s>>>(a);
   } else {
-    // deposit-and-shift kernel: the grid holds the tiles of the largest
-    // reach the handle allows; blocks beyond the step's tile count exit
+    // deposit-and-shift kernel, plain or compensated gather: the grid holds
+    // the tiles of the largest reach the handle allows; blocks beyond the
+    // step's tile count exit
     StepArgs b = a;
     b.nblocks = ds::tiles_for(a.nx, a.ny, a.r_cap);
-    ds::step2d_ds<false><<<(unsigned)b.nblocks, ds::NTHR, ds::smem_bytes(), s>>>(b);
+    if (a.kahan)
+      ds::step2d_ds<true><<<(unsigned)b.nblocks, ds::NTHR, ds::smem_bytes(), s>>>(b);
+    else
+      ds::step2d_ds<false><<<(unsigned)b.nblocks, ds::NTHR, ds::smem_bytes(), s>>>(b);
     ds::finalize2d<<<1, ds::NTHR, 0, s>>>(b.scr, b.part, b.nblocks, b.do_cons);
   }
   return cudaGetLastError();
@@ -72,13 +77,16 @@ cudaError_t step_prepare_f32(int dim, size_t smem) {
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // two blocks per multiprocessor need the largest shared-memory carveout
-  e = cudaFuncSetAttribute(ds::step2d_ds<false>,
-                           cudaFuncAttributePreferredSharedMemoryCarveout,
-                           (int)cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(ds::step2d_ds<false>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)ds::smem_bytes());
+  for (const void* fn : {(const void*)ds::step2d_ds<false>,
+                         (const void*)ds::step2d_ds<true>}) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ds::smem_bytes());
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace lbm
@@ -94,7 +102,7 @@ cudaError_t step_raise_smem_f32(int dim, size_t smem) {
       dim == 1 ? (const void*)step_kernel<float, 1, false>
                : (const void*)step_kernel<float, 2, false>,
       dim == 1 ? (const void*)step_kernel<float, 1, true, 32>
-               : (const void*)ds::step2d_ds<false>,
+               : (const void*)ds::step2d_ds<true>,
       dim == 1 ? (const void*)step_kernel<float, 1, false, 32>
                : (const void*)ds::step2d_ds<false>,
       dim == 1 ? (const void*)step_kernel<float, 1, true, 32, 16>

@@ -8,7 +8,7 @@ namespace lbm {
 cudaError_t launch_step_f64(int dim, const StepArgs& a, size_t smem,
                             cudaStream_t s) {
   if (dim == 1) {
-    const int tw = step_tile_1d(a.nx);
+    const int tw = step_tile_1d(a.nx, device_sm_count());
     dim3 grid((a.nx + tw - 1) / tw, 1);
     if (tw == 16)
       step_kernel<double, 1, false, 32, 16><<<grid, 32,

@@ -42,14 +42,16 @@ struct TileShape<2> {
   static constexpr int TX = 32, TY = 8, NP = 8, NK = 4, NLEV = 2;
 };
 
-// 1-D tile width of the exact-order kernel for a tube of nx nodes: 256 once
-// such tiles give two blocks per multiprocessor of a GB300 (152); below that
-// 32-thread blocks with narrow tiles, so that short tubes spread over many
-// multiprocessors (the FP64 rate per multiprocessor is low) and the window
-// of a tile (its width + 2 R sources) is formed in one pass of the block's
-// 32 threads.  Each destination's sum order does not depend on the tile.
-__host__ __device__ inline int step_tile_1d(int nx) {
-  return nx < 2 * 152 * 256 ? (nx <= 152 * 16 ? 16 : 32) : 256;
+// 1-D tile width of the exact-order kernel for a tube of nx nodes on a
+// device with `sms` multiprocessors: 256 once such tiles give two blocks per
+// multiprocessor; below that 32-thread blocks with narrow tiles, so that
+// short tubes spread over many multiprocessors (the FP64 rate per
+// multiprocessor is low) and the window of a tile (its width + 2 R sources)
+// is formed in one pass of the block's 32 threads.  Each destination's sum
+// order does not depend on the tile.
+__host__ __device__ inline int step_tile_1d(int nx, int sms) {
+  const long long n = nx;
+  return n < 2LL * sms * 256 ? (n <= 16LL * sms ? 16 : 32) : 256;
 }
 
 // Shared-memory layout of the source records, structure of arrays, sized

@@ -88,6 +88,7 @@ def load() -> ctypes.CDLL:
         "lbm_step": ([_H, ctypes.c_int64], ctypes.c_int),
         "lbm_moments": ([_H, _DP, _DP, _DP, _DP, _DP, ctypes.c_int64], ctypes.c_int),
         "lbm_conservation": ([_H, _DP], ctypes.c_int),
+        "lbm_last_totals": ([_H, _DP], ctypes.c_int),
         "lbm_reach": ([_H, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "lbm_diagnostics": ([_H, ctypes.POINTER(ctypes.c_int64),
                              ctypes.POINTER(ctypes.c_int64),
@@ -124,6 +125,8 @@ def load() -> ctypes.CDLL:
         "lbm_pool_destroy": ([_H], None),
         "lbm_measure_fma_peak": ([ctypes.c_int32, _DP, ctypes.c_void_p],
                                  ctypes.c_int),
+        "lbm_check_fp32_arith": ([ctypes.c_int64, ctypes.c_uint64, _DP,
+                                  ctypes.c_void_p], ctypes.c_int),
         "lbm_batch_tuning": ([_H, ctypes.POINTER(ctypes.c_int32), _DP],
                              ctypes.c_int),
         "lbm_batch_set_tile": ([_H, ctypes.c_int32], ctypes.c_int),
@@ -249,6 +252,12 @@ class Solver:
         _check(self.h, load().lbm_conservation(self.h, _dp(out)))
         return out
 
+    def last_totals(self) -> np.ndarray:
+        """Totals the step kernel formed at the last summing step."""
+        out = np.zeros(4)
+        _check(self.h, load().lbm_last_totals(self.h, _dp(out)))
+        return out
+
     def reach(self) -> int:
         r = ctypes.c_int32(0)
         _check(self.h, load().lbm_reach(self.h, ctypes.byref(r)))
@@ -289,6 +298,17 @@ def lbm_measure_fma_peak(precision, stream=None) -> float:
     if st != OK:
         raise LbmError(st, "lbm_measure_fma_peak")
     return out.value
+
+
+def lbm_check_fp32_arith(n, seed=1, stream=None) -> tuple[float, float]:
+    """Largest ulp distances of the FP32 kernels' reciprocal and quotient
+    from CUDA's correctly rounded division over n generated inputs
+    (diagnostics; see include/lbm.h)."""
+    out = (ctypes.c_double * 2)()
+    st = load().lbm_check_fp32_arith(int(n), int(seed), out, stream)
+    if st != OK:
+        raise LbmError(st, "lbm_check_fp32_arith")
+    return out[0], out[1]
 
 
 def make_tube(n, nsteps, dt, left, right, x_d=0.5, bc=TRANSMISSIVE) -> lbm_tube:

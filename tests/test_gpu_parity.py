@@ -696,3 +696,39 @@ def test_fma_peak_measurement():
     with pytest.raises(L.LbmError) as e:
         L.lbm_measure_fma_peak(7)
     assert e.value.status == L.EINVAL
+
+
+def test_fp32_reciprocal_and_quotient_against_correct_rounding():
+    """The FP32 kernels' reciprocal (hardware estimate + one Newton-Raphson
+    step) is within one unit in the last place of the correctly rounded 1/x,
+    and their quotient by the level denominators 4 (2 c1 + 1) (eqs 24-25,
+    Markstein's correction) within one of the correctly rounded n / d, over
+    a million generated inputs each."""
+    w_rcp, w_div = L.lbm_check_fp32_arith(1 << 20, seed=2026)
+    assert w_rcp <= 1.0, w_rcp
+    assert w_div <= 1.0, w_div
+    with pytest.raises(L.LbmError):
+        L.lbm_check_fp32_arith(-1)
+
+
+@pytest.mark.parametrize("prec,kahan", [(L.F32, 0), (L.F32, 1), (L.F64, 1)])
+def test_step_totals_match_exact_sum_of_the_state(prec, kahan):
+    """The totals the step kernels form while stepping (a10: compensated
+    FP32 pairs converted to FP64 once in the FP32 kernels, FP64 in the FP64
+    kernels) against the exactly rounded sum (math.fsum) of the same state
+    read back: within 1e-12 of the sum of magnitudes, on a grid of several
+    tiles with ragged edges."""
+    import math
+    nx, ny = 300, 170
+    prims = I.random_smooth_prims(2, nx, ny, seed=4100)
+    cfg = L.make_config(2, nx, ny, precision=prec, bc_x=L.PERIODIC,
+                        bc_y=L.PERIODIC, kahan=kahan, cons_every=1)
+    with L.Solver(cfg) as s:
+        s.set_primitives(*prims)
+        s.step(7)
+        tot = s.last_totals()
+        g = s.moments()
+    for k, f in enumerate(FIELDS):
+        want = math.fsum(g[f].tolist())
+        scale = math.fsum(np.abs(g[f]).tolist())
+        assert abs(tot[k] - want) <= 1e-12 * scale, (f, tot[k], want, scale)
