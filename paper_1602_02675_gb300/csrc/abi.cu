@@ -28,6 +28,10 @@ struct lbm_handle {
   // FP64 square lattice: source records of the state being stepped,
   // rewritten before every step.
   void* src = nullptr;
+  // FP32 square lattice: per-tile hints and the mixed-tile queue of the
+  // deposit kernel.
+  unsigned char* hint = nullptr;
+  int* mixed_list = nullptr;
   Scratch* scr = nullptr;
   double* part = nullptr;
   int part_cap = 0;
@@ -193,6 +197,12 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
   if (ok && c.dim == 2 && h->f64)
     ok = cudaMalloc(&h->src, src_bytes(h->nx, h->ny, h->r_cap, esize(h))) ==
          cudaSuccess;
+  const int dst = (c.dim == 2 && !h->f64) ? ds_tiles(h->nx, h->ny, h->r_cap) : 0;
+  if (ok && dst > 0) {
+    ok = cudaMalloc(&h->hint, (size_t)dst) == cudaSuccess &&
+         cudaMalloc(&h->mixed_list, sizeof(int) * (size_t)dst) == cudaSuccess;
+    if (ok) ok = cudaMemsetAsync(h->hint, 0, (size_t)dst, h->stream) == cudaSuccess;
+  }
   ok = ok && cudaMalloc(&h->scr, sizeof(Scratch)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->part, sizeof(double) * 4 * (size_t)h->part_cap) ==
                  cudaSuccess;
@@ -316,6 +326,8 @@ lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
   a.scr = h->scr;
   a.part = h->part;
   a.src = h->src;
+  a.hint = h->hint;
+  a.mixed_list = h->mixed_list;
   for (int64_t s = 0; s < nsteps; ++s) {
     for (int f = 0; f < 4; ++f) {
       a.in[f] = h->buf[h->cur][f];
@@ -443,6 +455,8 @@ void lbm_destroy(lbm_handle* h) {
     for (int f = 0; f < 4; ++f)
       if (h->buf[b][f]) cudaFree(h->buf[b][f]);
   if (h->src) cudaFree(h->src);
+  if (h->hint) cudaFree(h->hint);
+  if (h->mixed_list) cudaFree(h->mixed_list);
   if (h->scr) cudaFree(h->scr);
   if (h->part) cudaFree(h->part);
   if (h->staging) cudaFree(h->staging);

@@ -18,6 +18,8 @@ struct Scratch {
   unsigned ticket;         // blocks finished in the running launch
   unsigned long long eclamps;  // nodes whose e < 0 was clamped to 0
   double cons[4];          // FP64 totals (lattice units) of the last sum
+  unsigned mixed_n;        // FP32 square lattice: tiles queued for the
+  unsigned mixed_ticket;   // mixed-window kernel, and taken by it
 };
 
 // Constants of the equilibrium (Section III.B) for one lattice and gas.
@@ -53,6 +55,12 @@ struct StepArgs {
   EqConst k;
   Scratch* scr;
   double* part;       // [nblocks * 4] FP64 partial sums
+  // FP32 square lattice (deposit kernel): per tile, whether its window
+  // held several types at the last step (a hint only), and the queue of
+  // tiles the mixed-window kernel takes; both sized for the tiles of the
+  // largest reach.
+  unsigned char* hint = nullptr;
+  int* mixed_list = nullptr;
   // FP64 square lattice: source records of the input state over the grid
   // padded by r_cap (layout in step_kernel.cuh), written by the launcher's
   // records pass before each step, or null.
@@ -69,6 +77,11 @@ inline size_t src_bytes(int nx, int ny, int r_cap, size_t esize) {
 // Multiprocessors of the current device (cached per device; 1 if the
 // query fails, which only makes grids smaller).
 int device_sm_count();
+
+// Tiles of the FP32 square-lattice deposit kernel at the largest reach
+// r_cap (0 if r_cap is beyond its layout): the size of the per-tile hint
+// and queue arrays a handle holds for it.
+int ds_tiles(int nx, int ny, int r_cap);
 
 // Launch helpers (step kernels).
 size_t step_smem_bytes(int dim, bool f64, int r_cap);

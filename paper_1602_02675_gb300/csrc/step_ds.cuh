@@ -205,7 +205,13 @@ __device__ __forceinline__ SrcEq source_eq(float4 m, float kq) {
   const EqCore c = eq_core(rho, m.y, m.z, m.w, kq);
   q.emits = rho > 0.0f;
   q.clamp = q.emits && c.eraw < 0.0f;
-  q.c1 = c1_exact(c.X);
+  // c1 below 4 for the whole warp (X < 16): counted squares and the
+  // correctly rounded 1 / (4 (2 c1 + 1)) from a table, no estimate on the
+  // dependency chain; otherwise c1_of and the refined reciprocal
+  const bool wide = __any_sync(0xffffffffu, !(c.X < 16.0f));
+  q.c1 = (c.X >= 1.0f ? 1.0f : 0.0f) + (c.X >= 4.0f ? 1.0f : 0.0f) +
+         (c.X >= 9.0f ? 1.0f : 0.0f);
+  if (wide) q.c1 = c.X < 16.0f ? q.c1 : c1_of(c.X);
   const float c2 = __fadd_rn(q.c1, 1.0f);
   const float c2sq = __fmul_rn(c2, c2);
   // d1 = (c2^2 rho - X rho) / (4 (c2^2 - c1^2)), d2 = rho / 4 - d1; the
@@ -214,7 +220,12 @@ __device__ __forceinline__ SrcEq source_eq(float4 m, float kq) {
   // energy of every node alike
   const float den = __fmul_rn(4.0f, __fmaf_rn(2.0f, q.c1, 1.0f));
   const float num = __fmaf_rn(c2sq, rho, -__fmul_rn(c.X, rho));
-  const float d1 = div_markstein(num, den, rcp_nr(den));
+  float rden = q.c1 < 1.0f ? 0.25f
+                           : (q.c1 < 2.0f ? 1.0f / 12.0f
+                                          : (q.c1 < 3.0f ? 1.0f / 20.0f
+                                                         : 1.0f / 28.0f));
+  if (wide) rden = q.c1 <= 3.0f ? rden : rcp_nr(den);
+  const float d1 = div_markstein(num, den, rden);
   q.d1 = q.emits ? d1 : 0.0f;
   q.d2 = q.emits ? __fmaf_rn(0.25f, rho, -d1) : 0.0f;
   // phi = e - X / 2 (eq 15 with D/2 (gamma - 1) e = X / 2)
@@ -360,14 +371,15 @@ __device__ __forceinline__ float4 load_src(const StepArgs& a, const Column& c,
 __device__ __forceinline__ void walk_one_type(
     const StepArgs& a, float4* __restrict__ D1, float4* __restrict__ D2,
     float* rbase, int x0, int y0, int R, int TX, int TY, bool interior,
-    float Tin, const float4* cm, float* T0p, WinStats& st) {
+    float Tin, const float4* cm, float* T0p, bool count_clamps,
+    WinStats& st) {
   const Column col = column_of(a, x0, R, TX, interior);
   const int ly0 = SH * col.g;
   const float kq = a.k.kq_f;
   // rows r of this walk whose node the tile owns (its energy clamps are
   // counted here); none if the column is not owned
   const int own_lo = max(1, R - ly0);
-  const int own_hi = col.col_own
+  const int own_hi = col.col_own && count_clamps
                          ? min(min(SH, R + TY - 1 - ly0), a.ny - 1 - (y0 - R) - ly0)
                          : -1;
   float4 pw01a1 = f4(0.f, 0.f, 0.f, 0.f), pw01a2 = pw01a1;
@@ -437,6 +449,66 @@ __device__ __forceinline__ void walk_one_type(
       D1[ly * DP + col.lx] = add4(t01, u1);
       D2[ly * DP + col.lx] = add4(t02, u2);
     }
+  }
+}
+
+// Type of one window source without its level densities: emits, c1, the
+// shift n = floor(V) (eq 23) and whether its energy was clamped.
+__device__ __forceinline__ void source_type(float4 m, float kq, bool& emits,
+                                            bool& clamp, float& id,
+                                            float& c1, float& nxf,
+                                            float& nyf) {
+  const EqCore c = eq_core(m.x, m.y, m.z, m.w, kq);
+  emits = m.x > 0.0f;
+  clamp = emits && c.eraw < 0.0f;
+  c1 = c1_exact(c.X);
+  float f;
+  split_f(emits ? c.Vx : 0.0f, nxf, f);
+  split_f(emits ? c.Vy : 0.0f, nyf, f);
+  id = emits ? __fmaf_rn(65536.0f, c1,
+                         __fmaf_rn(256.0f, __fadd_rn(nxf, 128.0f),
+                                   __fadd_rn(nyf, 128.0f)))
+             : kNoType;
+}
+
+// Statistics walk of a tile queued as mixed: the types of every window
+// source (smallest, largest, minima of c1 and n) and the clamped energies
+// of the owned nodes, without deposits.
+__device__ __forceinline__ void walk_stats(const StepArgs& a, float* rbase,
+                                           int x0, int y0, int R, int TX,
+                                           int TY, bool interior,
+                                           WinStats& st) {
+  const Column col = column_of(a, x0, R, TX, interior);
+  const int ly0 = SH * col.g;
+  const float kq = a.k.kq_f;
+  const int own_lo = max(1, R - ly0);
+  const int own_hi = col.col_own
+                         ? min(min(SH, R + TY - 1 - ly0), a.ny - 1 - (y0 - R) - ly0)
+                         : -1;
+  SrcRing ring = ring_of(a, rbase);
+#pragma unroll
+  for (int k = 0; k < PF; ++k) ring.issue(a, col, y0, R, ly0 + k, k, interior);
+  int slot = 0;
+#pragma unroll 1
+  for (int r = 0; r <= SH; ++r) {
+    if (r + PF - 1 <= SH)
+      cp_async_wait<PF - 1>();
+    else
+      cp_async_wait<0>();
+    const float4 m = ring.take(a, col, y0, R, ly0 + r, slot, interior);
+    if (r + PF <= SH) ring.issue(a, col, y0, R, ly0 + r + PF, slot, interior);
+    slot = slot + 1 == PF ? 0 : slot + 1;
+    bool emits, clamp;
+    float id, c1, nxf, nyf;
+    source_type(m, kq, emits, clamp, id, c1, nxf, nyf);
+    st.tmin = fminf(st.tmin, id);
+    st.tmax = fmaxf(st.tmax, emits ? id : -1.0f);
+    if (emits) {
+      st.nxmin = fminf(st.nxmin, nxf);
+      st.nymin = fminf(st.nymin, nyf);
+      st.c1min = fminf(st.c1min, c1);
+    }
+    if (clamp && r >= own_lo && r <= own_hi) st.clamps += 1;
   }
 }
 
@@ -832,34 +904,112 @@ __device__ __forceinline__ void reduce_stats(WinStats& st, unsigned* red) {
   st.any = (r[5] & 0x80000000u) != 0;
 }
 
-// The step: one block per tile of the reach the step runs with.  Blocks
-// beyond the tile count of that reach (the grid is sized for the largest
-// reach) only clear their partial totals.
+// Tile geometry of a step: reach R (at least 1), tile size, tile count.
+struct TileGeo {
+  int R, TX, TY, tiles_x, ntiles;
+  bool over;  // the reach exceeds the layout or the handle's limit
+};
+__device__ __forceinline__ TileGeo geo_of(const StepArgs& a) {
+  TileGeo g;
+  const int R0 = a.scr->reach;
+  g.R = R0 < 1 ? 1 : R0;
+  g.TX = tile_w(g.R);
+  g.TY = tile_h(g.R);
+  g.tiles_x = (a.nx + g.TX - 1) / g.TX;
+  g.ntiles = g.tiles_x * ((a.ny + g.TY - 1) / g.TY);
+  g.over = R0 > a.r_cap || R0 > RMAX;
+  return g;
+}
+
+// Block-wide end of a tile: its reach, bad-state flag and compensated
+// partial totals (part[b], the finalize kernel sums them).
+struct TileRed {
+  float2 sum[4][NWARP];
+  int reach[NWARP];
+  int bad[NWARP];
+};
+__device__ __forceinline__ void tile_publish(const StepArgs& a, int b,
+                                             const TileOut& to, TileRed& red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = __reduce_max_sync(0xffffffffu, to.reach);
+  const int bad = __any_sync(0xffffffffu, to.bad) ? 1 : 0;
+  if (a.do_cons) {
+    const Sum2 ps[4] = {{to.s01.hi.x, to.s01.lo.x}, {to.s01.hi.y, to.s01.lo.y},
+                        {to.s23.hi.x, to.s23.lo.x}, {to.s23.hi.y, to.s23.lo.y}};
+    const Sum2 k = warp_sum2_fields(ps, lane);
+    if ((lane & 7) == 0) red.sum[lane >> 3][warp] = make_float2(k.hi, k.lo);
+  }
+  if (lane == 0) {
+    red.reach[warp] = r;
+    red.bad[warp] = bad;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    int rb = lane < NWARP ? red.reach[lane] : 0;
+    rb = __reduce_max_sync(0xffffffffu, rb);
+    const int bb = __any_sync(0xffffffffu, lane < NWARP && red.bad[lane] != 0);
+    if (lane == 0) {
+      atomicMax(&a.scr->reach_next, rb);
+      if (bb) atomicOr(&a.scr->flags, kFlagState);
+    }
+    if (a.do_cons) {
+      static_assert(NWARP == 8, "one lane per (field, warp)");
+      const Sum2 s = combine_warps_f2<NWARP>(red.sum, lane);
+      if ((lane & 7) == 0)
+        reinterpret_cast<float2*>(a.part)[(long long)b * 4 + (lane >> 3)] =
+            make_float2(s.hi, s.lo);
+    }
+  }
+}
+
+__device__ __forceinline__ TileOut tile_out_init() {
+  TileOut to;
+  to.reach = 0;
+  to.bad = false;
+  to.s01 = to.s23 = Sum2x2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  return to;
+}
+
+// Commits the block's clamped-energy count (one atomic per warp).
+__device__ __forceinline__ void commit_clamps(const StepArgs& a, unsigned c) {
+  const unsigned cl = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0 && cl)
+    atomicAdd(&a.scr->eclamps, (unsigned long long)cl);
+}
+
+// The step, first kernel: one block per tile of the reach the step runs
+// with (the grid holds the tiles of the largest reach; blocks beyond the
+// step's count only clear their partial totals).  A tile whose window
+// holds one type is done here; a tile whose window held several types at
+// the last step, or turns out to hold several now, is queued for the
+// mixed-window kernel and left to it.
 template <bool KAHAN>
 __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
   extern __shared__ __align__(16) float4 dsm[];
   __shared__ unsigned red[NSTAT * NWARP];
-  __shared__ float2 red_sum[4][NWARP];
-  __shared__ int red_reach[NWARP];
-  __shared__ int red_bad[NWARP];
+  __shared__ TileRed tred;
   float4* D1 = dsm;
   float4* D2 = dsm + PLANE;
   float* rbase = reinterpret_cast<float*>(dsm + 2 * PLANE);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int b = blockIdx.x;
-  const int R0 = a.scr->reach;
-  const int R = R0 < 1 ? 1 : R0;
-  const int TX = tile_w(R), TY = tile_h(R);
-  const int tiles_x = (a.nx + TX - 1) / TX;
-  const bool over = R0 > a.r_cap || R0 > RMAX;
-  if (over || b >= tiles_x * ((a.ny + TY - 1) / TY)) {
-    if (over && tid == 0 && b == 0) atomicOr(&a.scr->flags, kFlagReach);
+  const TileGeo g = geo_of(a);
+  if (g.over || b >= g.ntiles) {
+    if (g.over && tid == 0 && b == 0) atomicOr(&a.scr->flags, kFlagReach);
     if (a.do_cons && tid < 4)
       reinterpret_cast<float2*>(a.part)[(long long)b * 4 + tid] =
           make_float2(0.f, 0.f);
     return;
   }
-  const int ty_i = b / tiles_x, tx_i = b - ty_i * tiles_x;
+  auto enqueue = [&]() {
+    if (tid == 0) a.mixed_list[atomicAdd(&a.scr->mixed_n, 1u)] = b;
+  };
+  if (a.hint[b]) {
+    enqueue();
+    return;
+  }
+  const int R = g.R, TX = g.TX, TY = g.TY;
+  const int ty_i = b / g.tiles_x, tx_i = b - ty_i * g.tiles_x;
   const int x0 = tx_i * TX, y0 = ty_i * TY;
   const bool interior = x0 - R >= 0 && x0 - R + WCOLS <= a.nx &&
                         y0 - R >= 0 && y0 - R + WROWS <= a.ny;
@@ -876,22 +1026,21 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
                         __ldg(static_cast<const float*>(a.in[2]) + i),
                         __ldg(static_cast<const float*>(a.in[3]) + i));
     walk_one_type(a, D1, D2, rbase, x0, y0, R, TX, TY, interior, 0.0f, &m,
-                  &T0, st);
+                  &T0, true, st);
   }
-  {
-    const unsigned cl = __reduce_add_sync(0xffffffffu, st.clamps);
-    if (lane == 0 && cl) atomicAdd(&a.scr->eclamps, (unsigned long long)cl);
-  }
+  const unsigned my_clamps = st.clamps;
   reduce_stats(st, red);  // includes the barrier after the deposits
-
-  TileOut to;
-  to.reach = 0;
-  to.bad = false;
-  to.s01 = to.s23 = Sum2x2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-  if (st.tmax < 0.0f) {
+  const bool none = st.tmax < 0.0f;
+  if (!none && !(st.tmin == st.tmax && st.tmin == T0)) {
+    if (tid == 0) a.hint[b] = 1;
+    enqueue();            // the mixed-window kernel counts its clamps
+    return;
+  }
+  commit_clamps(a, my_clamps);
+  TileOut to = tile_out_init();
+  if (none) {
     finish_tile(a, x0, y0, TX, TY, true, to);  // nothing lands
-  } else if (st.tmin == st.tmax && st.tmin == T0) {
-    // one type
+  } else {
     const Type ty = decode_type(T0);
     if (type_fits(ty, R, 0)) {
       gather_dispatch<KAHAN>(a, D1, D2, x0, y0, R, TX, TY, ty, true, true, to);
@@ -899,65 +1048,95 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
       if (tid == 0) atomicOr(&a.scr->flags, kFlagReach);
       finish_tile(a, x0, y0, TX, TY, true, to);
     }
-  } else {
-    // several types: one general walk per group, ascending
-    const float c1min = st.c1min, nxmin = st.nxmin, nymin = st.nymin;
-    float G = 0.0f;  // (c1min, blocks (0, 0)); possibly empty
-    bool first = true;
-    while (true) {
-      __syncthreads();  // the previous gather is done with the deposits
-      WinStats s2 = stats_init();
-      walk_general(a, D1, D2, rbase, x0, y0, R, TX, interior, G, c1min,
-                   nxmin, nymin, s2);
-      reduce_stats(s2, red);
-      const bool last = !(s2.tnext < kNoType);
-      const float Gc = floorf(G * (1.0f / 65536.0f));
-      const float Gr = __fmaf_rn(-65536.0f, Gc, G);
-      const float GX = floorf(Gr * (1.0f / 256.0f));
-      const float GY = __fmaf_rn(-256.0f, GX, Gr);
-      const Type ty{(int)__fmaf_rn(2.0f, GX, nxmin),
-                    (int)__fmaf_rn(2.0f, GY, nymin), (int)(c1min + Gc)};
-      if (s2.any && type_fits(ty, R, 1)) {
-        gather_dispatch<KAHAN>(a, D1, D2, x0, y0, R, TX, TY, ty, first, last, to);
-        first = false;
-      } else {
-        if (s2.any && tid == 0) atomicOr(&a.scr->flags, kFlagReach);
-        if (last) finish_tile(a, x0, y0, TX, TY, first, to);
-      }
-      if (last) break;
-      G = s2.tnext;
-    }
   }
+  tile_publish(a, b, to, tred);
+}
 
-  // block reductions: reach, bad state, totals
-  int r = __reduce_max_sync(0xffffffffu, to.reach);
-  const int bad = __any_sync(0xffffffffu, to.bad) ? 1 : 0;
-  if (a.do_cons) {
-    const Sum2 ps[4] = {{to.s01.hi.x, to.s01.lo.x}, {to.s01.hi.y, to.s01.lo.y},
-                        {to.s23.hi.x, to.s23.lo.x}, {to.s23.hi.y, to.s23.lo.y}};
-    const Sum2 k = warp_sum2_fields(ps, lane);
-    if ((lane & 7) == 0) red_sum[lane >> 3][warp] = make_float2(k.hi, k.lo);
-  }
-  if (lane == 0) {
-    red_reach[warp] = r;
-    red_bad[warp] = bad;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    int rb = lane < NWARP ? red_reach[lane] : 0;
-    rb = __reduce_max_sync(0xffffffffu, rb);
-    const int bb = __any_sync(0xffffffffu, lane < NWARP && red_bad[lane] != 0);
-    if (lane == 0) {
-      atomicMax(&a.scr->reach_next, rb);
-      if (bb) atomicOr(&a.scr->flags, kFlagState);
+// The step, second kernel: persistent blocks take the tiles the first
+// kernel queued, one at a time.  Per tile a statistics walk; a window that
+// holds one type after all takes the one-type walk; otherwise one general
+// walk per group of sources (same c1, shifts within a 2 x 2 block), in
+// ascending group order, each adding its arrivals.  What a tile computes
+// depends only on the state, not on the queue order or the hints.
+template <bool KAHAN>
+__global__ void __launch_bounds__(NTHR, 2) step2d_ds_mixed(const StepArgs a) {
+  extern __shared__ __align__(16) float4 dsm[];
+  __shared__ unsigned red[NSTAT * NWARP];
+  __shared__ TileRed tred;
+  __shared__ int s_k;
+  float4* D1 = dsm;
+  float4* D2 = dsm + PLANE;
+  float* rbase = reinterpret_cast<float*>(dsm + 2 * PLANE);
+  const int tid = threadIdx.x;
+  const TileGeo g = geo_of(a);
+  const int nq = (int)a.scr->mixed_n;
+  if (g.over) return;
+  const int R = g.R, TX = g.TX, TY = g.TY;
+  while (true) {
+    if (tid == 0) s_k = (int)atomicAdd(&a.scr->mixed_ticket, 1u);
+    __syncthreads();
+    const int k = s_k;
+    __syncthreads();
+    if (k >= nq) break;
+    const int b = a.mixed_list[k];
+    const int ty_i = b / g.tiles_x, tx_i = b - ty_i * g.tiles_x;
+    const int x0 = tx_i * TX, y0 = ty_i * TY;
+    const bool interior = x0 - R >= 0 && x0 - R + WCOLS <= a.nx &&
+                          y0 - R >= 0 && y0 - R + WROWS <= a.ny;
+    WinStats st = stats_init();
+    walk_stats(a, rbase, x0, y0, R, TX, TY, interior, st);
+    commit_clamps(a, st.clamps);
+    reduce_stats(st, red);
+    TileOut to = tile_out_init();
+    const bool none = st.tmax < 0.0f;
+    if (tid == 0) a.hint[b] = (!none && st.tmin != st.tmax) ? 1 : 0;
+    if (none) {
+      finish_tile(a, x0, y0, TX, TY, true, to);
+    } else if (st.tmin == st.tmax) {
+      const float T = st.tmin;
+      WinStats s1 = stats_init();
+      walk_one_type(a, D1, D2, rbase, x0, y0, R, TX, TY, interior, T,
+                    nullptr, nullptr, false, s1);
+      reduce_stats(s1, red);
+      const Type ty = decode_type(T);
+      if (type_fits(ty, R, 0)) {
+        gather_dispatch<KAHAN>(a, D1, D2, x0, y0, R, TX, TY, ty, true, true,
+                               to);
+      } else {
+        if (tid == 0) atomicOr(&a.scr->flags, kFlagReach);
+        finish_tile(a, x0, y0, TX, TY, true, to);
+      }
+    } else {
+      const float c1min = st.c1min, nxmin = st.nxmin, nymin = st.nymin;
+      float G = 0.0f;  // (c1min, blocks (0, 0)); possibly empty
+      bool first = true;
+      while (true) {
+        __syncthreads();  // the previous gather is done with the deposits
+        WinStats s2 = stats_init();
+        walk_general(a, D1, D2, rbase, x0, y0, R, TX, interior, G, c1min,
+                     nxmin, nymin, s2);
+        reduce_stats(s2, red);
+        const bool last = !(s2.tnext < kNoType);
+        const float Gc = floorf(G * (1.0f / 65536.0f));
+        const float Gr = __fmaf_rn(-65536.0f, Gc, G);
+        const float GX = floorf(Gr * (1.0f / 256.0f));
+        const float GY = __fmaf_rn(-256.0f, GX, Gr);
+        const Type ty{(int)__fmaf_rn(2.0f, GX, nxmin),
+                      (int)__fmaf_rn(2.0f, GY, nymin), (int)(c1min + Gc)};
+        if (s2.any && type_fits(ty, R, 1)) {
+          gather_dispatch<KAHAN>(a, D1, D2, x0, y0, R, TX, TY, ty, first,
+                                 last, to);
+          first = false;
+        } else {
+          if (s2.any && tid == 0) atomicOr(&a.scr->flags, kFlagReach);
+          if (last) finish_tile(a, x0, y0, TX, TY, first, to);
+        }
+        if (last) break;
+        G = s2.tnext;
+      }
     }
-    if (a.do_cons) {
-      static_assert(NWARP == 8, "one lane per (field, warp)");
-      const Sum2 s = combine_warps_f2<NWARP>(red_sum, lane);
-      if ((lane & 7) == 0)
-        reinterpret_cast<float2*>(a.part)[(long long)b * 4 + (lane >> 3)] =
-            make_float2(s.hi, s.lo);
-    }
+    tile_publish(a, b, to, tred);
+    __syncthreads();  // the next tile reuses the deposits and the ring
   }
 }
 
@@ -993,6 +1172,8 @@ __global__ void __launch_bounds__(NTHR)
     if (!(scr->flags & kFlagReach)) scr->reach = scr->reach_next;
     scr->reach_next = 0;
     scr->ticket = 0u;
+    scr->mixed_n = 0u;
+    scr->mixed_ticket = 0u;
   }
 }
 

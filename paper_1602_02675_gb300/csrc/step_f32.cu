@@ -39,13 +39,24 @@ cudaError_t launch_step_f32(int dim, const StepArgs& a, size_t smem,
     // step's tile count exit
     StepArgs b = a;
     b.nblocks = ds::tiles_for(a.nx, a.ny, a.r_cap);
-    if (a.kahan)
+    if (!b.hint || !b.mixed_list) return cudaErrorInvalidValue;
+    // the mixed-window kernel: persistent, two blocks per multiprocessor
+    int nb2 = 2 * device_sm_count();
+    if (nb2 > b.nblocks) nb2 = b.nblocks;
+    if (a.kahan) {
       ds::step2d_ds<true><<<(unsigned)b.nblocks, ds::NTHR, ds::smem_bytes(), s>>>(b);
-    else
+      ds::step2d_ds_mixed<true><<<(unsigned)nb2, ds::NTHR, ds::smem_bytes(), s>>>(b);
+    } else {
       ds::step2d_ds<false><<<(unsigned)b.nblocks, ds::NTHR, ds::smem_bytes(), s>>>(b);
+      ds::step2d_ds_mixed<false><<<(unsigned)nb2, ds::NTHR, ds::smem_bytes(), s>>>(b);
+    }
     ds::finalize2d<<<1, ds::NTHR, 0, s>>>(b.scr, b.part, b.nblocks, b.do_cons);
   }
   return cudaGetLastError();
+}
+
+int ds_tiles(int nx, int ny, int r_cap) {
+  return r_cap > ds::RMAX ? 0 : ds::tiles_for(nx, ny, r_cap);
 }
 
 size_t step_smem_f32(int dim, int r_cap) {
@@ -78,7 +89,9 @@ cudaError_t step_prepare_f32(int dim, size_t smem) {
   if (e != cudaSuccess) return e;
   // two blocks per multiprocessor need the largest shared-memory carveout
   for (const void* fn : {(const void*)ds::step2d_ds<false>,
-                         (const void*)ds::step2d_ds<true>}) {
+                         (const void*)ds::step2d_ds<true>,
+                         (const void*)ds::step2d_ds_mixed<false>,
+                         (const void*)ds::step2d_ds_mixed<true>}) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
