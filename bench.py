@@ -204,7 +204,12 @@ class Clocks:
 # our arm
 # --------------------------------------------------------------------------
 def fp32_kernel_name(kahan):
-    return "lbm::ds::step2d_ds" if kahan == 0 else "step_kernel<float,2,true>"
+    return "lbm::ds::step2d_ds<%s>" % ("false" if kahan == 0 else "true")
+
+
+# launches of ours per 2-D FP32 step: the one-type tile kernel, the
+# persistent mixed-tile kernel and the one-block finalize kernel
+DS_LAUNCHES_PER_STEP = 3
 
 
 def run_cylinder(args, rank, world):
@@ -300,7 +305,8 @@ def run_cylinder(args, rank, world):
             "nominal_peak": 7900.0,
             "frac_of_nominal": round(achieved / 7900.0, 4),
             "duration": "CUDA events around lbm_step over the whole timed "
-                        "solve: step kernel + one-block finalize kernel"}
+                        "solve: the one-type tile kernel, the mixed-window "
+                        "kernel and the one-block finalize kernel"}
     peak32 = L.lbm_measure_fma_peak(L.F32, stream.cuda_stream)
     peak64 = L.lbm_measure_fma_peak(L.F64, stream.cuda_stream)
     alu = {"flop_per_node_update": 256,
@@ -347,7 +353,7 @@ def run_cylinder(args, rank, world):
         "roofline": roof,
         "alu_check": alu,
         "clocks": clk,
-        "gpu_launches": 2 * K if args.kahan == 0 else K,
+        "gpu_launches": DS_LAUNCHES_PER_STEP * K,
         "wall_s_timed_fp32": round(wall32, 4),
         "precision": precision,
     }
@@ -565,7 +571,8 @@ def l1_vs_oracle(L) -> dict:
                      for f in ("rho", "mx", "rhoE")}
         out[name]["my_max_abs"] = float(np.max(np.abs(g["my"])))
     out["case"] = ("sod_2d_4096x512, 820 steps to t = 0.2, every row; f32: "
-                   "deposit kernel, f32_kahan: compensated exact-order kernel")
+                   "deposit kernel, f32_kahan: deposit kernel with the "
+                   "compensated gather")
     return out
 
 
@@ -840,8 +847,8 @@ def main():
     ap.add_argument("--seq-tubes", type=int, default=48)
     ap.add_argument("--precision", default="both", choices=["both", "f32"])
     ap.add_argument("--kahan", type=int, default=0, choices=[0, 1],
-                    help="FP32 kernel: 0 deposit kernel, 1 compensated "
-                         "exact-order kernel")
+                    help="FP32 deposit kernel: 0 plain gather, 1 "
+                         "compensated gather")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -904,7 +911,7 @@ def run_sod2d_main(args, rank, world):
                        "parallelism": (f"replicas x{world}" if world > 1
                                        else "1 GPU")},
             "roofline": sub["roofline"], "clocks": sub.get("clocks"),
-            "gpu_launches": 2 * args.steps if args.kahan == 0 else args.steps,
+            "gpu_launches": DS_LAUNCHES_PER_STEP * args.steps,
             "sod2d": sub}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

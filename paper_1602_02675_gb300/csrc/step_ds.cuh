@@ -1151,16 +1151,37 @@ __global__ void __launch_bounds__(NTHR)
   __shared__ float2 red[4][NWARP];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (do_cons) {
-    const float2* p2 = reinterpret_cast<const float2*>(part);
-    Sum2 s4[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    for (int b = tid; b < nblk; b += NTHR) {
+    // each thread a fixed strided set of tiles, four at a time (their loads
+    // in flight together), then a fixed combine
+    const float4* p4 = reinterpret_cast<const float4*>(part);
+    constexpr int U = 4;
+    Sum2 s4[U][4];
 #pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        const float2 v = p2[(long long)b * 4 + f];
-        s4[f] = sum2_add(s4[f], Sum2{v.x, v.y});
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) s4[u][f] = Sum2{0.f, 0.f};
+    for (int b0 = tid; b0 < nblk; b0 += U * NTHR) {
+      float4 v[U][2];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int b = b0 + u * NTHR;
+        const bool ok = b < nblk;
+        v[u][0] = ok ? p4[(long long)b * 2] : f4(0.f, 0.f, 0.f, 0.f);
+        v[u][1] = ok ? p4[(long long)b * 2 + 1] : f4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        s4[u][0] = sum2_add(s4[u][0], Sum2{v[u][0].x, v[u][0].y});
+        s4[u][1] = sum2_add(s4[u][1], Sum2{v[u][0].z, v[u][0].w});
+        s4[u][2] = sum2_add(s4[u][2], Sum2{v[u][1].x, v[u][1].y});
+        s4[u][3] = sum2_add(s4[u][3], Sum2{v[u][1].z, v[u][1].w});
       }
     }
-    const Sum2 k = warp_sum2_fields(s4, lane);
+#pragma unroll
+    for (int u = 1; u < U; ++u)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) s4[0][f] = sum2_add(s4[0][f], s4[u][f]);
+    const Sum2 k = warp_sum2_fields(s4[0], lane);
     if ((lane & 7) == 0) red[lane >> 3][warp] = make_float2(k.hi, k.lo);
     __syncthreads();
     if (warp == 0) {

@@ -27,7 +27,7 @@ def _oracle_tube(t, nsteps, lam):
     return O.lattice_to_physical(1.4, lam, s2), O.totals(s2)
 
 
-def _oracle_fp32_storage_error(t, nsteps, lam):
+def _oracle_fp32_storage_error(t, nsteps, lam, ref=None):
     """L1 (of range) error the oracle itself incurs when its state is
     rounded to FP32 after every step: the floor any FP32 path can reach.
     Near the top of a level interval (X = D(gamma-1)e/(1-theta) close to
@@ -35,7 +35,8 @@ def _oracle_fp32_storage_error(t, nsteps, lam):
     1e-5 for some tubes."""
     P = O.Params(dim=1, nx=t.n, bc_x=O.TRANSMISSIVE)
     s = O.riemann_planar(P, 0.0, 1.0, 0.5, t.left, t.right, lam)
-    ref, _ = O.run(P, s, nsteps)
+    if ref is None:
+        ref, _ = O.run(P, s, nsteps)
     r = lambda a: a.astype(np.float32).astype(np.float64)
     for _ in range(nsteps):
         s, _, _ = O.step(P, s)
@@ -81,16 +82,26 @@ def test_batch_matches_oracle_per_tube(precision):
             assert np.all(np.abs(tot[j] - want) <= tol * scale), (j, tot[j], want)
 
 
-def test_full_batch_sampled_tubes_fp32():
-    """The benchmark's batch at full size (4096 seeded tubes of 256..16384
-    nodes, FP32 with compensated sums, the tuned tile): the six tubes the
-    oracle runs fastest, checked against the oracle run of each alone."""
+def _full_specs():
     specs = []
     for t in I.tubes_batch(4096):
         nsteps, lam = t.steps_and_lambda(0.2)
         specs.append((t, nsteps, (lam / t.n) * t.n))
-    cheap = sorted(range(len(specs)),
-                   key=lambda j: specs[j][0].n * specs[j][1])[:6]
+    return specs
+
+
+def test_full_batch_sampled_tubes_fp32():
+    """The benchmark's batch at full size (4096 seeded tubes of 256..16384
+    nodes, FP32 with compensated sums, the tuned tile): the six tubes the
+    oracle runs fastest, the longest (most node updates) and the hottest
+    (largest p / rho on either side), each against the oracle run of it
+    alone."""
+    specs = _full_specs()
+    work = [t.n * ns for t, ns, _ in specs]
+    temp = [max(t.left[2] / t.left[0], t.right[2] / t.right[0])
+            for t, _, _ in specs]
+    cheap = sorted(range(len(specs)), key=lambda j: work[j])[:6]
+    cheap += [int(np.argmax(work)), int(np.argmax(temp))]
     with _make(specs, L.F32, kahan=1) as b:
         b.run()
         b.sync()
@@ -98,13 +109,48 @@ def test_full_batch_sampled_tubes_fp32():
         got = {j: b.moments(j) for j in cheap}
     for j in cheap:
         t, ns, lam = specs[j]
-        o, _ = _oracle_tube(t, ns, lam)
+        P = O.Params(dim=1, nx=t.n, bc_x=O.TRANSMISSIVE)
+        ref, _ = O.run(P, O.riemann_planar(P, 0.0, 1.0, 0.5, t.left, t.right,
+                                           lam), ns)
+        o = O.lattice_to_physical(1.4, lam, ref)
+        floor = None
         for f in ("rho", "mx", "rhoE"):
             rng = o[f].max() - o[f].min()
             err = np.mean(np.abs(got[j][f] - o[f])) / rng
             if err > 1e-5:
-                floor = _oracle_fp32_storage_error(t, ns, lam)[f]
-                assert err <= 4.0 * floor, (j, f, err, floor)
+                if floor is None:
+                    floor = _oracle_fp32_storage_error(t, ns, lam, ref)
+                assert err <= 4.0 * floor[f], (j, f, err, floor[f])
+
+
+def test_full_batch_fp32_against_fp64_every_tube():
+    """All 4096 tubes of the benchmark's batch in FP32 (compensated sums)
+    against the FP64 batch (bit-exact with the oracle per tube): mean
+    |error| / range per tube and field.  The 1-D step amplifies rounding
+    near the top of a level interval, so some hot tubes cannot stay within
+    1e-5 in any FP32 arithmetic: the median must, at most 5 % of the tubes
+    may exceed it, and the worst tube must be within 4x of what the oracle
+    itself loses by rounding its state to FP32 every step."""
+    specs = _full_specs()
+    res = {}
+    for prec in (L.F64, L.F32):
+        with _make(specs, prec, kahan=1) as b:
+            b.run()
+            b.sync()
+            res[prec] = [b.moments(j) for j in range(len(specs))]
+    worst = (0.0, None, None)
+    for f in ("rho", "mx", "rhoE"):
+        e = np.array([np.mean(np.abs(g[f] - o[f])) / (o[f].max() - o[f].min())
+                      for g, o in zip(res[L.F32], res[L.F64])])
+        assert np.median(e) <= 1e-5, (f, np.median(e))
+        assert np.mean(e > 1e-5) <= 0.05, (f, int(np.sum(e > 1e-5)))
+        j = int(np.argmax(e))
+        if e[j] > worst[0]:
+            worst = (float(e[j]), j, f)
+    err, j, f = worst
+    if err > 1e-5:
+        floor = _oracle_fp32_storage_error(*specs[j])[f]
+        assert err <= 4.0 * floor, (j, f, err, floor)
 
 
 @pytest.mark.parametrize("precision", [L.F32, L.F64])
