@@ -28,9 +28,9 @@ struct lbm_handle {
   // FP64 square lattice: source records of the state being stepped,
   // rewritten before every step.
   void* src = nullptr;
-  // FP32 square lattice: per-tile hints and the mixed-tile queue of the
-  // deposit kernel.
-  unsigned char* hint = nullptr;
+  // FP32 square lattice: per-tile window records and the mixed-tile queue
+  // of the deposit kernel.
+  unsigned* hint = nullptr;
   int* mixed_list = nullptr;
   Scratch* scr = nullptr;
   double* part = nullptr;
@@ -199,9 +199,11 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
          cudaSuccess;
   const int dst = (c.dim == 2 && !h->f64) ? ds_tiles(h->nx, h->ny, h->r_cap) : 0;
   if (ok && dst > 0) {
-    ok = cudaMalloc(&h->hint, (size_t)dst) == cudaSuccess &&
+    ok = cudaMalloc(&h->hint, sizeof(unsigned) * (size_t)dst) == cudaSuccess &&
          cudaMalloc(&h->mixed_list, sizeof(int) * (size_t)dst) == cudaSuccess;
-    if (ok) ok = cudaMemsetAsync(h->hint, 0, (size_t)dst, h->stream) == cudaSuccess;
+    if (ok)
+      ok = cudaMemsetAsync(h->hint, 0, sizeof(unsigned) * (size_t)dst,
+                           h->stream) == cudaSuccess;
   }
   ok = ok && cudaMalloc(&h->scr, sizeof(Scratch)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->part, sizeof(double) * 4 * (size_t)h->part_cap) ==

@@ -55,11 +55,12 @@ struct StepArgs {
   EqConst k;
   Scratch* scr;
   double* part;       // [nblocks * 4] FP64 partial sums
-  // FP32 square lattice (deposit kernel): per tile, whether its window
-  // held several types at the last step (a hint only), and the queue of
+  // FP32 square lattice (deposit kernel): per tile, the record of its
+  // window at the last step (0: one type; else the window's smallest c1 and
+  // shift and its group block, a starting guess only), and the queue of
   // tiles the mixed-window kernel takes; both sized for the tiles of the
   // largest reach.
-  unsigned char* hint = nullptr;
+  unsigned* hint = nullptr;
   int* mixed_list = nullptr;
   // FP64 square lattice: source records of the input state over the grid
   // padded by r_cap (layout in step_kernel.cuh), written by the launcher's

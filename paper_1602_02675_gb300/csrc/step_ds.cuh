@@ -20,33 +20,36 @@
 // and data that vary along x only stay so bit for bit (their y-momentum
 // arrivals from rows +-c cancel exactly).
 //
-// Layout of one launch: one block per tile.  The block's window is 61 x 48
-// sources (WCOLS x WROWS); with the step's reach R the tile is the window
-// minus R on every side, (61 - 2R) x (48 - 2R) destinations.
+// Layout: one block per tile.  The block's window is 60 x 48 sources
+// (WCOLS x WROWS); with the step's reach R the tile is the window minus R on
+// every side, (60 - 2R) x (48 - 2R) destinations.
 //  * Phase 1 (window).  Thread (lane, wx, g) owns window column
-//    lane + 30 wx (the two warps of a row overlap by two columns; column 61
-//    holds deposits only) and walks rows 12 g - 1 .. 12 g + 12 (the groups
-//    overlap; row 48 holds deposits only).  Walking down its column it loads
-//    each source's moments (coalesced: a warp reads 32 consecutive nodes of
-//    a row), forms the equilibrium and deposits: the parts that land in its
-//    own column it sums itself over the rows, the parts that land one or two
-//    columns to the right come from the lanes to the left by shuffles, and
-//    the deposit goes to shared memory.  Sources outside the grid are the
-//    additional points of Section V.B (nearest node, periodic image, or
-//    mirror image with the normal momentum negated).
+//    lane + 29 wx (the two warps of a row overlap by three columns; column 60
+//    holds deposits only) and walks the rows of group g (12 deposit rows,
+//    the groups' walks overlap; row 48 holds deposits only).  Walking down
+//    its column it loads each source's moments (coalesced: a warp reads 32
+//    consecutive nodes of a row), forms the equilibrium and deposits: the
+//    parts that land in its own column it sums itself over the rows, the
+//    parts that land one or more columns to the right come from the lanes to
+//    the left by shuffles, and the deposit goes to shared memory.  Sources
+//    outside the grid are the additional points of Section V.B (nearest
+//    node, periodic image, or mirror image with the normal momentum negated).
 //  * Phase 2 (tile).  Each thread gathers destinations of the tile in
 //    row-major order, 256 apart, from the deposits: per level four reads
 //    (+x, -x, +y, -y packets), and writes the new moments; then the new
 //    node's reach and the block's compensated partial totals.
-// The window's sources are all of one type in most tiles; the first deposit
-// is formed for the type of the tile's central node, and the block checks
-// that every source had that type.  Otherwise the sources are grouped by c1
-// and by blocks of two lattice shifts per axis, n in {a, a+1} x {b, b+1}:
-// relative to the base (a, b) such a source lands at s + dn + k, dn in
-// {0, 1}^2, so the deposit weights become hat functions over three offsets
-// per axis (a general deposit, one walk per group), and the gather is the
-// one-type gather at shift (a, b).  Groups are done in ascending order,
-// each adding its arrivals to the destinations.
+// The window's sources are all of one type in most tiles early in a flow:
+// the first kernel deposits for the type of the tile's central node and
+// checks that every source had that type.  Otherwise the tile goes to the
+// second kernel, which groups the sources by c1 and by blocks of S lattice
+// shifts per axis (S = 1, 2 or 3, from the spread of n over the window):
+// n in {a .. a+S-1} x {b .. b+S-1}.  Relative to the base (a, b) such a
+// source lands at s + dn + k, dn in {0 .. S-1}^2, so the deposit weights
+// become hat functions over S + 1 offsets per axis (one walk per group),
+// and the gather is the one-type gather at shift (a, b).  Groups are done in
+// ascending order, each adding its arrivals to the destinations.  The
+// smallest c1 and shift of a window are taken from the tile's previous step
+// and checked during its first walk (redone when a source lies below them).
 #pragma once
 
 #include <cstdint>
@@ -59,9 +62,10 @@ namespace ds {
 
 constexpr int NWX = 2;                    // warps across a window row
 constexpr int CW = 32 * NWX;              // threads across
-constexpr int WSTEP = 30;                 // column offset of the second warp
-constexpr int DCOLS = WSTEP + 32;         // deposit columns 1 .. 61
-constexpr int WCOLS = DCOLS - 1;          // source columns 0 .. 60
+constexpr int SPMAX = 3;                  // largest shift block of a group
+constexpr int WSTEP = 32 - SPMAX;         // column offset of the second warp
+constexpr int DCOLS = WSTEP + 32;         // deposit columns 1 .. 60
+constexpr int WCOLS = DCOLS - 1;          // source columns 0 .. 59
 constexpr int NG = 4;                     // row groups
 constexpr int SH = 12;                    // rows a group deposits
 constexpr int WROWS = NG * SH;            // source rows 0 .. 47
@@ -238,24 +242,81 @@ __device__ __forceinline__ SrcEq source_eq(float4 m, float kq) {
   return q;
 }
 
+__device__ __forceinline__ float type_of(float c1, float nxf, float nyf) {
+  return __fmaf_rn(65536.0f, c1,
+                   __fmaf_rn(256.0f, __fadd_rn(nxf, 128.0f),
+                             __fadd_rn(nyf, 128.0f)));
+}
 __device__ __forceinline__ float type_id(const SrcEq& q) {
-  return q.emits ? __fmaf_rn(65536.0f, q.c1,
-                             __fmaf_rn(256.0f, __fadd_rn(q.nxf, 128.0f),
-                                       __fadd_rn(q.nyf, 128.0f)))
-                 : kNoType;
+  return q.emits ? type_of(q.c1, q.nxf, q.nyf) : kNoType;
 }
 
-// Statistics of a window walk, per thread until reduce_stats combines them
-// over the block.
-struct WinStats {
-  float tmin, tmax, tnext;      // types: smallest, largest, next group
-  float nxmin, nymin, c1min;    // over emitting sources
-  unsigned clamps;              // clamped energies of owned nodes
-  bool any;                     // a source took part in the deposit
+// Statistics of a window walk, per thread until
+// reduce_gstats combines them over the block: smallest and largest c1 and
+// shift over the emitting sources, the next group above the walk's, whether
+// a source of the walk's group was deposited, whether an emitting source
+// lies below the assumed minima, and the clamped energies of owned nodes.
+struct GStats {
+  float c1min, nxmin, nymin, tnext, c1max, nxmax, nymax;
+  unsigned clamps;
+  bool any, under;
 };
-__device__ __forceinline__ WinStats stats_init() {
-  return WinStats{kNoType, -1.0f, kNoType, kNoType, kNoType, kNoType, 0u,
-                  false};
+__device__ __forceinline__ GStats gstats_init() {
+  return GStats{kNoType, kNoType, kNoType, kNoType, -kNoType, -kNoType,
+                -kNoType, 0u, false, false};
+}
+__device__ __forceinline__ void gstats_add(GStats& st, bool emits, float c1,
+                                           float nxf, float nyf) {
+  if (emits) {
+    st.c1min = fminf(st.c1min, c1);
+    st.c1max = fmaxf(st.c1max, c1);
+    st.nxmin = fminf(st.nxmin, nxf);
+    st.nxmax = fmaxf(st.nxmax, nxf);
+    st.nymin = fminf(st.nymin, nyf);
+    st.nymax = fmaxf(st.nymax, nyf);
+  }
+}
+
+// Block reduction of GStats (all threads call it and get the result; it
+// holds the barrier that makes a walk's deposits visible).  The values are
+// small integers, reduced as ints.
+constexpr int NGSTAT = 9;
+__device__ __forceinline__ void reduce_gstats(GStats& st, int* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr unsigned F = 0xffffffffu;
+  int v[NGSTAT];
+  v[0] = __reduce_min_sync(F, (int)st.c1min);
+  v[1] = __reduce_min_sync(F, (int)st.nxmin);
+  v[2] = __reduce_min_sync(F, (int)st.nymin);
+  v[3] = __reduce_min_sync(F, (int)st.tnext);
+  v[4] = __reduce_max_sync(F, (int)st.c1max);
+  v[5] = __reduce_max_sync(F, (int)st.nxmax);
+  v[6] = __reduce_max_sync(F, (int)st.nymax);
+  v[7] = __any_sync(F, st.any) ? 1 : 0;
+  v[8] = __any_sync(F, st.under) ? 1 : 0;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NGSTAT; ++k) red[k * NWARP + warp] = v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NGSTAT; ++k) v[k] = red[k * NWARP];
+#pragma unroll
+  for (int w = 1; w < NWARP; ++w) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = min(v[k], red[k * NWARP + w]);
+#pragma unroll
+    for (int k = 4; k < NGSTAT; ++k) v[k] = max(v[k], red[k * NWARP + w]);
+  }
+  st.c1min = (float)v[0];
+  st.nxmin = (float)v[1];
+  st.nymin = (float)v[2];
+  st.tnext = (float)v[3];
+  st.c1max = (float)v[4];
+  st.nxmax = (float)v[5];
+  st.nymax = (float)v[6];
+  st.any = v[7] != 0;
+  st.under = v[8] != 0;
 }
 
 // Where a thread's column sits and how it reads its sources.
@@ -276,9 +337,10 @@ __device__ __forceinline__ Column column_of(const StepArgs& a, int x0, int R,
   c.flipx = false;
   c.gx = (interior || !c.col_valid) ? c.sx
                                     : axis_src(a.bc_x, a.nx, c.sx, &c.flipx);
-  // deposits of column 0 are never read; the second warp's first two lanes
-  // repeat the first warp's last two columns
-  c.store_col = c.wx == 0 ? c.lane >= 1 : c.lane >= 2;
+  // deposits of column 0 are never read; the second warp's first SPMAX
+  // lanes repeat the first warp's last SPMAX columns (and lack the parts
+  // that shuffles from farther left would bring)
+  c.store_col = c.wx == 0 ? c.lane >= 1 : c.lane >= SPMAX;
   c.col_own = c.store_col && c.lx >= R && c.lx < R + TX && c.sx < a.nx;
   return c;
 }
@@ -372,7 +434,7 @@ __device__ __forceinline__ void walk_one_type(
     const StepArgs& a, float4* __restrict__ D1, float4* __restrict__ D2,
     float* rbase, int x0, int y0, int R, int TX, int TY, bool interior,
     float Tin, const float4* cm, float* T0p, bool count_clamps,
-    WinStats& st) {
+    GStats& st) {
   const Column col = column_of(a, x0, R, TX, interior);
   const int ly0 = SH * col.g;
   const float kq = a.k.kq_f;
@@ -417,16 +479,9 @@ __device__ __forceinline__ void walk_one_type(
       qn = row_eq(r + 1, slot);
       slot = slot + 1 == PF ? 0 : slot + 1;
     }
-    const float id = type_id(q);
-    const bool mine = id == T;
+    const bool mine = type_id(q) == T;
     st.any |= mine;
-    st.tmin = fminf(st.tmin, id);
-    st.tmax = fmaxf(st.tmax, q.emits ? id : -1.0f);
-    if (q.emits) {
-      st.nxmin = fminf(st.nxmin, q.nxf);
-      st.nymin = fminf(st.nymin, q.nyf);
-      st.c1min = fminf(st.c1min, q.c1);
-    }
+    gstats_add(st, q.emits, q.c1, q.nxf, q.nyf);
     if (q.clamp && r >= own_lo && r <= own_hi) st.clamps += 1;
     // level records L_v = d_v (1, V_x, V_y, E_b) of the sources of type T
     const float4 v4 = f4(1.0f, q.Vx, q.Vy, q.Eb);
@@ -471,13 +526,38 @@ __device__ __forceinline__ void source_type(float4 m, float kq, bool& emits,
              : kNoType;
 }
 
-// Statistics walk of a tile queued as mixed: the types of every window
-// source (smallest, largest, minima of c1 and n) and the clamped energies
-// of the owned nodes, without deposits.
+// Shift block of a window's groups: the larger spread of n over the
+// window's emitting sources, at most SPMAX.
+__device__ __forceinline__ int block_of(const GStats& st) {
+  const float s = fmaxf(st.nxmax - st.nxmin, st.nymax - st.nymin) + 1.0f;
+  return s <= 1.0f ? 1 : (s >= (float)SPMAX ? SPMAX : (int)s);
+}
+
+// Per-tile record a step leaves for the next: 0 when the window held one
+// type (or nothing), else bit 31 with the window's smallest c1 and shift and
+// its block size, or bit 31 and bit 30 when those do not fit the record.
+__device__ __forceinline__ unsigned rec_encode(float c1min, float nxmin,
+                                               float nymin, int S) {
+  if (!(c1min <= 63.0f && nxmin >= -128.0f && nxmin <= 127.0f &&
+        nymin >= -128.0f && nymin <= 127.0f))
+    return 0xc0000000u;
+  return 0x80000000u | ((unsigned)(S - 1) << 24) | ((unsigned)c1min << 16) |
+         ((unsigned)((int)nxmin + 128) << 8) | (unsigned)((int)nymin + 128);
+}
+__device__ __forceinline__ unsigned rec_of(const GStats& st) {
+  if (st.c1max < 0.0f) return 0u;   // nothing emits
+  if (st.c1min == st.c1max && st.nxmin == st.nxmax && st.nymin == st.nymax)
+    return 0u;
+  return rec_encode(st.c1min, st.nxmin, st.nymin, block_of(st));
+}
+
+// Statistics walk of a queued tile without a usable record: c1 and shifts
+// of every window source and the clamped energies of the owned nodes,
+// without deposits.
 __device__ __forceinline__ void walk_stats(const StepArgs& a, float* rbase,
                                            int x0, int y0, int R, int TX,
                                            int TY, bool interior,
-                                           WinStats& st) {
+                                           GStats& st) {
   const Column col = column_of(a, x0, R, TX, interior);
   const int ly0 = SH * col.g;
   const float kq = a.k.kq_f;
@@ -501,60 +581,61 @@ __device__ __forceinline__ void walk_stats(const StepArgs& a, float* rbase,
     bool emits, clamp;
     float id, c1, nxf, nyf;
     source_type(m, kq, emits, clamp, id, c1, nxf, nyf);
-    st.tmin = fminf(st.tmin, id);
-    st.tmax = fmaxf(st.tmax, emits ? id : -1.0f);
-    if (emits) {
-      st.nxmin = fminf(st.nxmin, nxf);
-      st.nymin = fminf(st.nymin, nyf);
-      st.c1min = fminf(st.c1min, c1);
-    }
+    gstats_add(st, emits, c1, nxf, nyf);
     if (clamp && r >= own_lo && r <= own_hi) st.clamps += 1;
   }
 }
 
-// Group of an emitting source in the general walk: c1 relative to the
-// tile's smallest, and its shift n relative to the tile's smallest, in
-// blocks of two per axis.
-__device__ __forceinline__ float group_id(const SrcEq& q, float c1min,
-                                          float nxmin, float nymin) {
-  if (!q.emits) return kNoType;
-  const float gx = floorf(__fsub_rn(q.nxf, nxmin) * 0.5f);
-  const float gy = floorf(__fsub_rn(q.nyf, nymin) * 0.5f);
-  return __fmaf_rn(65536.0f, __fsub_rn(q.c1, c1min), __fmaf_rn(256.0f, gx, gy));
-}
-
-// Source of the general walk: level records and the hat weights over
-// offsets {0, 1, 2} per axis (dn = n - base in {0, 1}).
+// A group walk's view of one source: its level records (zero unless the
+// source is in the group) and its hat weights over offsets 0 .. S per axis.
+template <int S>
 struct GSrc {
   float4 l1, l2;
-  float ax0, ax1, ax2, ay0, ay1, ay2;
+  float ax[S + 1], ay[S + 1];
 };
 
-// General walk for group G (c1 = c1min + Cc, n in {a, a+1} x {b, b+1} with
-// a = nxmin + 2 GX, b = nymin + 2 GY): deposits D(q) = sum over the
-// group's sources s and corners k of w_k(s) L(s) at q = s + (n - base) + k,
-// and finds the next group above G.
-__device__ __forceinline__ void walk_general(
+// Group walk (S = shift block): deposits the sources of group G, i.e. c1 =
+// c1m + Gc and n in {a .. a+S-1} x {b .. b+S-1} with a = nxm + S GX,
+// b = nym + S GY (G = Gc 65536 + GX 256 + GY):
+//   D(q) = sum over the group's sources s and offsets o in {0 .. S}^2 of
+//          h_x(o_x) h_y(o_y) L(s),  q = s + o,
+// h the hat weights of eq 29 at dn = n - (a, b): (1 - f) at dn, f at dn + 1.
+// Deposit row t takes the sources of rows t - S .. t of this column (kept
+// from the rows walked before) and, for o_x > 0, those of the columns to
+// the left (shuffles by o_x).  Also gathers the window statistics and the
+// next group above G.
+template <int S>
+__device__ __forceinline__ void walk_group(
     const StepArgs& a, float4* __restrict__ D1, float4* __restrict__ D2,
-    float* rbase, int x0, int y0, int R, int TX, bool interior, float G,
-    float c1min,
-    float nxmin, float nymin, WinStats& st) {
+    float* rbase, int x0, int y0, int R, int TX, int TY, bool interior,
+    float G, float c1m, float nxm, float nym, bool count_clamps,
+    GStats& st) {
   const Column col = column_of(a, x0, R, TX, interior);
-  const int ly0 = SH * col.g - 1;
+  const int ly0 = SH * col.g - (S - 1);
+  constexpr int LAST = SH + S - 1;
   const float kq = a.k.kq_f;
+  // rows of this walk whose node the tile owns and that lie in the group's
+  // deposit rows (each owned node counted by one walk)
+  const int own_lo = max(S, R - ly0);
+  const int own_hi = col.col_own && count_clamps
+                         ? min(min(LAST, R + TY - 1 - ly0), a.ny - 1 - (y0 - R) - ly0)
+                         : -1;
   const float Gc = floorf(G * (1.0f / 65536.0f));
   const float Gr = __fmaf_rn(-65536.0f, Gc, G);
   const float GX = floorf(Gr * (1.0f / 256.0f));
   const float GY = __fmaf_rn(-256.0f, GX, Gr);
-  const float bx = __fmaf_rn(2.0f, GX, nxmin), by = __fmaf_rn(2.0f, GY, nymin);
-  GSrc p1, p2;
-  p1.l1 = p1.l2 = f4(0.f, 0.f, 0.f, 0.f);
-  p1.ax0 = p1.ax1 = p1.ax2 = p1.ay0 = p1.ay1 = p1.ay2 = 0.0f;
-  p2 = p1;
+  const float Sf = (float)S, rS = 1.0f / (float)S;   // rS >= 1/S: exact floors
+  // h[k]: the source k + 1 rows above the current one
+  GSrc<S> h[S];
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    h[k].l1 = h[k].l2 = f4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int o = 0; o <= S; ++o) h[k].ax[o] = h[k].ay[o] = 0.0f;
+  }
   SrcRing ring = ring_of(a, rbase);
 #pragma unroll
   for (int k = 0; k < PF; ++k) ring.issue(a, col, y0, R, ly0 + k, k, interior);
-  constexpr int LAST = SH + 1;
   auto row_eq = [&](int r, int slot) {
     if (r + PF - 1 <= LAST)
       cp_async_wait<PF - 1>();
@@ -574,53 +655,63 @@ __device__ __forceinline__ void walk_general(
       qn = row_eq(r + 1, slot);
       slot = slot + 1 == PF ? 0 : slot + 1;
     }
-    const float gid = group_id(q, c1min, nxmin, nymin);
+    // the source's group, relative to the assumed minima
+    const float dc = __fsub_rn(q.c1, c1m);
+    const float dx = __fsub_rn(q.nxf, nxm), dy = __fsub_rn(q.nyf, nym);
+    const float gx = floorf(dx * rS), gy = floorf(dy * rS);
+    const float gid = q.emits ? __fmaf_rn(65536.0f, dc, __fmaf_rn(256.0f, gx, gy))
+                              : kNoType;
     const bool mine = gid == G;
     st.any |= mine;
     st.tnext = fminf(st.tnext, gid > G ? gid : kNoType);
-    GSrc cur;
+    st.under |= q.emits && fminf(dc, fminf(dx, dy)) < 0.0f;
+    gstats_add(st, q.emits, q.c1, q.nxf, q.nyf);
+    if (q.clamp && r >= own_lo && r <= own_hi) st.clamps += 1;
+    GSrc<S> cur;
     const float4 v4 = f4(1.0f, q.Vx, q.Vy, q.Eb);
     cur.l1 = mul4(mine ? q.d1 : 0.0f, v4);
     cur.l2 = mul4(mine ? q.d2 : 0.0f, v4);
-    // hat weights: dn = 0 -> (1 - f, f, 0), dn = 1 -> (0, 1 - f, f)
-    const bool sx1 = q.nxf != bx, sy1 = q.nyf != by;
+    const float dnx = __fmaf_rn(-Sf, gx, dx), dny = __fmaf_rn(-Sf, gy, dy);
     const float gx1 = __fsub_rn(1.0f, q.fx), gy1 = __fsub_rn(1.0f, q.fy);
-    cur.ax0 = sx1 ? 0.0f : gx1;
-    cur.ax1 = sx1 ? gx1 : q.fx;
-    cur.ax2 = sx1 ? q.fx : 0.0f;
-    cur.ay0 = sy1 ? 0.0f : gy1;
-    cur.ay1 = sy1 ? gy1 : q.fy;
-    cur.ay2 = sy1 ? q.fy : 0.0f;
-    // own-column parts landing 0, 1, 2 columns to the right: rows t
-    // (offset 0), t - 1 (offset 1) and t - 2 (offset 2) of this column
-    float4 D1r, D2r;
-    {
-      const float w0 = __fmul_rn(cur.ax2, cur.ay0), w1 = __fmul_rn(p1.ax2, p1.ay1),
-                  w2 = __fmul_rn(p2.ax2, p2.ay2);
-      const float4 t1 = fma4(w0, cur.l1, fma4(w1, p1.l1, mul4(w2, p2.l1)));
-      const float4 t2 = fma4(w0, cur.l2, fma4(w1, p1.l2, mul4(w2, p2.l2)));
-      const float4 z = f4(0.f, 0.f, 0.f, 0.f);
-      const bool ok = col.lane >= 2;
-      const float4 s1 = shfl_up4n(t1, 2), s2 = shfl_up4n(t2, 2);
-      D1r = ok ? s1 : z;
-      D2r = ok ? s2 : z;
+#pragma unroll
+    for (int o = 0; o <= S; ++o) {
+      const float of = (float)o;
+      cur.ax[o] = dnx == of ? gx1 : (dnx == of - 1.0f ? q.fx : 0.0f);
+      cur.ay[o] = dny == of ? gy1 : (dny == of - 1.0f ? q.fy : 0.0f);
     }
-    {
-      const float w0 = __fmul_rn(cur.ax1, cur.ay0), w1 = __fmul_rn(p1.ax1, p1.ay1),
-                  w2 = __fmul_rn(p2.ax1, p2.ay2);
-      const float4 t1 = fma4(w0, cur.l1, fma4(w1, p1.l1, mul4(w2, p2.l1)));
-      const float4 t2 = fma4(w0, cur.l2, fma4(w1, p1.l2, mul4(w2, p2.l2)));
-      const float4 s1 = shfl_up4(t1), s2 = shfl_up4(t2);
-      const float w0b = __fmul_rn(cur.ax0, cur.ay0), w1b = __fmul_rn(p1.ax0, p1.ay1),
-                  w2b = __fmul_rn(p2.ax0, p2.ay2);
-      const float4 o1 = fma4(w0b, cur.l1, fma4(w1b, p1.l1, mul4(w2b, p2.l1)));
-      const float4 o2 = fma4(w0b, cur.l2, fma4(w1b, p1.l2, mul4(w2b, p2.l2)));
-      D1r = add4(add4(o1, s1), D1r);
-      D2r = add4(add4(o2, s2), D2r);
+    // deposit row ly: the part of this column's sources landing o_x columns
+    // to the right, summed over their rows, then moved right by shuffles
+    float4 D1r = f4(0.f, 0.f, 0.f, 0.f), D2r = D1r;
+#pragma unroll
+    for (int ox = 0; ox <= S; ++ox) {
+      // oldest source first, the current one last: with S = 1 the one-type
+      // walk's operations in its order, so both give the same bits
+      const float wl = __fmul_rn(h[S - 1].ax[ox], h[S - 1].ay[S]);
+      float4 t1 = mul4(wl, h[S - 1].l1), t2 = mul4(wl, h[S - 1].l2);
+#pragma unroll
+      for (int k = S - 2; k >= 0; --k) {
+        const float w = __fmul_rn(h[k].ax[ox], h[k].ay[k + 1]);
+        t1 = fma4(w, h[k].l1, t1);
+        t2 = fma4(w, h[k].l2, t2);
+      }
+      const float w0 = __fmul_rn(cur.ax[ox], cur.ay[0]);
+      t1 = fma4(w0, cur.l1, t1);
+      t2 = fma4(w0, cur.l2, t2);
+      if (ox == 0) {
+        D1r = t1;
+        D2r = t2;
+      } else {
+        const float4 z = f4(0.f, 0.f, 0.f, 0.f);
+        const bool ok = col.lane >= ox;
+        const float4 s1 = shfl_up4n(t1, ox), s2 = shfl_up4n(t2, ox);
+        D1r = add4(D1r, ok ? s1 : z);
+        D2r = add4(D2r, ok ? s2 : z);
+      }
     }
-    p2 = p1;
-    p1 = cur;
-    if (r >= 2 && col.store_col) {
+#pragma unroll
+    for (int k = S - 1; k > 0; --k) h[k] = h[k - 1];
+    h[0] = cur;
+    if (r >= S && col.store_col) {
       D1[ly * DP + col.lx] = D1r;
       D2[ly * DP + col.lx] = D2r;
     }
@@ -853,55 +944,13 @@ __device__ __forceinline__ void finish_tile(const StepArgs& a, int x0, int y0,
   }
 }
 
-// Every packet of a one-type walk (slack 0) or of a general walk's group
-// (slack 1: its base may lie one below its sources' shift) within reach R
-// reads deposits that lie in rows 1 .. 48 and columns 1 .. 61.
+// Every packet of a one-type walk (slack 0) or of a group walk (slack 1:
+// its base may lie below its sources' shift) within reach R reads deposits
+// that lie in rows 1 .. 48 and columns 1 .. 60.
 __device__ __forceinline__ bool type_fits(Type ty, int R, int slack) {
   const int c2 = ty.c1 + 1;
   return ty.nx <= R - 1 - c2 && -ty.nx <= R - c2 + slack &&
          ty.ny <= R - 1 - c2 && -ty.ny <= R - c2 + slack;
-}
-
-// Block reduction of the window statistics (all threads call it; it holds
-// the barrier that makes the deposits visible).  Minima are reduced on
-// non-negative bit patterns (n shifted by 128, -1 mapped to 0 for tmax).
-constexpr int NSTAT = 6;
-__device__ __forceinline__ void reduce_stats(WinStats& st, unsigned* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned v[NSTAT];
-  v[0] = __reduce_min_sync(0xffffffffu, __float_as_uint(st.tmin));
-  v[1] = __reduce_min_sync(0xffffffffu, __float_as_uint(st.tnext));
-  v[2] = __reduce_min_sync(0xffffffffu, __float_as_uint(st.nxmin + 128.0f));
-  v[3] = __reduce_min_sync(0xffffffffu, __float_as_uint(st.nymin + 128.0f));
-  v[4] = __reduce_min_sync(0xffffffffu, __float_as_uint(st.c1min));
-  // largest type + 1 (0: no emitting source); any = bit 31
-  const unsigned mx = __reduce_max_sync(
-      0xffffffffu, st.tmax < 0.0f ? 0u : __float_as_uint(st.tmax) + 1u);
-  const unsigned an = __any_sync(0xffffffffu, st.any) ? 0x80000000u : 0u;
-  v[5] = mx | an;
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < NSTAT; ++k) red[k * NWARP + warp] = v[k];
-  }
-  __syncthreads();
-  unsigned r[NSTAT] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu,
-                       0xffffffffu, 0u};
-#pragma unroll
-  for (int w = 0; w < NWARP; ++w) {
-#pragma unroll
-    for (int k = 0; k < NSTAT - 1; ++k) r[k] = min(r[k], red[k * NWARP + w]);
-    const unsigned t = red[(NSTAT - 1) * NWARP + w];
-    r[NSTAT - 1] = max(r[NSTAT - 1] & 0x7fffffffu, t & 0x7fffffffu) |
-                   ((r[NSTAT - 1] | t) & 0x80000000u);
-  }
-  st.tmin = __uint_as_float(r[0]);
-  st.tnext = __uint_as_float(r[1]);
-  st.nxmin = __uint_as_float(r[2]) - 128.0f;
-  st.nymin = __uint_as_float(r[3]) - 128.0f;
-  st.c1min = __uint_as_float(r[4]);
-  const unsigned m = r[5] & 0x7fffffffu;
-  st.tmax = m == 0 ? -1.0f : __uint_as_float(m - 1u);
-  st.any = (r[5] & 0x80000000u) != 0;
 }
 
 // Tile geometry of a step: reach R (at least 1), tile size, tile count.
@@ -986,7 +1035,7 @@ __device__ __forceinline__ void commit_clamps(const StepArgs& a, unsigned c) {
 template <bool KAHAN>
 __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
   extern __shared__ __align__(16) float4 dsm[];
-  __shared__ unsigned red[NSTAT * NWARP];
+  __shared__ int red[NGSTAT * NWARP];
   __shared__ TileRed tred;
   float4* D1 = dsm;
   float4* D2 = dsm + PLANE;
@@ -1017,7 +1066,7 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
   // guess: the type of the tile's central node (every thread forms it; its
   // load overlaps the walk's first loads)
   float T0;
-  WinStats st = stats_init();
+  GStats st = gstats_init();
   {
     const int cx = min(x0 + TX / 2, a.nx - 1), cy = min(y0 + TY / 2, a.ny - 1);
     const long long i = (long long)cy * a.nx + cx;
@@ -1029,10 +1078,14 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
                   &T0, true, st);
   }
   const unsigned my_clamps = st.clamps;
-  reduce_stats(st, red);  // includes the barrier after the deposits
-  const bool none = st.tmax < 0.0f;
-  if (!none && !(st.tmin == st.tmax && st.tmin == T0)) {
-    if (tid == 0) a.hint[b] = 1;
+  reduce_gstats(st, red);  // includes the barrier after the deposits
+  const bool none = st.c1max < 0.0f;
+  const bool one = st.c1min == st.c1max && st.nxmin == st.nxmax &&
+                   st.nymin == st.nymax;
+  if (!none && !(one && T0 == type_of(st.c1min, st.nxmin, st.nymin))) {
+    // the window's smallest c1 and shift and its block (exact for this
+    // step): the mixed-window kernel starts from them
+    if (tid == 0) a.hint[b] = rec_of(st);
     enqueue();            // the mixed-window kernel counts its clamps
     return;
   }
@@ -1053,15 +1106,18 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
 }
 
 // The step, second kernel: persistent blocks take the tiles the first
-// kernel queued, one at a time.  Per tile a statistics walk; a window that
-// holds one type after all takes the one-type walk; otherwise one general
-// walk per group of sources (same c1, shifts within a 2 x 2 block), in
-// ascending group order, each adding its arrivals.  What a tile computes
-// depends only on the state, not on the queue order or the hints.
+// kernel queued, one at a time.  A tile's sources are grouped by c1 and by
+// shift blocks (c1 relative to the window's smallest, n relative to the
+// smallest shift in blocks of S per axis); one group walk per group, in
+// ascending group order, each gather adding its arrivals.  The minima and S
+// come from the tile's record of the previous step (or this step's first
+// kernel); when the first walk finds a source below them, the walks restart
+// from the true minima.  What a tile computes depends only on the state and
+// on the minima and S it ends with, not on the queue order.
 template <bool KAHAN>
 __global__ void __launch_bounds__(NTHR, 2) step2d_ds_mixed(const StepArgs a) {
   extern __shared__ __align__(16) float4 dsm[];
-  __shared__ unsigned red[NSTAT * NWARP];
+  __shared__ int red[NGSTAT * NWARP];
   __shared__ TileRed tred;
   __shared__ int s_k;
   float4* D1 = dsm;
@@ -1083,58 +1139,80 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds_mixed(const StepArgs a) {
     const int x0 = tx_i * TX, y0 = ty_i * TY;
     const bool interior = x0 - R >= 0 && x0 - R + WCOLS <= a.nx &&
                           y0 - R >= 0 && y0 - R + WROWS <= a.ny;
-    WinStats st = stats_init();
-    walk_stats(a, rbase, x0, y0, R, TX, TY, interior, st);
-    commit_clamps(a, st.clamps);
-    reduce_stats(st, red);
-    TileOut to = tile_out_init();
-    const bool none = st.tmax < 0.0f;
-    if (tid == 0) a.hint[b] = (!none && st.tmin != st.tmax) ? 1 : 0;
-    if (none) {
-      finish_tile(a, x0, y0, TX, TY, true, to);
-    } else if (st.tmin == st.tmax) {
-      const float T = st.tmin;
-      WinStats s1 = stats_init();
-      walk_one_type(a, D1, D2, rbase, x0, y0, R, TX, TY, interior, T,
-                    nullptr, nullptr, false, s1);
-      reduce_stats(s1, red);
-      const Type ty = decode_type(T);
-      if (type_fits(ty, R, 0)) {
-        gather_dispatch<KAHAN>(a, D1, D2, x0, y0, R, TX, TY, ty, true, true,
-                               to);
-      } else {
-        if (tid == 0) atomicOr(&a.scr->flags, kFlagReach);
-        finish_tile(a, x0, y0, TX, TY, true, to);
-      }
+    const unsigned rec = a.hint[b];
+    float c1m, nxm, nym;
+    int S;
+    bool counted = false, checked = false;
+    if ((rec & 0xc0000000u) == 0x80000000u) {
+      S = min((int)((rec >> 24) & 3u) + 1, SPMAX);
+      c1m = (float)((rec >> 16) & 0xffu);
+      nxm = (float)((int)((rec >> 8) & 0xffu) - 128);
+      nym = (float)((int)(rec & 0xffu) - 128);
     } else {
-      const float c1min = st.c1min, nxmin = st.nxmin, nymin = st.nymin;
-      float G = 0.0f;  // (c1min, blocks (0, 0)); possibly empty
-      bool first = true;
-      while (true) {
-        __syncthreads();  // the previous gather is done with the deposits
-        WinStats s2 = stats_init();
-        walk_general(a, D1, D2, rbase, x0, y0, R, TX, interior, G, c1min,
-                     nxmin, nymin, s2);
-        reduce_stats(s2, red);
-        const bool last = !(s2.tnext < kNoType);
-        const float Gc = floorf(G * (1.0f / 65536.0f));
-        const float Gr = __fmaf_rn(-65536.0f, Gc, G);
-        const float GX = floorf(Gr * (1.0f / 256.0f));
-        const float GY = __fmaf_rn(-256.0f, GX, Gr);
-        const Type ty{(int)__fmaf_rn(2.0f, GX, nxmin),
-                      (int)__fmaf_rn(2.0f, GY, nymin), (int)(c1min + Gc)};
-        if (s2.any && type_fits(ty, R, 1)) {
-          gather_dispatch<KAHAN>(a, D1, D2, x0, y0, R, TX, TY, ty, first,
-                                 last, to);
-          first = false;
-        } else {
-          if (s2.any && tid == 0) atomicOr(&a.scr->flags, kFlagReach);
-          if (last) finish_tile(a, x0, y0, TX, TY, first, to);
-        }
-        if (last) break;
-        G = s2.tnext;
-      }
+      GStats s0 = gstats_init();
+      walk_stats(a, rbase, x0, y0, R, TX, TY, interior, s0);
+      commit_clamps(a, s0.clamps);
+      counted = true;
+      reduce_gstats(s0, red);
+      c1m = s0.c1min;
+      nxm = s0.nxmin;
+      nym = s0.nymin;
+      S = block_of(s0);
+      checked = true;
     }
+    TileOut to = tile_out_init();
+    GStats fin = gstats_init();
+    float G = 0.0f;  // (c1m, blocks (0, 0)); possibly empty
+    bool first = true;
+    while (true) {
+      __syncthreads();  // the previous gather and statistics are done
+      GStats s2 = gstats_init();
+      if (S == 1)
+        walk_group<1>(a, D1, D2, rbase, x0, y0, R, TX, TY, interior, G, c1m,
+                      nxm, nym, !counted, s2);
+      else if (S == 2)
+        walk_group<2>(a, D1, D2, rbase, x0, y0, R, TX, TY, interior, G, c1m,
+                      nxm, nym, !counted, s2);
+      else
+        walk_group<3>(a, D1, D2, rbase, x0, y0, R, TX, TY, interior, G, c1m,
+                      nxm, nym, !counted, s2);
+      if (!counted) commit_clamps(a, s2.clamps);
+      counted = true;
+      reduce_gstats(s2, red);
+      if (!checked) {
+        // the groups follow from this step's state alone: minima and block
+        // taken from an earlier step are redone when they differ
+        checked = true;
+        if (s2.under || c1m != s2.c1min || nxm != s2.nxmin ||
+            nym != s2.nymin || S != block_of(s2)) {
+          c1m = s2.c1min;
+          nxm = s2.nxmin;
+          nym = s2.nymin;
+          S = block_of(s2);
+          G = 0.0f;
+          continue;
+        }
+      }
+      fin = s2;
+      const bool last = !(s2.tnext < kNoType);
+      const float Gc = floorf(G * (1.0f / 65536.0f));
+      const float Gr = __fmaf_rn(-65536.0f, Gc, G);
+      const float GX = floorf(Gr * (1.0f / 256.0f));
+      const float GY = __fmaf_rn(-256.0f, GX, Gr);
+      const Type ty{(int)__fmaf_rn((float)S, GX, nxm),
+                    (int)__fmaf_rn((float)S, GY, nym), (int)(c1m + Gc)};
+      if (s2.any && type_fits(ty, R, 1)) {
+        gather_dispatch<KAHAN>(a, D1, D2, x0, y0, R, TX, TY, ty, first, last,
+                               to);
+        first = false;
+      } else {
+        if (s2.any && tid == 0) atomicOr(&a.scr->flags, kFlagReach);
+        if (last) finish_tile(a, x0, y0, TX, TY, first, to);
+      }
+      if (last) break;
+      G = s2.tnext;
+    }
+    if (tid == 0) a.hint[b] = rec_of(fin);
     tile_publish(a, b, to, tred);
     __syncthreads();  // the next tile reuses the deposits and the ring
   }

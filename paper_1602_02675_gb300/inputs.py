@@ -107,6 +107,32 @@ def banded_prims(nx: int, ny: int, seed: int, u_band=(0.1, 0.8),
     return [rho.ravel(), u.ravel(), v.ravel(), p.ravel()]
 
 
+def patch_prims(nx: int, ny: int, seed: int, patch: int = 7,
+                u_max: float = 1.3, p_over_rho=(0.3, 3.5)):
+    """2-D primitive fields (rho, u, v, p), x fastest, made of square
+    patches of `patch` nodes with their own random velocity (|u|, |v| <
+    u_max) and p/rho (log-uniform in the given range), each with a gentle
+    smooth ripple: at lambda = 1 a window of a few dozen patches holds
+    lattice shifts floor(V) of both signs on both axes and several level
+    speeds at once (c1 up to 2, reach up to 6 over the first steps)."""
+    rng = np.random.default_rng(seed)
+    px, py = -(-nx // patch), -(-ny // patch)
+    u = rng.uniform(-u_max, u_max, (py, px))
+    v = rng.uniform(-u_max, u_max, (py, px))
+    por = np.exp(rng.uniform(np.log(p_over_rho[0]), np.log(p_over_rho[1]),
+                             (py, px)))
+    rho = rng.uniform(0.5, 1.5, (py, px))
+    iy = np.arange(ny) // patch
+    ix = np.arange(nx) // patch
+    X, Y = np.meshgrid((np.arange(nx) + 0.5) / nx, (np.arange(ny) + 0.5) / ny)
+    ripple = 1.0 + 0.02 * np.sin(2 * np.pi * (3 * X + 2 * Y) + rng.uniform(0, 6))
+    R = rho[iy][:, ix] * ripple
+    U = u[iy][:, ix] * ripple
+    V = v[iy][:, ix] / ripple
+    P = R * por[iy][:, ix]
+    return [R.ravel(), U.ravel(), V.ravel(), P.ravel()]
+
+
 def random_node_prims(dim: int, n: int, seed: int):
     """Independent random states per node (harsh: exercises every level
     count, fractional velocities of both signs, large reach)."""

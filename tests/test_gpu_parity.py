@@ -159,6 +159,53 @@ def test_fast_flow_parity(bcs, bands, p_over_rho):
         _assert_l1(g, o, 2)
 
 
+@pytest.mark.parametrize("kahan", [0, 1])
+@pytest.mark.parametrize("bcs", [(L.PERIODIC, L.PERIODIC),
+                                 (L.TRANSMISSIVE, L.REFLECTING)])
+def test_patchwork_windows_many_groups_fp32_l1(bcs, kahan):
+    """Windows holding several level speeds and lattice shifts of both
+    signs on both axes: the mixed-window kernel's group walks (blocks of 1
+    to 3 shifts, several groups per tile, minima carried from step to
+    step).  FP32 within 1e-5 of range of the oracle after 1 and 4 steps."""
+    nx, ny = 150, 110
+    prims = I.patch_prims(nx, ny, seed=13)
+    for steps in (1, 4):
+        o = _oracle(2, nx, ny, *bcs, prims=prims, steps=steps)
+        g = _gpu(2, nx, ny, *bcs, prims=prims, steps=steps, precision=L.F32,
+                 kahan=kahan)
+        assert g["diag"]["flags"] == 0
+        _assert_l1(g, o, 2)
+
+
+@pytest.mark.parametrize("kahan", [0, 1])
+@pytest.mark.parametrize("seed", [14, 15])
+def test_fp32_square_step_depends_on_state_only(seed, kahan):
+    """The deposit kernels keep per-tile records of the windows they met
+    (starting guesses for the next step).  The result must not depend on
+    them: steps taken after checkpoints into fresh handles, whose records
+    are empty, equal the uninterrupted run bit for bit (lambda = 1, so the
+    checkpoint is exact)."""
+    nx, ny = 150, 110
+    prims = I.patch_prims(nx, ny, seed=seed)
+    cfg = L.make_config(2, nx, ny, precision=L.F32, bc_x=L.PERIODIC,
+                        bc_y=L.PERIODIC, kahan=kahan)
+    with L.Solver(cfg) as a:
+        a.set_primitives(*prims)
+        a.step(6)
+        ref = a.moments()
+    m = None
+    for part in (2, 3, 1):
+        with L.Solver(cfg) as b:
+            if m is None:
+                b.set_primitives(*prims)
+            else:
+                b.set_moments(m["rho"], m["mx"], m["my"], m["rhoE"])
+            b.step(part)
+            m = b.moments()
+    for f in FIELDS:
+        assert np.array_equal(m[f], ref[f]), f
+
+
 def test_fp32_reach_limit_beyond_register_window():
     """max_reach 8 exceeds the register kernel's fixed window (reach 6), so
     the FP32 handle without compensated sums steps with the exact-order
