@@ -369,15 +369,15 @@ struct SrcRing {
   float* base;
   const float* f[4];
   int stride_rows;
+  template <bool INT>
   __device__ __forceinline__ void issue(const StepArgs& a, const Column& c,
-                                        int y0, int R, int ly, int slot,
-                                        bool interior) {
+                                        int y0, int R, int ly, int slot) {
     const bool valid = c.col_valid && ly >= 0 && ly < WROWS;
     long long i = 0;
     if (valid) {
       const int sy = y0 - R + ly;
       bool flipy = false;
-      const int gy = interior ? sy : axis_src(a.bc_y, a.ny, sy, &flipy);
+      const int gy = INT ? sy : axis_src(a.bc_y, a.ny, sy, &flipy);
       i = (long long)gy * a.nx + c.gx;
     }
     float* d = base + slot * 4 * NTHR + threadIdx.x;
@@ -385,13 +385,14 @@ struct SrcRing {
     for (int k = 0; k < 4; ++k) cp_async4(d + k * NTHR, f[k] + i, valid);
     cp_async_commit();
   }
+  template <bool INT>
   __device__ __forceinline__ float4 take(const StepArgs& a, const Column& c,
-                                         int y0, int R, int ly, int slot,
-                                         bool interior) const {
+                                         int y0, int R, int ly,
+                                         int slot) const {
     const float* d = base + slot * 4 * NTHR + threadIdx.x;
     float4 m = f4(d[0], d[NTHR], d[2 * NTHR], d[3 * NTHR]);
     if (c.flipx) m.y = -m.y;
-    if (!interior && ly >= 0 && ly < WROWS) {
+    if (!INT && ly >= 0 && ly < WROWS) {
       bool flipy = false;
       axis_src(a.bc_y, a.ny, y0 - R + ly, &flipy);
       if (flipy) m.z = -m.z;
@@ -408,34 +409,16 @@ __device__ __forceinline__ SrcRing ring_of(const StepArgs& a, float* base) {
   return r;
 }
 
-// Moments of window source (column c, row ly); zero outside the window.
-__device__ __forceinline__ float4 load_src(const StepArgs& a, const Column& c,
-                                           int y0, int R, int ly,
-                                           bool interior) {
-  float4 m = f4(0.f, 0.f, 0.f, 0.f);
-  if (!c.col_valid || ly < 0 || ly >= WROWS) return m;
-  const int sy = y0 - R + ly;
-  bool flipy = false;
-  const int gy = interior ? sy : axis_src(a.bc_y, a.ny, sy, &flipy);
-  const long long i = (long long)gy * a.nx + c.gx;
-  m.x = __ldg(static_cast<const float*>(a.in[0]) + i);
-  m.y = __ldg(static_cast<const float*>(a.in[1]) + i);
-  m.z = __ldg(static_cast<const float*>(a.in[2]) + i);
-  m.w = __ldg(static_cast<const float*>(a.in[3]) + i);
-  if (c.flipx) m.y = -m.y;
-  if (flipy) m.z = -m.z;
-  return m;
-}
-
 // One-type walk: deposits the sources whose type is T (the corner weights
 // of eq 29 on offsets {0, 1}^2) and gathers the statistics of every source
 // (pass 0: types, minima, clamped energies of owned nodes).
+template <bool INT>
 __device__ __forceinline__ void walk_one_type(
     const StepArgs& a, float4* __restrict__ D1, float4* __restrict__ D2,
-    float* rbase, int x0, int y0, int R, int TX, int TY, bool interior,
+    float* rbase, int x0, int y0, int R, int TX, int TY,
     float Tin, const float4* cm, float* T0p, bool count_clamps,
     GStats& st) {
-  const Column col = column_of(a, x0, R, TX, interior);
+  const Column col = column_of(a, x0, R, TX, INT);
   const int ly0 = SH * col.g;
   const float kq = a.k.kq_f;
   // rows r of this walk whose node the tile owns (its energy clamps are
@@ -451,7 +434,7 @@ __device__ __forceinline__ void walk_one_type(
   // stall
   SrcRing ring = ring_of(a, rbase);
 #pragma unroll
-  for (int k = 0; k < PF; ++k) ring.issue(a, col, y0, R, ly0 + k, k, interior);
+  for (int k = 0; k < PF; ++k) ring.template issue<INT>(a, col, y0, R, ly0 + k, k);
   if (T0p) {
     // the tile's guess type, from the central node loaded by the caller
     *T0p = type_id(source_eq(*cm, kq));
@@ -465,8 +448,8 @@ __device__ __forceinline__ void walk_one_type(
       cp_async_wait<PF - 1>();
     else
       cp_async_wait<0>();
-    const float4 m = ring.take(a, col, y0, R, ly0 + r, slot, interior);
-    if (r + PF <= SH) ring.issue(a, col, y0, R, ly0 + r + PF, slot, interior);
+    const float4 m = ring.template take<INT>(a, col, y0, R, ly0 + r, slot);
+    if (r + PF <= SH) ring.template issue<INT>(a, col, y0, R, ly0 + r + PF, slot);
     return source_eq(m, kq);
   };
   SrcEq qn = row_eq(0, 0);
@@ -554,11 +537,11 @@ __device__ __forceinline__ unsigned rec_of(const GStats& st) {
 // Statistics walk of a queued tile without a usable record: c1 and shifts
 // of every window source and the clamped energies of the owned nodes,
 // without deposits.
+template <bool INT>
 __device__ __forceinline__ void walk_stats(const StepArgs& a, float* rbase,
                                            int x0, int y0, int R, int TX,
-                                           int TY, bool interior,
-                                           GStats& st) {
-  const Column col = column_of(a, x0, R, TX, interior);
+                                           int TY, GStats& st) {
+  const Column col = column_of(a, x0, R, TX, INT);
   const int ly0 = SH * col.g;
   const float kq = a.k.kq_f;
   const int own_lo = max(1, R - ly0);
@@ -567,7 +550,7 @@ __device__ __forceinline__ void walk_stats(const StepArgs& a, float* rbase,
                          : -1;
   SrcRing ring = ring_of(a, rbase);
 #pragma unroll
-  for (int k = 0; k < PF; ++k) ring.issue(a, col, y0, R, ly0 + k, k, interior);
+  for (int k = 0; k < PF; ++k) ring.template issue<INT>(a, col, y0, R, ly0 + k, k);
   int slot = 0;
 #pragma unroll 1
   for (int r = 0; r <= SH; ++r) {
@@ -575,8 +558,8 @@ __device__ __forceinline__ void walk_stats(const StepArgs& a, float* rbase,
       cp_async_wait<PF - 1>();
     else
       cp_async_wait<0>();
-    const float4 m = ring.take(a, col, y0, R, ly0 + r, slot, interior);
-    if (r + PF <= SH) ring.issue(a, col, y0, R, ly0 + r + PF, slot, interior);
+    const float4 m = ring.template take<INT>(a, col, y0, R, ly0 + r, slot);
+    if (r + PF <= SH) ring.template issue<INT>(a, col, y0, R, ly0 + r + PF, slot);
     slot = slot + 1 == PF ? 0 : slot + 1;
     bool emits, clamp;
     float id, c1, nxf, nyf;
@@ -604,13 +587,13 @@ struct GSrc {
 // from the rows walked before) and, for o_x > 0, those of the columns to
 // the left (shuffles by o_x).  Also gathers the window statistics and the
 // next group above G.
-template <int S>
+template <int S, bool INT>
 __device__ __forceinline__ void walk_group(
     const StepArgs& a, float4* __restrict__ D1, float4* __restrict__ D2,
-    float* rbase, int x0, int y0, int R, int TX, int TY, bool interior,
+    float* rbase, int x0, int y0, int R, int TX, int TY,
     float G, float c1m, float nxm, float nym, bool count_clamps,
     GStats& st) {
-  const Column col = column_of(a, x0, R, TX, interior);
+  const Column col = column_of(a, x0, R, TX, INT);
   const int ly0 = SH * col.g - (S - 1);
   constexpr int LAST = SH + S - 1;
   const float kq = a.k.kq_f;
@@ -635,14 +618,14 @@ __device__ __forceinline__ void walk_group(
   }
   SrcRing ring = ring_of(a, rbase);
 #pragma unroll
-  for (int k = 0; k < PF; ++k) ring.issue(a, col, y0, R, ly0 + k, k, interior);
+  for (int k = 0; k < PF; ++k) ring.template issue<INT>(a, col, y0, R, ly0 + k, k);
   auto row_eq = [&](int r, int slot) {
     if (r + PF - 1 <= LAST)
       cp_async_wait<PF - 1>();
     else
       cp_async_wait<0>();
-    const float4 m = ring.take(a, col, y0, R, ly0 + r, slot, interior);
-    if (r + PF <= LAST) ring.issue(a, col, y0, R, ly0 + r + PF, slot, interior);
+    const float4 m = ring.template take<INT>(a, col, y0, R, ly0 + r, slot);
+    if (r + PF <= LAST) ring.template issue<INT>(a, col, y0, R, ly0 + r + PF, slot);
     return source_eq(m, kq);
   };
   SrcEq qn = row_eq(0, 0);
@@ -1074,8 +1057,13 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
                         __ldg(static_cast<const float*>(a.in[1]) + i),
                         __ldg(static_cast<const float*>(a.in[2]) + i),
                         __ldg(static_cast<const float*>(a.in[3]) + i));
-    walk_one_type(a, D1, D2, rbase, x0, y0, R, TX, TY, interior, 0.0f, &m,
-                  &T0, true, st);
+    // interior windows need no boundary handling: their own, smaller walk
+    if (interior)
+      walk_one_type<true>(a, D1, D2, rbase, x0, y0, R, TX, TY, 0.0f, &m, &T0,
+                          true, st);
+    else
+      walk_one_type<false>(a, D1, D2, rbase, x0, y0, R, TX, TY, 0.0f, &m,
+                           &T0, true, st);
   }
   const unsigned my_clamps = st.clamps;
   reduce_gstats(st, red);  // includes the barrier after the deposits
@@ -1150,7 +1138,10 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds_mixed(const StepArgs a) {
       nym = (float)((int)(rec & 0xffu) - 128);
     } else {
       GStats s0 = gstats_init();
-      walk_stats(a, rbase, x0, y0, R, TX, TY, interior, s0);
+      if (interior)
+        walk_stats<true>(a, rbase, x0, y0, R, TX, TY, s0);
+      else
+        walk_stats<false>(a, rbase, x0, y0, R, TX, TY, s0);
       commit_clamps(a, s0.clamps);
       counted = true;
       reduce_gstats(s0, red);
@@ -1167,15 +1158,28 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds_mixed(const StepArgs a) {
     while (true) {
       __syncthreads();  // the previous gather and statistics are done
       GStats s2 = gstats_init();
-      if (S == 1)
-        walk_group<1>(a, D1, D2, rbase, x0, y0, R, TX, TY, interior, G, c1m,
-                      nxm, nym, !counted, s2);
-      else if (S == 2)
-        walk_group<2>(a, D1, D2, rbase, x0, y0, R, TX, TY, interior, G, c1m,
-                      nxm, nym, !counted, s2);
-      else
-        walk_group<3>(a, D1, D2, rbase, x0, y0, R, TX, TY, interior, G, c1m,
-                      nxm, nym, !counted, s2);
+      const bool cc = !counted;
+      if (interior) {
+        if (S == 1)
+          walk_group<1, true>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m,
+                              nxm, nym, cc, s2);
+        else if (S == 2)
+          walk_group<2, true>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m,
+                              nxm, nym, cc, s2);
+        else
+          walk_group<3, true>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m,
+                              nxm, nym, cc, s2);
+      } else {
+        if (S == 1)
+          walk_group<1, false>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m,
+                               nxm, nym, cc, s2);
+        else if (S == 2)
+          walk_group<2, false>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m,
+                               nxm, nym, cc, s2);
+        else
+          walk_group<3, false>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m,
+                               nxm, nym, cc, s2);
+      }
       if (!counted) commit_clamps(a, s2.clamps);
       counted = true;
       reduce_gstats(s2, red);
