@@ -509,6 +509,63 @@ def run_sod2d(args, L, torch, stream, world, rank, secondary=False):
     return out
 
 
+PATCH_N = 4096
+
+
+def run_patch2d(args):
+    """--workload patch2d: a 4096 x 4096 periodic patchwork state (squares
+    of 7 nodes, each with its own velocity, |V| < 1.3, and p/rho in
+    0.3 .. 3.5; inputs.patch_prims): every window holds several level
+    speeds and lattice shifts of both signs, so every tile after the first
+    step takes the mixed-window kernel.  FP32, K steps after W warm-up
+    steps, timed as one block with CUDA events (state 268 MB per set,
+    larger than L2)."""
+    import torch
+    from paper_1602_02675_gb300 import inputs as I
+    from paper_1602_02675_gb300 import lbm as L
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.Stream()
+    n = PATCH_N
+    K = args.steps if args.steps > 0 else 20
+    cfg = L.make_config(2, n, n, dt=1.0 / n, precision=L.F32,
+                        bc_x=L.PERIODIC, bc_y=L.PERIODIC, kahan=args.kahan,
+                        cons_every=1, stream=stream.cuda_stream)
+    prims = I.patch_prims(n, n, seed=7)
+    with L.Solver(cfg) as s, torch.cuda.stream(stream):
+        s.set_primitives(*prims)
+        s.step(args.warmup)
+        stream.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+        a.record(stream)
+        s.step(K)
+        b.record(stream)
+        stream.synchronize()
+        clk = clocks.stop()
+        ms = a.elapsed_time(b)
+        s.synchronize()
+        diag, reach = s.diagnostics(), s.reach()
+    mean_ms = ms / K
+    peak, peak_kind = load_peaks()
+    achieved = 32 * n * n / (mean_ms / 1e3) / 1e9
+    return {"metric": METRIC, "value": n * n * K / (ms / 1e3),
+            "unit": "node-updates/s", "n_gpus": 1, "steps": K,
+            "warmup": args.warmup, "ms_per_step": round(mean_ms, 5),
+            "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic (patchwork of uniform squares)",
+            "config": {"workload": "patchwork_2d_4096x4096_periodic",
+                       "nx": n, "ny": n, "timed": f"steps {args.warmup + 1}-"
+                       f"{args.warmup + K}", "l2": "state larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1),
+                         "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4),
+                         "peak_kind": peak_kind},
+            "gpu_launches": DS_LAUNCHES_PER_STEP * K,
+            "end_state": {"reach": reach, "diagnostics": diag},
+            "clocks": clk}
+
+
 # --------------------------------------------------------------------------
 # the oracle on the host: CPU baseline and reference arm
 # --------------------------------------------------------------------------
@@ -836,7 +893,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--precision-steps", type=int, default=100)
     ap.add_argument("--workload", default="cylinder2d",
-                    choices=sorted(WORKLOADS) + ["tubes", "serve", "sod1d"])
+                    choices=sorted(WORKLOADS) + ["tubes", "serve", "sod1d",
+                                                 "patch2d"])
     ap.add_argument("--repeats", type=int, default=100,
                     help="sod1d: solves timed")
     ap.add_argument("--requests", type=int, default=2000)
@@ -871,6 +929,9 @@ def main():
         return
     if args.workload == "sod1d":
         print(json.dumps(run_sod1d(args)))
+        return
+    if args.workload == "patch2d":
+        print(json.dumps(run_patch2d(args)))
         return
     if args.impl == "reference":
         line = run_reference(args, rank, world)

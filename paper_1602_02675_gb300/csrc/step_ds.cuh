@@ -251,19 +251,18 @@ __device__ __forceinline__ float type_id(const SrcEq& q) {
   return q.emits ? type_of(q.c1, q.nxf, q.nyf) : kNoType;
 }
 
-// Statistics of a window walk, per thread until
-// reduce_gstats combines them over the block: smallest and largest c1 and
-// shift over the emitting sources, the next group above the walk's, whether
-// a source of the walk's group was deposited, whether an emitting source
-// lies below the assumed minima, and the clamped energies of owned nodes.
+// Statistics of a window walk, per thread until reduce_gstats combines them
+// over the block: smallest and largest c1 and shift over the emitting
+// sources, the next group above the walk's, whether a source of the walk's
+// group was deposited, and the clamped energies of owned nodes.
 struct GStats {
   float c1min, nxmin, nymin, tnext, c1max, nxmax, nymax;
   unsigned clamps;
-  bool any, under;
+  bool any;
 };
 __device__ __forceinline__ GStats gstats_init() {
   return GStats{kNoType, kNoType, kNoType, kNoType, -kNoType, -kNoType,
-                -kNoType, 0u, false, false};
+                -kNoType, 0u, false};
 }
 __device__ __forceinline__ void gstats_add(GStats& st, bool emits, float c1,
                                            float nxf, float nyf) {
@@ -280,7 +279,7 @@ __device__ __forceinline__ void gstats_add(GStats& st, bool emits, float c1,
 // Block reduction of GStats (all threads call it and get the result; it
 // holds the barrier that makes a walk's deposits visible).  The values are
 // small integers, reduced as ints.
-constexpr int NGSTAT = 9;
+constexpr int NGSTAT = 8;
 __device__ __forceinline__ void reduce_gstats(GStats& st, int* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr unsigned F = 0xffffffffu;
@@ -293,7 +292,6 @@ __device__ __forceinline__ void reduce_gstats(GStats& st, int* red) {
   v[5] = __reduce_max_sync(F, (int)st.nxmax);
   v[6] = __reduce_max_sync(F, (int)st.nymax);
   v[7] = __any_sync(F, st.any) ? 1 : 0;
-  v[8] = __any_sync(F, st.under) ? 1 : 0;
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < NGSTAT; ++k) red[k * NWARP + warp] = v[k];
@@ -316,7 +314,6 @@ __device__ __forceinline__ void reduce_gstats(GStats& st, int* red) {
   st.nxmax = (float)v[5];
   st.nymax = (float)v[6];
   st.any = v[7] != 0;
-  st.under = v[8] != 0;
 }
 
 // Where a thread's column sits and how it reads its sources.
@@ -647,7 +644,6 @@ __device__ __forceinline__ void walk_group(
     const bool mine = gid == G;
     st.any |= mine;
     st.tnext = fminf(st.tnext, gid > G ? gid : kNoType);
-    st.under |= q.emits && fminf(dc, fminf(dx, dy)) < 0.0f;
     gstats_add(st, q.emits, q.c1, q.nxf, q.nyf);
     if (q.clamp && r >= own_lo && r <= own_hi) st.clamps += 1;
     GSrc<S> cur;
@@ -1184,11 +1180,27 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds_mixed(const StepArgs a) {
       counted = true;
       reduce_gstats(s2, red);
       if (!checked) {
-        // the groups follow from this step's state alone: minima and block
-        // taken from an earlier step are redone when they differ
+        // the result must follow from this step's state alone.  A window
+        // whose shifts span at most SPMAX per axis takes one group per c1,
+        // in ascending c1 order, and any block that holds all its shifts
+        // deposits the same values (offsets outside the sources' range add
+        // exact zeros in the same order), so minima and block taken from an
+        // earlier step stand when the c1 minimum is not above the state's
+        // and the block holds the window's shifts.  Wider windows take the
+        // blocks from the state's minima.
         checked = true;
-        if (s2.under || c1m != s2.c1min || nxm != s2.nxmin ||
-            nym != s2.nymin || S != block_of(s2)) {
+        const bool wide_n = fmaxf(s2.nxmax - s2.nxmin, s2.nymax - s2.nymin) >=
+                            (float)SPMAX;
+        // (and its packets of the largest level speed stay within the
+        // deposits, which a block based below the state's minima can miss)
+        const bool holds =
+            c1m <= s2.c1min && nxm <= s2.nxmin &&
+            s2.nxmax <= nxm + (float)(S - 1) && nym <= s2.nymin &&
+            s2.nymax <= nym + (float)(S - 1) &&
+            type_fits(Type{(int)nxm, (int)nym, (int)s2.c1max}, R, 1);
+        const bool same = c1m == s2.c1min && nxm == s2.nxmin &&
+                          nym == s2.nymin && S == SPMAX;
+        if (s2.c1max >= 0.0f && !(wide_n ? same : holds)) {
           c1m = s2.c1min;
           nxm = s2.nxmin;
           nym = s2.nymin;
