@@ -187,6 +187,11 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
   h->nblocks = (int)step_blocks(c.dim, h->nx, h->ny);  // nx ny <= INT32_MAX
   h->part_cap = h->nblocks > totals_blocks(h->n) ? h->nblocks
                                                  : totals_blocks(h->n);
+  if (c.dim == 2 && !h->f64) {
+    // the deposit kernel's tiles and its finalize blocks' partials
+    const int dt = ds_tiles(h->nx, h->ny, h->r_cap) + ds_finalize_blocks();
+    if (dt > h->part_cap) h->part_cap = dt;
+  }
   const size_t fb = esize(h) * (size_t)h->n;
   bool ok = true;
   for (int b = 0; b < 2 && ok; ++b)

@@ -83,6 +83,9 @@ int device_sm_count();
 // r_cap (0 if r_cap is beyond its layout): the size of the per-tile hint
 // and queue arrays a handle holds for it.
 int ds_tiles(int nx, int ny, int r_cap);
+// Blocks of the deposit kernel's finalize launch (each leaves one set of
+// partial totals after the tiles' partials).
+int ds_finalize_blocks();
 
 // Launch helpers (step kernels).
 size_t step_smem_bytes(int dim, bool f64, int r_cap);

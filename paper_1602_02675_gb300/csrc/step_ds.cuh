@@ -194,11 +194,45 @@ __device__ __forceinline__ Type decode_type(float t) {
   return Type{(int)hx - 128, (int)hy - 128, (int)c1};
 }
 
+// Constants of one level pair (c1, c2 = c1 + 1) for the level densities
+// (eqs 24-25 with d0 = 0 and b1 = 4 on the square lattice): c1^2, c2^2, the
+// denominator 4 (c2^2 - c1^2) = 4 (2 c1 + 1) and its correctly rounded
+// reciprocal (from a table for c1 <= 3, no estimate on the dependency chain).
+struct LevelK {
+  float c1sq, c2sq, den, rden;
+};
+__device__ __forceinline__ LevelK level_k(float c1) {
+  LevelK k;
+  const float c2 = __fadd_rn(c1, 1.0f);
+  k.c1sq = __fmul_rn(c1, c1);
+  k.c2sq = __fmul_rn(c2, c2);
+  k.den = __fmul_rn(4.0f, __fmaf_rn(2.0f, c1, 1.0f));
+  k.rden = c1 < 1.0f ? 0.25f
+                     : (c1 < 2.0f ? 1.0f / 12.0f
+                                  : (c1 < 3.0f ? 1.0f / 20.0f
+                                               : (c1 < 4.0f ? 1.0f / 28.0f
+                                                            : rcp_nr(k.den))));
+  return k;
+}
+// d1 = (c2^2 rho - X rho) / (4 (c2^2 - c1^2)), d2 = rho / 4 - d1 of a source
+// whose c1 is k's; the quotient rounded as one division would round it
+// (Markstein's correction): a shared rounding of 1 / den would bias the
+// packets' energy of every node alike.  Zero for a source that emits
+// nothing.
+__device__ __forceinline__ void level_dens(float rho, float X, bool emits,
+                                           const LevelK& k, float& d1,
+                                           float& d2) {
+  const float num = __fmaf_rn(k.c2sq, rho, -__fmul_rn(X, rho));
+  const float q = div_markstein(num, k.den, k.rden);
+  d1 = emits ? q : 0.0f;
+  d2 = emits ? __fmaf_rn(0.25f, rho, -q) : 0.0f;
+}
+
 // Equilibrium of one window source (Section III.B with d0 = 0 and b1 = 4
-// on the square lattice): c1 (eq 26), level densities (eqs 24-25), the
-// level records' shared part (1, V_x, V_y, E_b) with E_b = |V|^2/2 + phi
-// (eqs 13-15), and the split of V (eq 23).  A source that emits nothing
-// (rho <= 0) has zero densities, V and E_b.
+// on the square lattice): c1 (eq 26), the level records' shared part
+// (1, V_x, V_y, E_b) with E_b = |V|^2/2 + phi (eqs 13-15), the split of V
+// (eq 23), and the level densities (eqs 24-25).  A source that emits
+// nothing (rho <= 0) has zero densities, V and E_b.
 struct SrcEq {
   bool emits, clamp;
   float c1, nxf, nyf, fx, fy, d1, d2, Vx, Vy, Eb;
@@ -209,29 +243,13 @@ __device__ __forceinline__ SrcEq source_eq(float4 m, float kq) {
   const EqCore c = eq_core(rho, m.y, m.z, m.w, kq);
   q.emits = rho > 0.0f;
   q.clamp = q.emits && c.eraw < 0.0f;
-  // c1 below 4 for the whole warp (X < 16): counted squares and the
-  // correctly rounded 1 / (4 (2 c1 + 1)) from a table, no estimate on the
-  // dependency chain; otherwise c1_of and the refined reciprocal
+  // c1 below 4 for the whole warp (X < 16): counted squares; otherwise
+  // c1_of
   const bool wide = __any_sync(0xffffffffu, !(c.X < 16.0f));
   q.c1 = (c.X >= 1.0f ? 1.0f : 0.0f) + (c.X >= 4.0f ? 1.0f : 0.0f) +
          (c.X >= 9.0f ? 1.0f : 0.0f);
   if (wide) q.c1 = c.X < 16.0f ? q.c1 : c1_of(c.X);
-  const float c2 = __fadd_rn(q.c1, 1.0f);
-  const float c2sq = __fmul_rn(c2, c2);
-  // d1 = (c2^2 rho - X rho) / (4 (c2^2 - c1^2)), d2 = rho / 4 - d1; the
-  // quotient rounded as one division would round it (Markstein's
-  // correction): a shared rounding of 1 / den would bias the packets'
-  // energy of every node alike
-  const float den = __fmul_rn(4.0f, __fmaf_rn(2.0f, q.c1, 1.0f));
-  const float num = __fmaf_rn(c2sq, rho, -__fmul_rn(c.X, rho));
-  float rden = q.c1 < 1.0f ? 0.25f
-                           : (q.c1 < 2.0f ? 1.0f / 12.0f
-                                          : (q.c1 < 3.0f ? 1.0f / 20.0f
-                                                         : 1.0f / 28.0f));
-  if (wide) rden = q.c1 <= 3.0f ? rden : rcp_nr(den);
-  const float d1 = div_markstein(num, den, rden);
-  q.d1 = q.emits ? d1 : 0.0f;
-  q.d2 = q.emits ? __fmaf_rn(0.25f, rho, -d1) : 0.0f;
+  level_dens(rho, c.X, q.emits, level_k(q.c1), q.d1, q.d2);
   // phi = e - X / 2 (eq 15 with D/2 (gamma - 1) e = X / 2)
   const float phi = __fmaf_rn(-0.5f, c.X, fmaxf(c.eraw, 0.0f));
   q.Eb = q.emits ? __fmaf_rn(0.5f, c.kin2, phi) : 0.0f;
@@ -239,6 +257,32 @@ __device__ __forceinline__ SrcEq source_eq(float4 m, float kq) {
   q.Vy = q.emits ? c.Vy : 0.0f;
   split_f(q.Vx, q.nxf, q.fx);
   split_f(q.Vy, q.nyf, q.fy);
+  return q;
+}
+// The same for a source of the tile's guessed type: whether it has that
+// type (c1^2 <= X < c2^2 with k's c1, the same shift n) replaces c1.
+struct SrcEqT {
+  bool emits, clamp, mine;
+  float fx, fy, d1, d2, Vx, Vy, Eb;
+};
+__device__ __forceinline__ SrcEqT source_eq_typed(float4 m, float kq,
+                                                  const LevelK& k, float nxT,
+                                                  float nyT) {
+  SrcEqT q;
+  const float rho = m.x;
+  const EqCore c = eq_core(rho, m.y, m.z, m.w, kq);
+  q.emits = rho > 0.0f;
+  q.clamp = q.emits && c.eraw < 0.0f;
+  level_dens(rho, c.X, q.emits, k, q.d1, q.d2);
+  const float phi = __fmaf_rn(-0.5f, c.X, fmaxf(c.eraw, 0.0f));
+  q.Eb = q.emits ? __fmaf_rn(0.5f, c.kin2, phi) : 0.0f;
+  q.Vx = q.emits ? c.Vx : 0.0f;
+  q.Vy = q.emits ? c.Vy : 0.0f;
+  float nxf, nyf;
+  split_f(q.Vx, nxf, q.fx);
+  split_f(q.Vy, nyf, q.fy);
+  q.mine = q.emits && c.X >= k.c1sq && c.X < k.c2sq && nxf == nxT &&
+           nyf == nyT;
   return q;
 }
 
@@ -406,22 +450,49 @@ __device__ __forceinline__ SrcRing ring_of(const StepArgs& a, float* base) {
   return r;
 }
 
-// One-type walk: deposits the sources whose type is T (the corner weights
-// of eq 29 on offsets {0, 1}^2) and gathers the statistics of every source
-// (pass 0: types, minima, clamped energies of owned nodes).
+// Type of one window source without its level densities: emits, c1, the
+// shift n = floor(V) (eq 23) and whether its energy was clamped.
+__device__ __forceinline__ void source_type(float4 m, float kq, bool& emits,
+                                            bool& clamp, float& id,
+                                            float& c1, float& nxf,
+                                            float& nyf) {
+  const EqCore c = eq_core(m.x, m.y, m.z, m.w, kq);
+  emits = m.x > 0.0f;
+  clamp = emits && c.eraw < 0.0f;
+  c1 = c1_exact(c.X);
+  float f;
+  split_f(emits ? c.Vx : 0.0f, nxf, f);
+  split_f(emits ? c.Vy : 0.0f, nyf, f);
+  id = emits ? __fmaf_rn(65536.0f, c1,
+                         __fmaf_rn(256.0f, __fadd_rn(nxf, 128.0f),
+                                   __fadd_rn(nyf, 128.0f)))
+             : kNoType;
+}
+
+// Result of a one-type walk, per thread: whether a source emits, whether an
+// emitting source has another type than the walk's, and the clamped
+// energies of owned nodes.
+struct OneTypeFlags {
+  unsigned clamps;
+  bool emit, other;
+};
+
+// One-type walk for the tile's guessed type T, the type of its central node
+// m (every thread forms it): deposits the sources of type T (the corner
+// weights of eq 29 on offsets {0, 1}^2) and notes whether any emitting
+// source has another type.
 template <bool INT>
 __device__ __forceinline__ void walk_one_type(
     const StepArgs& a, float4* __restrict__ D1, float4* __restrict__ D2,
-    float* rbase, int x0, int y0, int R, int TX, int TY,
-    float Tin, const float4* cm, float* T0p, bool count_clamps,
-    GStats& st) {
+    float* rbase, int x0, int y0, int R, int TX, int TY, float4 m,
+    float& T, OneTypeFlags& fl) {
   const Column col = column_of(a, x0, R, TX, INT);
   const int ly0 = SH * col.g;
   const float kq = a.k.kq_f;
   // rows r of this walk whose node the tile owns (its energy clamps are
   // counted here); none if the column is not owned
   const int own_lo = max(1, R - ly0);
-  const int own_hi = col.col_own && count_clamps
+  const int own_hi = col.col_own
                          ? min(min(SH, R + TY - 1 - ly0), a.ny - 1 - (y0 - R) - ly0)
                          : -1;
   float4 pw01a1 = f4(0.f, 0.f, 0.f, 0.f), pw01a2 = pw01a1;
@@ -432,11 +503,13 @@ __device__ __forceinline__ void walk_one_type(
   SrcRing ring = ring_of(a, rbase);
 #pragma unroll
   for (int k = 0; k < PF; ++k) ring.template issue<INT>(a, col, y0, R, ly0 + k, k);
-  if (T0p) {
-    // the tile's guess type, from the central node loaded by the caller
-    *T0p = type_id(source_eq(*cm, kq));
+  float c1T, nxT, nyT;
+  {
+    bool emits, clamp;
+    source_type(m, kq, emits, clamp, T, c1T, nxT, nyT);
+    if (!emits) c1T = 1.0e6f;   // no source has this type
   }
-  const float T = T0p ? *T0p : Tin;
+  const LevelK lk = level_k(c1T);
   // Software pipeline: the equilibrium of row r + 1 is formed while row r
   // is deposited (two independent dependency chains per thread).
   // (a rolled loop: the walk's code stays small in the instruction cache)
@@ -445,28 +518,27 @@ __device__ __forceinline__ void walk_one_type(
       cp_async_wait<PF - 1>();
     else
       cp_async_wait<0>();
-    const float4 m = ring.template take<INT>(a, col, y0, R, ly0 + r, slot);
+    const float4 mm = ring.template take<INT>(a, col, y0, R, ly0 + r, slot);
     if (r + PF <= SH) ring.template issue<INT>(a, col, y0, R, ly0 + r + PF, slot);
-    return source_eq(m, kq);
+    return source_eq_typed(mm, kq, lk, nxT, nyT);
   };
-  SrcEq qn = row_eq(0, 0);
+  SrcEqT qn = row_eq(0, 0);
   int slot = 1;
 #pragma unroll 1
   for (int r = 0; r <= SH; ++r) {
     const int ly = ly0 + r;
-    const SrcEq q = qn;
+    const SrcEqT q = qn;
     if (r < SH) {
       qn = row_eq(r + 1, slot);
       slot = slot + 1 == PF ? 0 : slot + 1;
     }
-    const bool mine = type_id(q) == T;
-    st.any |= mine;
-    gstats_add(st, q.emits, q.c1, q.nxf, q.nyf);
-    if (q.clamp && r >= own_lo && r <= own_hi) st.clamps += 1;
+    fl.emit |= q.emits;
+    fl.other |= q.emits && !q.mine;
+    if (q.clamp && r >= own_lo && r <= own_hi) fl.clamps += 1;
     // level records L_v = d_v (1, V_x, V_y, E_b) of the sources of type T
     const float4 v4 = f4(1.0f, q.Vx, q.Vy, q.Eb);
-    const float4 a1 = mul4(mine ? q.d1 : 0.0f, v4);
-    const float4 a2 = mul4(mine ? q.d2 : 0.0f, v4);
+    const float4 a1 = mul4(q.mine ? q.d1 : 0.0f, v4);
+    const float4 a2 = mul4(q.mine ? q.d2 : 0.0f, v4);
     // corner weights (eq 29)
     const float gx1 = __fsub_rn(1.0f, q.fx), gy1 = __fsub_rn(1.0f, q.fy);
     const float w00 = __fmul_rn(gx1, gy1), w10 = __fmul_rn(q.fx, gy1);
@@ -487,24 +559,6 @@ __device__ __forceinline__ void walk_one_type(
   }
 }
 
-// Type of one window source without its level densities: emits, c1, the
-// shift n = floor(V) (eq 23) and whether its energy was clamped.
-__device__ __forceinline__ void source_type(float4 m, float kq, bool& emits,
-                                            bool& clamp, float& id,
-                                            float& c1, float& nxf,
-                                            float& nyf) {
-  const EqCore c = eq_core(m.x, m.y, m.z, m.w, kq);
-  emits = m.x > 0.0f;
-  clamp = emits && c.eraw < 0.0f;
-  c1 = c1_exact(c.X);
-  float f;
-  split_f(emits ? c.Vx : 0.0f, nxf, f);
-  split_f(emits ? c.Vy : 0.0f, nyf, f);
-  id = emits ? __fmaf_rn(65536.0f, c1,
-                         __fmaf_rn(256.0f, __fadd_rn(nxf, 128.0f),
-                                   __fadd_rn(nyf, 128.0f)))
-             : kNoType;
-}
 
 // Shift block of a window's groups: the larger spread of n over the
 // window's emitting sources, at most SPMAX.
@@ -516,11 +570,12 @@ __device__ __forceinline__ int block_of(const GStats& st) {
 // Per-tile record a step leaves for the next: 0 when the window held one
 // type (or nothing), else bit 31 with the window's smallest c1 and shift and
 // its block size, or bit 31 and bit 30 when those do not fit the record.
+constexpr unsigned kRecUnknown = 0xc0000000u;
 __device__ __forceinline__ unsigned rec_encode(float c1min, float nxmin,
                                                float nymin, int S) {
   if (!(c1min <= 63.0f && nxmin >= -128.0f && nxmin <= 127.0f &&
         nymin >= -128.0f && nymin <= 127.0f))
-    return 0xc0000000u;
+    return kRecUnknown;
   return 0x80000000u | ((unsigned)(S - 1) << 24) | ((unsigned)c1min << 16) |
          ((unsigned)((int)nxmin + 128) << 8) | (unsigned)((int)nymin + 128);
 }
@@ -1045,7 +1100,7 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
   // guess: the type of the tile's central node (every thread forms it; its
   // load overlaps the walk's first loads)
   float T0;
-  GStats st = gstats_init();
+  OneTypeFlags fl{0u, false, false};
   {
     const int cx = min(x0 + TX / 2, a.nx - 1), cy = min(y0 + TY / 2, a.ny - 1);
     const long long i = (long long)cy * a.nx + cx;
@@ -1055,25 +1110,21 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
                         __ldg(static_cast<const float*>(a.in[3]) + i));
     // interior windows need no boundary handling: their own, smaller walk
     if (interior)
-      walk_one_type<true>(a, D1, D2, rbase, x0, y0, R, TX, TY, 0.0f, &m, &T0,
-                          true, st);
+      walk_one_type<true>(a, D1, D2, rbase, x0, y0, R, TX, TY, m, T0, fl);
     else
-      walk_one_type<false>(a, D1, D2, rbase, x0, y0, R, TX, TY, 0.0f, &m,
-                           &T0, true, st);
+      walk_one_type<false>(a, D1, D2, rbase, x0, y0, R, TX, TY, m, T0, fl);
   }
-  const unsigned my_clamps = st.clamps;
-  reduce_gstats(st, red);  // includes the barrier after the deposits
-  const bool none = st.c1max < 0.0f;
-  const bool one = st.c1min == st.c1max && st.nxmin == st.nxmax &&
-                   st.nymin == st.nymax;
-  if (!none && !(one && T0 == type_of(st.c1min, st.nxmin, st.nymin))) {
-    // the window's smallest c1 and shift and its block (exact for this
-    // step): the mixed-window kernel starts from them
-    if (tid == 0) a.hint[b] = rec_of(st);
-    enqueue();            // the mixed-window kernel counts its clamps
+  // the barriers after the deposits, with the block's flags
+  const bool other = __syncthreads_or(fl.other) != 0;
+  const bool none = __syncthreads_or(fl.emit) == 0;
+  if (other) {
+    // the mixed-window kernel finds the window's minima and counts its
+    // clamps
+    if (tid == 0) a.hint[b] = kRecUnknown;
+    enqueue();
     return;
   }
-  commit_clamps(a, my_clamps);
+  commit_clamps(a, fl.clamps);
   TileOut to = tile_out_init();
   if (none) {
     finish_tile(a, x0, y0, TX, TY, true, to);  // nothing lands
@@ -1234,17 +1285,25 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds_mixed(const StepArgs a) {
   }
 }
 
-// After each launch of step2d_ds (one block): the tiles' compensated
-// (hi, lo) partial totals summed in compensated FP32 in a fixed order and
-// converted to FP64 once per field, and the reach hand-off to the next step.
-// A launch that met a reach beyond its layout leaves the reach as it was,
-// so later steps report the same error.
+// After each step (FIN_BLOCKS blocks): the tiles' compensated (hi, lo)
+// partial totals summed in compensated FP32 in a fixed order -- block j
+// takes the j-th of FIN_BLOCKS equal runs of tiles, the last block to finish
+// sums the blocks' results in block order and converts them to FP64 once per
+// field -- and the reach hand-off to the next step.  A step that met a reach
+// beyond its layout leaves the reach as it was, so later steps report the
+// same error.  The blocks' results follow the tiles' partials in part.
+constexpr int FIN_BLOCKS = 32;
 __global__ void __launch_bounds__(NTHR)
-    finalize2d(Scratch* scr, const double* __restrict__ part, int nblk,
+    finalize2d(Scratch* scr, double* __restrict__ part, int nblk,
                int do_cons) {
   __shared__ float2 red[4][NWARP];
+  __shared__ bool last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float2* fin = reinterpret_cast<float2*>(part) + (long long)nblk * 4;
   if (do_cons) {
+    const int chunk = (nblk + FIN_BLOCKS - 1) / FIN_BLOCKS;
+    const int lo = blockIdx.x * chunk;
+    const int hi = min(nblk, lo + chunk);
     // each thread a fixed strided set of tiles, four at a time (their loads
     // in flight together), then a fixed combine
     const float4* p4 = reinterpret_cast<const float4*>(part);
@@ -1254,12 +1313,12 @@ __global__ void __launch_bounds__(NTHR)
     for (int u = 0; u < U; ++u)
 #pragma unroll
       for (int f = 0; f < 4; ++f) s4[u][f] = Sum2{0.f, 0.f};
-    for (int b0 = tid; b0 < nblk; b0 += U * NTHR) {
+    for (int b0 = lo + tid; b0 < hi; b0 += U * NTHR) {
       float4 v[U][2];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int b = b0 + u * NTHR;
-        const bool ok = b < nblk;
+        const bool ok = b < hi;
         v[u][0] = ok ? p4[(long long)b * 2] : f4(0.f, 0.f, 0.f, 0.f);
         v[u][1] = ok ? p4[(long long)b * 2 + 1] : f4(0.f, 0.f, 0.f, 0.f);
       }
@@ -1280,8 +1339,26 @@ __global__ void __launch_bounds__(NTHR)
     __syncthreads();
     if (warp == 0) {
       const Sum2 t = combine_warps_f2<NWARP>(red, lane);
-      if ((lane & 7) == 0) scr->cons[lane >> 3] = (double)t.hi + (double)t.lo;
+      if ((lane & 7) == 0)
+        fin[(long long)blockIdx.x * 4 + (lane >> 3)] = make_float2(t.hi, t.lo);
+      __threadfence();
     }
+  }
+  __syncthreads();
+  if (tid == 0) last = atomicAdd(&scr->ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (do_cons && warp == 0) {
+    static_assert(FIN_BLOCKS == 32, "one lane per block result");
+    Sum2 ps[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const float2 v = __ldcg(&fin[(long long)lane * 4 + f]);
+      ps[f] = Sum2{v.x, v.y};
+    }
+    const Sum2 t = warp_sum2_fields(ps, lane);
+    if ((lane & 7) == 0) scr->cons[lane >> 3] = (double)t.hi + (double)t.lo;
   }
   if (tid == 0) {
     if (!(scr->flags & kFlagReach)) scr->reach = scr->reach_next;

@@ -50,10 +50,13 @@ cudaError_t launch_step_f32(int dim, const StepArgs& a, size_t smem,
       ds::step2d_ds<false><<<(unsigned)b.nblocks, ds::NTHR, ds::smem_bytes(), s>>>(b);
       ds::step2d_ds_mixed<false><<<(unsigned)nb2, ds::NTHR, ds::smem_bytes(), s>>>(b);
     }
-    ds::finalize2d<<<1, ds::NTHR, 0, s>>>(b.scr, b.part, b.nblocks, b.do_cons);
+    ds::finalize2d<<<ds::FIN_BLOCKS, ds::NTHR, 0, s>>>(b.scr, b.part, b.nblocks,
+                                                       b.do_cons);
   }
   return cudaGetLastError();
 }
+
+int ds_finalize_blocks() { return ds::FIN_BLOCKS; }
 
 int ds_tiles(int nx, int ny, int r_cap) {
   return r_cap > ds::RMAX ? 0 : ds::tiles_for(nx, ny, r_cap);
