@@ -509,6 +509,70 @@ def run_sod2d(args, L, torch, stream, world, rank, secondary=False):
     return out
 
 
+def run_batch2d(args):
+    """--workload batch2d: many small 2-D grids (sides log-uniform 64..512,
+    planar Riemann jumps with the served requests' states: left (1, 0, 1),
+    pressure ratio log-uniform 2..100, density ratio 1..10, end time
+    0.05..0.25; transmissive x, reflecting y; FP32) solved to their end
+    times, once as one lbm_batch2d (three launches per lattice step for the
+    whole batch) and once grid by grid through lbm_step on one stream (the
+    one-solve-at-a-time path).  Both timed with CUDA events, creation and
+    initial states excluded."""
+    import torch
+    from paper_1602_02675_gb300 import lbm as L
+    from paper_1602_02675_gb300 import serve as S
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.Stream()
+    count = args.grids
+    reqs = S.mixed_requests(count, seed=20271, n2=(64, 512),
+                            frac_1d=0.0)
+    specs = []
+    for r in reqs:
+        steps, lam = r.steps_and_lambda()
+        cfg = L.make_config(2, r.n, r.ny, dt=lam / r.n, precision=L.F32,
+                            bc_x=L.TRANSMISSIVE, bc_y=L.REFLECTING,
+                            kahan=args.kahan, stream=stream.cuda_stream)
+        specs.append((cfg, r, steps))
+    nu = sum(r.n * r.ny * k for _, r, k in specs)
+    grids = [L.make_grid2d(c, r.left, r.right, L.PLANAR_X, r.x_d, 0.5, 0.0, k)
+             for c, r, k in specs]
+
+    def timed(fn):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            stream.synchronize()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            stream.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    with L.Batch2D(grids, stream=stream.cuda_stream) as b:
+        t_batch = timed(b.run)
+        steps_batch = b.steps()
+    solvers = []
+    for c, r, k in specs:
+        s = L.Solver(c)
+        s.init_riemann(r.left, r.right, L.PLANAR_X, r.x_d)
+        solvers.append((s, k))
+    t_alone = timed(lambda: [s.step(k) for s, k in solvers])
+    for s, _ in solvers:
+        s.close()
+    return {"metric": METRIC, "value": nu / t_batch, "unit": "node-updates/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic (served 2-D requests' states, sides 64..512)",
+            "config": {"workload": f"batch2d_{count}_grids_64_512",
+                       "grids": count, "node_updates": nu,
+                       "batch_steps": steps_batch},
+            "solves_per_s": count / t_batch, "s_batch": round(t_batch, 4),
+            "one_at_a_time": {"value": nu / t_alone, "s": round(t_alone, 4),
+                              "solves_per_s": count / t_alone},
+            "speedup": round(t_alone / t_batch, 3),
+            "gpu_launches": 3 * steps_batch}
+
+
+PATCH_N = 4096
 PATCH_N = 4096
 
 
@@ -895,13 +959,15 @@ def main():
     ap.add_argument("--precision-steps", type=int, default=100)
     ap.add_argument("--workload", default="cylinder2d",
                     choices=sorted(WORKLOADS) + ["tubes", "serve", "sod1d",
-                                                 "patch2d"])
+                                                 "patch2d", "batch2d"])
     ap.add_argument("--repeats", type=int, default=100,
                     help="sod1d: solves timed")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--max-side", type=int, default=2048)
     ap.add_argument("--tubes", type=int, default=4096)
+    ap.add_argument("--grids", type=int, default=256,
+                    help="batch2d: grids in the batch")
     ap.add_argument("--batch-reps", type=int, default=2)
     ap.add_argument("--seq-tubes", type=int, default=48)
     ap.add_argument("--precision", default="both", choices=["both", "f32"])
@@ -933,6 +999,9 @@ def main():
         return
     if args.workload == "patch2d":
         print(json.dumps(run_patch2d(args)))
+        return
+    if args.workload == "batch2d":
+        print(json.dumps(run_batch2d(args)))
         return
     if args.impl == "reference":
         line = run_reference(args, rank, world)

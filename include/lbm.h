@@ -264,6 +264,57 @@ const char* lbm_batch_last_error(const lbm_batch* b);
 /* Free a batch; NULL-safe; waits for queued work. */
 void lbm_batch_destroy(lbm_batch* b);
 
+/* ---- batched small 2-D grids -------------------------------------------
+ *
+ * Many independent square-lattice grids (Section IV.B; each with its own
+ * size, boundaries, time step, initial state and step count) advanced
+ * together in FP32: a lattice step is three launches for the whole batch --
+ * the deposit kernel over the tiles of every grid that still has steps to
+ * take, the mixed-window kernel over one queue of the batch's mixed tiles,
+ * and the finalize kernel (each grid's totals and reach) -- instead of three
+ * per grid.  Each grid's step is the step lbm_step takes on a handle of the
+ * grid's configuration (same kernels and arithmetic), so every grid's
+ * result equals that handle's bit for bit.
+ */
+typedef struct lbm_batch2d lbm_batch2d;
+
+typedef struct {
+  lbm_config cfg;        /* dim 2, precision LBM_F32, max_reach 0 (6) or
+                            at most 6; cfg.stream is ignored */
+  lbm_prim inner, outer; /* initial state, as lbm_init_riemann */
+  int32_t geom;          /* lbm_geom */
+  int32_t pad_;
+  double a0, a1, radius; /* as lbm_init_riemann */
+  int64_t nsteps;        /* steps this grid takes */
+} lbm_grid2d;
+
+/* Create a batch of count grids (device memory for each, initial states,
+   first reach), all on `stream`.  LBM_EINVAL for a grid the deposit kernel
+   does not take (1-D, FP64, a reach limit above 6) or a negative step
+   count.  Grids keep the caller's indices.  Synchronous. */
+lbm_status lbm_batch2d_create(const lbm_grid2d* grids, int32_t count,
+                              void* stream, lbm_batch2d** out);
+
+/* Queue up to max_steps lattice steps (negative: until every grid has
+   taken its steps); grids past their step count are left as they are.
+   Stream-ordered, does not wait. */
+lbm_status lbm_batch2d_run(lbm_batch2d* b, int64_t max_steps);
+
+/* Lattice steps queued so far (the batch's step counter). */
+lbm_status lbm_batch2d_steps(const lbm_batch2d* b, int64_t* steps);
+
+/* Physical moments of one grid after its last step (or its latest, if the
+   batch has not reached it), as lbm_moments; errors the grid's steps met
+   (LBM_ESTATE, LBM_EREACH) are reported here.  Waits. */
+lbm_status lbm_batch2d_moments(lbm_batch2d* b, int32_t grid, double* rho,
+                               double* mx, double* my, double* rhoE,
+                               double* p, int64_t n);
+
+const char* lbm_batch2d_last_error(const lbm_batch2d* b);
+
+/* Free a batch; NULL-safe; waits for queued work. */
+void lbm_batch2d_destroy(lbm_batch2d* b);
+
 /* ---- tube pool for continuous batching ---------------------------------
  *
  * 1-D tubes (lbm_tube) join and leave between steps; each lbm_pool_step is

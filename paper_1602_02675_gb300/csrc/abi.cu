@@ -118,6 +118,45 @@ lbm_status seed_reach(lbm_handle* h) {
 
 }  // namespace
 
+namespace lbm {
+
+bool handle_ds_args(lbm_handle* h, int parity, StepArgs* a) {
+  if (!h || h->broken || h->dim != 2 || h->f64 || h->r_cap > ds_rmax() ||
+      !h->hint || !h->mixed_list)
+    return false;
+  a->nx = h->nx;
+  a->ny = h->ny;
+  a->bc_x = h->cfg.bc_x;
+  a->bc_y = h->cfg.bc_y;
+  a->r_cap = h->r_cap;
+  a->kahan = h->cfg.kahan ? 1 : 0;
+  a->exact_order = 0;
+  a->do_cons = 0;
+  a->nblocks = ds_tiles(h->nx, h->ny, h->r_cap);
+  a->k = h->k;
+  a->scr = h->scr;
+  a->part = h->part;
+  a->src = nullptr;
+  a->hint = h->hint;
+  a->mixed_list = h->mixed_list;
+  for (int f = 0; f < 4; ++f) {
+    a->in[f] = h->buf[parity][f];
+    a->out[f] = h->buf[parity ^ 1][f];
+  }
+  return true;
+}
+
+int handle_cons_every(const lbm_handle* h) { return h->cfg.cons_every; }
+
+int64_t handle_steps(const lbm_handle* h) { return h->steps; }
+
+void handle_took_steps(lbm_handle* h, int64_t n) {
+  h->cur ^= (int)(n & 1);
+  h->steps += n;
+}
+
+}  // namespace lbm
+
 extern "C" {
 
 int32_t lbm_abi_version(void) { return 1; }

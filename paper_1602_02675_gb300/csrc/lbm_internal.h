@@ -5,6 +5,8 @@
 
 #include <cuda_runtime.h>
 
+struct lbm_handle;
+
 namespace lbm {
 
 // Device error flags (Scratch::flags).
@@ -83,7 +85,20 @@ int device_sm_count();
 // r_cap (0 if r_cap is beyond its layout): the size of the per-tile hint
 // and queue arrays a handle holds for it.
 int ds_tiles(int nx, int ny, int r_cap);
-// Blocks of the deposit kernel's finalize launch (each leaves one set of
+// Largest reach limit the deposit kernel's window takes.
+int ds_rmax();
+
+// For the batched 2-D grids (batch2d.cu): the deposit kernel's arguments of
+// handle h's step from state parity `parity` (in = buffers parity, out = the
+// other set; do_cons 0), or false if h does not step with the deposit kernel
+// or is broken; the handle's cons_every and step count; and the bookkeeping
+// after the batch took n steps of h's grid.
+bool handle_ds_args(lbm_handle* h, int parity, StepArgs* a);
+int handle_cons_every(const lbm_handle* h);
+int64_t handle_steps(const lbm_handle* h);
+void handle_took_steps(lbm_handle* h, int64_t n);
+
+// Blocks of the deposit kernel's finalize launch// Blocks of the deposit kernel's finalize launch (each leaves one set of
 // partial totals after the tiles' partials).
 int ds_finalize_blocks();
 

@@ -1066,16 +1066,25 @@ __device__ __forceinline__ void commit_clamps(const StepArgs& a, unsigned c) {
 // holds one type is done here; a tile whose window held several types at
 // the last step, or turns out to hold several now, is queued for the
 // mixed-window kernel and left to it.
+// Shared memory of a deposit block: the two deposit planes and the source
+// ring (dynamic), the statistics and totals scratch (static).
+struct DsSmem {
+  float4* D1;
+  float4* D2;
+  float* rbase;
+  int* red;
+  TileRed* tred;
+};
+// Tile b of the grid a describes; `item` is what the mixed-window queue
+// (count qn, list ql) receives for it.
 template <bool KAHAN>
-__global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
-  extern __shared__ __align__(16) float4 dsm[];
-  __shared__ int red[NGSTAT * NWARP];
-  __shared__ TileRed tred;
-  float4* D1 = dsm;
-  float4* D2 = dsm + PLANE;
-  float* rbase = reinterpret_cast<float*>(dsm + 2 * PLANE);
+__device__ __forceinline__ void ds_first_tile(const StepArgs& a, int b,
+                                              int item, unsigned* qn,
+                                              int* ql, const DsSmem& sm) {
+  float4* D1 = sm.D1;
+  float4* D2 = sm.D2;
+  float* rbase = sm.rbase;
   const int tid = threadIdx.x;
-  const int b = blockIdx.x;
   const TileGeo g = geo_of(a);
   if (g.over || b >= g.ntiles) {
     if (g.over && tid == 0 && b == 0) atomicOr(&a.scr->flags, kFlagReach);
@@ -1085,7 +1094,7 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
     return;
   }
   auto enqueue = [&]() {
-    if (tid == 0) a.mixed_list[atomicAdd(&a.scr->mixed_n, 1u)] = b;
+    if (tid == 0) ql[atomicAdd(qn, 1u)] = item;
   };
   if (a.hint[b]) {
     enqueue();
@@ -1137,7 +1146,17 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
       finish_tile(a, x0, y0, TX, TY, true, to);
     }
   }
-  tile_publish(a, b, to, tred);
+  tile_publish(a, b, to, *sm.tred);
+}
+template <bool KAHAN>
+__global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
+  extern __shared__ __align__(16) float4 dsm[];
+  __shared__ int red[NGSTAT * NWARP];
+  __shared__ TileRed tred;
+  const DsSmem sm{dsm, dsm + PLANE, reinterpret_cast<float*>(dsm + 2 * PLANE),
+                  red, &tred};
+  ds_first_tile<KAHAN>(a, blockIdx.x, blockIdx.x, &a.scr->mixed_n,
+                       a.mixed_list, sm);
 }
 
 // The step, second kernel: persistent blocks take the tiles the first
@@ -1150,26 +1169,17 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
 // from the true minima.  What a tile computes depends only on the state and
 // on the minima and S it ends with, not on the queue order.
 template <bool KAHAN>
-__global__ void __launch_bounds__(NTHR, 2) step2d_ds_mixed(const StepArgs a) {
-  extern __shared__ __align__(16) float4 dsm[];
-  __shared__ int red[NGSTAT * NWARP];
-  __shared__ TileRed tred;
-  __shared__ int s_k;
-  float4* D1 = dsm;
-  float4* D2 = dsm + PLANE;
-  float* rbase = reinterpret_cast<float*>(dsm + 2 * PLANE);
+__device__ __forceinline__ void ds_mixed_tile(const StepArgs& a, int b,
+                                              const DsSmem& sm) {
+  float4* D1 = sm.D1;
+  float4* D2 = sm.D2;
+  float* rbase = sm.rbase;
+  int* red = sm.red;
   const int tid = threadIdx.x;
   const TileGeo g = geo_of(a);
-  const int nq = (int)a.scr->mixed_n;
   if (g.over) return;
   const int R = g.R, TX = g.TX, TY = g.TY;
-  while (true) {
-    if (tid == 0) s_k = (int)atomicAdd(&a.scr->mixed_ticket, 1u);
-    __syncthreads();
-    const int k = s_k;
-    __syncthreads();
-    if (k >= nq) break;
-    const int b = a.mixed_list[k];
+  {
     const int ty_i = b / g.tiles_x, tx_i = b - ty_i * g.tiles_x;
     const int x0 = tx_i * TX, y0 = ty_i * TY;
     const bool interior = x0 - R >= 0 && x0 - R + WCOLS <= a.nx &&
@@ -1280,7 +1290,25 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds_mixed(const StepArgs a) {
       G = s2.tnext;
     }
     if (tid == 0) a.hint[b] = rec_of(fin);
-    tile_publish(a, b, to, tred);
+    tile_publish(a, b, to, *sm.tred);
+  }
+}
+template <bool KAHAN>
+__global__ void __launch_bounds__(NTHR, 2) step2d_ds_mixed(const StepArgs a) {
+  extern __shared__ __align__(16) float4 dsm[];
+  __shared__ int red[NGSTAT * NWARP];
+  __shared__ TileRed tred;
+  __shared__ int s_k;
+  const DsSmem sm{dsm, dsm + PLANE, reinterpret_cast<float*>(dsm + 2 * PLANE),
+                  red, &tred};
+  const int nq = (int)a.scr->mixed_n;
+  while (true) {
+    if (threadIdx.x == 0) s_k = (int)atomicAdd(&a.scr->mixed_ticket, 1u);
+    __syncthreads();
+    const int k = s_k;
+    __syncthreads();
+    if (k >= nq) break;
+    ds_mixed_tile<KAHAN>(a, a.mixed_list[k], sm);
     __syncthreads();  // the next tile reuses the deposits and the ring
   }
 }
@@ -1293,16 +1321,18 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds_mixed(const StepArgs a) {
 // beyond its layout leaves the reach as it was, so later steps report the
 // same error.  The blocks' results follow the tiles' partials in part.
 constexpr int FIN_BLOCKS = 32;
-__global__ void __launch_bounds__(NTHR)
-    finalize2d(Scratch* scr, double* __restrict__ part, int nblk,
-               int do_cons) {
+// Block j of a grid's FIN_BLOCKS finalize blocks (all threads call it).
+__device__ __forceinline__ void ds_finalize_part(Scratch* scr,
+                                                 double* __restrict__ part,
+                                                 int nblk, int do_cons,
+                                                 int j) {
   __shared__ float2 red[4][NWARP];
   __shared__ bool last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float2* fin = reinterpret_cast<float2*>(part) + (long long)nblk * 4;
   if (do_cons) {
     const int chunk = (nblk + FIN_BLOCKS - 1) / FIN_BLOCKS;
-    const int lo = blockIdx.x * chunk;
+    const int lo = j * chunk;
     const int hi = min(nblk, lo + chunk);
     // each thread a fixed strided set of tiles, four at a time (their loads
     // in flight together), then a fixed combine
@@ -1340,12 +1370,12 @@ __global__ void __launch_bounds__(NTHR)
     if (warp == 0) {
       const Sum2 t = combine_warps_f2<NWARP>(red, lane);
       if ((lane & 7) == 0)
-        fin[(long long)blockIdx.x * 4 + (lane >> 3)] = make_float2(t.hi, t.lo);
+        fin[(long long)j * 4 + (lane >> 3)] = make_float2(t.hi, t.lo);
       __threadfence();
     }
   }
   __syncthreads();
-  if (tid == 0) last = atomicAdd(&scr->ticket, 1u) == gridDim.x - 1;
+  if (tid == 0) last = atomicAdd(&scr->ticket, 1u) == FIN_BLOCKS - 1;
   __syncthreads();
   if (!last) return;
   __threadfence();

@@ -3,6 +3,14 @@
 #include "step_kernel.cuh"
 
 namespace lbm {
+namespace ds {
+// One grid's finalize launch: FIN_BLOCKS blocks (ds_finalize_part).
+__global__ void __launch_bounds__(NTHR)
+    finalize2d(Scratch* scr, double* __restrict__ part, int nblk,
+               int do_cons) {
+  ds_finalize_part(scr, part, nblk, do_cons, blockIdx.x);
+}
+}  // namespace ds
 
 cudaError_t launch_step_f32(int dim, const StepArgs& a, size_t smem,
                             cudaStream_t s) {
@@ -57,6 +65,8 @@ cudaError_t launch_step_f32(int dim, const StepArgs& a, size_t smem,
 }
 
 int ds_finalize_blocks() { return ds::FIN_BLOCKS; }
+
+int ds_rmax() { return ds::RMAX; }
 
 int ds_tiles(int nx, int ny, int r_cap) {
   return r_cap > ds::RMAX ? 0 : ds::tiles_for(nx, ny, r_cap);

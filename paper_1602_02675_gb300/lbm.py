@@ -55,6 +55,13 @@ class lbm_tube(ctypes.Structure):
                 ("bc", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
+class lbm_grid2d(ctypes.Structure):
+    _fields_ = [("cfg", lbm_config), ("inner", lbm_prim), ("outer", lbm_prim),
+                ("geom", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("a0", ctypes.c_double), ("a1", ctypes.c_double),
+                ("radius", ctypes.c_double), ("nsteps", ctypes.c_int64)]
+
+
 class LbmError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -130,6 +137,16 @@ def load() -> ctypes.CDLL:
         "lbm_batch_tuning": ([_H, ctypes.POINTER(ctypes.c_int32), _DP],
                              ctypes.c_int),
         "lbm_batch_set_tile": ([_H, ctypes.c_int32], ctypes.c_int),
+        "lbm_batch2d_create": ([ctypes.POINTER(lbm_grid2d), ctypes.c_int32,
+                                ctypes.c_void_p, ctypes.POINTER(_H)],
+                               ctypes.c_int),
+        "lbm_batch2d_run": ([_H, ctypes.c_int64], ctypes.c_int),
+        "lbm_batch2d_steps": ([_H, ctypes.POINTER(ctypes.c_int64)],
+                              ctypes.c_int),
+        "lbm_batch2d_moments": ([_H, ctypes.c_int32, _DP, _DP, _DP, _DP, _DP,
+                                 ctypes.c_int64], ctypes.c_int),
+        "lbm_batch2d_last_error": ([_H], ctypes.c_char_p),
+        "lbm_batch2d_destroy": ([_H], None),
         "lbm_step_noalloc": ([ctypes.POINTER(lbm_noalloc_desc),
                               ctypes.c_void_p * 4, ctypes.c_void_p * 4,
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -374,6 +391,69 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             load().lbm_batch_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _prim4(s):
+    """(rho, u, p) or (rho, u, v, p) as four floats."""
+    s = tuple(float(v) for v in s)
+    return s if len(s) == 4 else (s[0], s[1], 0.0, s[2])
+
+
+def make_grid2d(cfg, inner, outer, geom=PLANAR_X, a0=0.5, a1=0.5,
+                radius=0.0, nsteps=0) -> lbm_grid2d:
+    """One grid of a Batch2D: its configuration (2-D, F32), its initial
+    state as Solver.init_riemann takes it, and its step count."""
+    return lbm_grid2d(cfg, lbm_prim(*_prim4(inner)), lbm_prim(*_prim4(outer)),
+                      geom, 0, a0, a1, radius, nsteps)
+
+
+class Batch2D:
+    """Many independent small 2-D grids advanced together (lbm_batch2d_*):
+    three launches per lattice step for the whole batch."""
+
+    def __init__(self, grids, stream=None):
+        lib = load()
+        arr = (lbm_grid2d * len(grids))(*grids)
+        self.n = [g.cfg.nx * g.cfg.ny for g in grids]
+        h = _H()
+        st = lib.lbm_batch2d_create(arr, len(grids), stream, ctypes.byref(h))
+        if st != OK:
+            raise LbmError(st, "lbm_batch2d_create")
+        self.h = h
+
+    def _check(self, st):
+        if st != OK:
+            msg = load().lbm_batch2d_last_error(self.h)
+            raise LbmError(st, msg.decode() if msg else "")
+
+    def run(self, max_steps=-1):
+        self._check(load().lbm_batch2d_run(self.h, int(max_steps)))
+
+    def steps(self) -> int:
+        s = ctypes.c_int64(0)
+        self._check(load().lbm_batch2d_steps(self.h, ctypes.byref(s)))
+        return s.value
+
+    def moments(self, j) -> dict:
+        n = self.n[j]
+        out = {k: np.empty(n) for k in ("rho", "mx", "my", "rhoE", "p")}
+        self._check(load().lbm_batch2d_moments(
+            self.h, j, _dp(out["rho"]), _dp(out["mx"]), _dp(out["my"]),
+            _dp(out["rhoE"]), _dp(out["p"]), n))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbm_batch2d_destroy(self.h)
             self.h = None
 
     __del__ = close

@@ -7,16 +7,18 @@ Section V.C) arrive over time.  Every tick the server
    has room for them (a request that does not fit waits; later, smaller
    ones may pass it);
 2. advances every admitted solve by up to ``steps_per_tick`` steps: all 1-D
-   tubes together with one ``lbm_pool_run`` call (a launch per step), each 2-D
-   grid with one ``lbm_step`` call on its own CUDA stream, so their kernels
-   overlap on the device;
+   tubes together with one ``lbm_pool_run`` call (a launch per step); the
+   FP32 2-D grids admitted in the same round together as one batch
+   (``lbm_batch2d_run``: three launches per lattice step for the whole
+   batch), each batch and each FP64 grid (``lbm_step``) on its own CUDA
+   stream, so their kernels overlap on the device;
 3. retires the solves that reached their step count, reading their moments
    back and freeing their memory.
 
 This module only schedules: every step of every solve runs in the CUDA
 library (``liblbm.so``).  A solve's result does not depend on what else is
-being served: the pool gives each tube its own step counter, and each grid
-has its own handle.
+being served: the pool gives each tube its own step counter, and a
+batched grid's steps are those of a handle of its own (bit for bit).
 """
 from __future__ import annotations
 
@@ -84,10 +86,24 @@ class Result:
 @dataclass
 class _Active2D:
     req: Request
-    solver: object
+    solver: object       # its handle (FP64), or None when batched
     stream: object
     steps: int
     taken: int = 0
+    group: object = None  # _Group2D of a batched grid
+    index: int = 0        # its grid index in the batch
+    done: bool = False
+
+
+@dataclass
+class _Group2D:
+    """FP32 2-D grids admitted in one round, stepped as one batch; its
+    memory is released when the last of its grids is retired."""
+    batch: object
+    stream: object
+    live: int
+    nbytes: int
+    steps_done: int = 0
 
 
 @dataclass
@@ -144,6 +160,7 @@ class Server:
 
     def _admit(self) -> None:
         waiting = []
+        new2d = []
         for req in self.pending:
             steps, lam = req.steps_and_lambda()
             never = (req.nodes() > self.pool_nodes if req.dim == 1 else
@@ -162,6 +179,16 @@ class Server:
                 if self._used + need > self.budget:
                     waiting.append(req)
                     continue
+                if self.precision == L.F32:
+                    # stepped with the others of this round as one batch
+                    cfg = L.make_config(2, req.n, req.ny, dt=lam / req.n,
+                                        precision=self.precision,
+                                        bc_x=L.TRANSMISSIVE,
+                                        bc_y=L.REFLECTING, kahan=0)
+                    new2d.append((req, cfg, steps, need))
+                    self._used += need
+                    self.peak_used = max(self.peak_used, self._used)
+                    continue
                 stream = (self._spare_streams.pop() if self._spare_streams
                           else self._torch.cuda.Stream())
                 cfg = L.make_config(2, req.n, req.ny, dt=lam / req.n,
@@ -179,6 +206,25 @@ class Server:
                 else:
                     self.errors[req.rid] = str(e)
         self.pending = waiting
+        if new2d:
+            stream = (self._spare_streams.pop() if self._spare_streams
+                      else self._torch.cuda.Stream())
+            grids = [L.make_grid2d(cfg, req.left, req.right, L.PLANAR_X,
+                                   req.x_d, 0.5, 0.0, steps)
+                     for req, cfg, steps, _ in new2d]
+            try:
+                batch = L.Batch2D(grids, stream=stream.cuda_stream)
+            except L.LbmError as e:
+                for req, _, _, need in new2d:
+                    self.errors[req.rid] = str(e)
+                    self._used -= need
+                self._spare_streams.append(stream)
+                return
+            group = _Group2D(batch, stream, len(new2d),
+                             sum(need for *_, need in new2d))
+            for j, (req, _, steps, _) in enumerate(new2d):
+                self._a2.append(_Active2D(req, None, stream, steps,
+                                          group=group, index=j))
 
     def _advance(self) -> None:
         k = max(1, int(self.steps_per_tick))
@@ -188,11 +234,21 @@ class Server:
             self._pool.run(kk)
             for a in self._a1:
                 a.taken = min(a.steps, a.taken + kk)
+        groups = {}
         for a in self._a2:
+            if a.group is not None:
+                groups[id(a.group)] = a.group
+                continue
             n = min(k, a.steps - a.taken)
             if n > 0:
                 a.solver.step(n)
                 a.taken += n
+        for g in groups.values():
+            g.batch.run(k)            # grids past their steps stay as they are
+            g.steps_done += k
+        for a in self._a2:
+            if a.group is not None:
+                a.taken = min(a.steps, a.group.steps_done)
 
     def _retire(self) -> None:
         keep1 = []
@@ -214,14 +270,22 @@ class Server:
                 keep2.append(a)
                 continue
             try:
-                f = a.solver.moments()
+                f = (a.solver.moments() if a.group is None
+                     else a.group.batch.moments(a.index))
                 self.results[a.req.rid] = Result(a.req.rid, f, a.req.arrival,
                                                  self.clock(), a.steps)
             except L.LbmError as e:
                 self.errors[a.req.rid] = str(e)
-            a.solver.close()
-            self._spare_streams.append(a.stream)
-            self._used -= bytes_needed(a.req, self.precision)
+            if a.group is None:
+                a.solver.close()
+                self._spare_streams.append(a.stream)
+                self._used -= bytes_needed(a.req, self.precision)
+                continue
+            a.group.live -= 1
+            if a.group.live == 0:
+                a.group.batch.close()
+                self._spare_streams.append(a.group.stream)
+                self._used -= a.group.nbytes
         self._a2 = keep2
 
     def drain(self) -> None:
@@ -230,7 +294,10 @@ class Server:
 
     def close(self) -> None:
         for a in self._a2:
-            a.solver.close()
+            if a.group is None:
+                a.solver.close()
+            else:
+                a.group.batch.close()
         self._a2 = []
         self._a1 = []
         if getattr(self, "_pool", None) is not None:
