@@ -206,11 +206,11 @@ def test_fp32_square_step_depends_on_state_only(seed, kahan):
         assert np.array_equal(m[f], ref[f]), f
 
 
-def test_fp32_reach_limit_beyond_register_window():
-    """max_reach 8 exceeds the register kernel's fixed window (reach 6), so
-    the FP32 handle without compensated sums steps with the exact-order
-    kernel instead; same results within the FP32 bar, and FP64 with the
-    same limit (records padded by 8) bit for bit."""
+def test_fp32_reach_limit_beyond_deposit_window():
+    """max_reach 8 exceeds the deposit kernel's window (reach 6), so the
+    FP32 handle steps with the exact-order kernel instead; same results
+    within the FP32 bar, and FP64 with the same limit (records padded by 8)
+    bit for bit."""
     nx, ny = 70, 40
     prims = I.random_smooth_prims(2, nx, ny, seed=3500)
     bcs = (L.PERIODIC, L.REFLECTING)
@@ -364,9 +364,9 @@ def test_sod_1d_fp32_l1(kahan):
 @pytest.mark.parametrize("kahan", [1, 0])
 @pytest.mark.parametrize("bcs", BC2)
 def test_random_2d_fp32_l1(bcs, kahan):
-    """kahan = 1: compensated exact-order kernel; kahan = 0: the register
-    kernel (uniform-type tiles on the fast path, mixed tiles on the general
-    path: this smooth field with a jump has both)."""
+    """The deposit kernel, compensated (kahan = 1) and plain (kahan = 0):
+    one-type tiles in the first kernel, mixed windows in the second (this
+    smooth field with a jump has both)."""
     nx, ny = 70, 45
     prims = I.random_smooth_prims(2, nx, ny, seed=3000 + bcs[0])
     g = _gpu(2, nx, ny, *bcs, prims=prims, steps=20, precision=L.F32,
@@ -460,8 +460,8 @@ def test_cylinder_full_size_sampled_outputs():
     """The 8192^2 periodic cylinder at full size, two steps: sampled nodes
     (the centre, the circle's edge, the periodic corners, seeded others)
     against the oracle run on a patch around each.  FP64 bit for bit; the
-    FP32 register kernel and the compensated FP32 kernel within 1e-5 of the
-    field's range."""
+    FP32 deposit kernel, plain and compensated, within 1e-5 of the field's
+    range."""
     N, steps, h = 8192, 2, 24
     rng = np.random.default_rng(20263)
     edge = int(round((0.5 + 0.4) * N - 0.5))
@@ -572,7 +572,7 @@ def test_errors_are_reported():
 @pytest.mark.parametrize("prec,kahan", [(L.F64, 1), (L.F32, 1), (L.F32, 0)])
 def test_errors_are_reported_2d(prec, kahan):
     """Square lattice, every step path (FP64 records pass and gather, FP32
-    exact-order kernel, FP32 register kernel): a negative density is
+    deposit kernel plain and compensated): a negative density is
     LBM_ESTATE; a reach beyond max_reach is LBM_EREACH."""
     n = 40
     N = n * n
@@ -612,11 +612,10 @@ def test_uniform_state_stays_uniform_bitwise():
 
 
 def test_restart_fp32_records_bitwise():
-    """FP32 square lattice with kahan = 0 carries each node's equilibrium
-    from the step that produced it to the next step (global records).
-    Checkpoint through lbm_moments / lbm_set_moments rebuilds them with the
-    records kernel instead: n then m steps must equal n + m steps bit for
-    bit (lambda = 1, so the unit conversion is exact)."""
+    """FP32 square lattice: checkpoint through lbm_moments / lbm_set_moments
+    in the same handle (its per-tile window records carry on): n then m
+    steps must equal n + m steps bit for bit (lambda = 1, so the unit
+    conversion is exact)."""
     nx, ny = 77, 45
     prims = I.random_smooth_prims(2, nx, ny, seed=71)
     cfg = L.make_config(2, nx, ny, precision=L.F32, bc_x=L.TRANSMISSIVE,
@@ -640,7 +639,7 @@ def test_restart_fp32_records_bitwise():
 def test_energy_clamps_counted_like_oracle(prec, kahan):
     """Nodes whose internal energy e = E - |V|^2/2 is negative are clamped to
     e = 0 and counted once per step that uses them, by every kernel (the
-    FP32 register kernel reads the clamp from the node's record)."""
+    FP32 deposit kernel counts them in the walk that owns the node)."""
     nx, ny = 48, 40
     n = nx * ny
     rng = np.random.default_rng(8)
@@ -663,7 +662,7 @@ def test_energy_clamps_counted_like_oracle(prec, kahan):
     assert d["eclamps"] == ec
 
 
-def test_fp32_register_kernel_reports_bad_state():
+def test_fp32_deposit_kernel_reports_bad_state():
     nx, ny = 64, 40
     cfg = L.make_config(2, nx, ny, precision=L.F32, bc_x=L.PERIODIC,
                         bc_y=L.PERIODIC, kahan=0)
@@ -680,15 +679,17 @@ def test_fp32_register_kernel_reports_bad_state():
 
 @pytest.mark.parametrize("bcs", BC2)
 @pytest.mark.parametrize("shape", [(3, 2), (7, 5), (33, 9)])
-def test_tiny_grids_fp32_register_kernel(bcs, shape):
+def test_tiny_grids_fp32_deposit_kernel(bcs, shape):
     """Grids narrower than the migration halo: most window slots of the
-    register kernel lie outside the grid and are filled from the nodes that
-    supply them (possibly several reflections or wraps away).  On a 3 x 2
-    grid a field may vary by only 1e-4 of its size, and m_y between two
-    walls one row apart is a near-cancelling sum of O(1) terms, so the mean
-    error is taken relative to the field's size (momentum: the larger of
-    max |m_x| and max |m_y|): a slot filled from the wrong node or with the
-    wrong mirror sign errs by the size of its contribution itself."""
+    deposit kernel lie outside the grid and are filled from the nodes that
+    supply them (possibly several reflections or wraps away).  Mean error
+    within 1e-5 of the field's range (the stated metric) wherever that
+    range is at least 1 % of the field's size.  On a 3 x 2 grid a field may
+    vary by only 1e-4 of its size, and m_y between two walls one row apart
+    is a near-cancelling sum of O(1) terms; there the error is taken
+    relative to the field's size (momentum: the larger of max |m_x| and max
+    |m_y|): a slot filled from the wrong node or with the wrong mirror sign
+    errs by the size of its contribution itself."""
     nx, ny = shape
     prims = I.random_smooth_prims(2, nx, ny, seed=4100 + nx * ny + bcs[0])
     g = _gpu(2, nx, ny, *bcs, prims=prims, steps=8, precision=L.F32,
@@ -697,9 +698,10 @@ def test_tiny_grids_fp32_register_kernel(bcs, shape):
     mom = max(np.max(np.abs(o["mx"])), np.max(np.abs(o["my"])))
     for f in FIELDS:
         size = mom if f in ("mx", "my") else np.max(np.abs(o[f]))
-        scale = max(np.ptp(o[f]), size, 1e-300)
+        rng = np.ptp(o[f])
+        scale = rng if rng >= 1e-2 * size else max(size, 1e-300)
         err = np.mean(np.abs(g[f] - o[f])) / scale
-        assert err <= 1e-5, (f, err)
+        assert err <= 1e-5, (f, err, rng, size)
 
 
 def test_sod_1d_solve_replayed_from_cuda_graph_bitwise():
