@@ -20,11 +20,11 @@
 // and data that vary along x only stay so bit for bit (their y-momentum
 // arrivals from rows +-c cancel exactly).
 //
-// Layout: one block per tile.  The block's window is 60 x 48 sources
+// Layout: one block per tile.  The block's window is 59 x 48 sources
 // (WCOLS x WROWS); with the step's reach R the tile is the window minus R on
-// every side, (60 - 2R) x (48 - 2R) destinations.
+// every side, (59 - 2R) x (48 - 2R) destinations.
 //  * Phase 1 (window).  Thread (lane, wx, g) owns window column
-//    lane + 29 wx (the two warps of a row overlap by three columns; column 60
+//    lane + 28 wx (the two warps of a row overlap by four columns; column 59
 //    holds deposits only) and walks the rows of group g (12 deposit rows,
 //    the groups' walks overlap; row 48 holds deposits only).  Walking down
 //    its column it loads each source's moments (coalesced: a warp reads 32
@@ -41,11 +41,12 @@
 // The window's sources are all of one type in most tiles early in a flow:
 // the first kernel deposits for the type of the tile's central node and
 // checks that every source had that type.  Otherwise the tile goes to the
-// second kernel, which groups the sources by c1 and by blocks of S lattice
-// shifts per axis (S = 1, 2 or 3, from the spread of n over the window):
-// n in {a .. a+S-1} x {b .. b+S-1}.  Relative to the base (a, b) such a
-// source lands at s + dn + k, dn in {0 .. S-1}^2, so the deposit weights
-// become hat functions over S + 1 offsets per axis (one walk per group),
+// second kernel, which groups the sources by c1 and by blocks of SX x SY
+// lattice shifts (SX, SY up to 4, from the spread of n over the window):
+// n in {a .. a+SX-1} x {b .. b+SY-1}.  Relative to the base (a, b) such a
+// source lands at s + dn + k, dn in {0 .. SX-1} x {0 .. SY-1}, so the
+// deposit weights become hat functions over SX + 1 and SY + 1 offsets (one
+// walk per group),
 // and the gather is the one-type gather at shift (a, b).  Groups are done in
 // ascending order, each adding its arrivals to the destinations.  The
 // smallest c1 and shift of a window are taken from the tile's previous step
@@ -62,10 +63,10 @@ namespace ds {
 
 constexpr int NWX = 2;                    // warps across a window row
 constexpr int CW = 32 * NWX;              // threads across
-constexpr int SPMAX = 3;                  // largest shift block of a group
+constexpr int SPMAX = 4;                  // largest shift block of a group
 constexpr int WSTEP = 32 - SPMAX;         // column offset of the second warp
-constexpr int DCOLS = WSTEP + 32;         // deposit columns 1 .. 60
-constexpr int WCOLS = DCOLS - 1;          // source columns 0 .. 59
+constexpr int DCOLS = WSTEP + 32;         // deposit columns 1 .. 59
+constexpr int WCOLS = DCOLS - 1;          // source columns 0 .. 58
 constexpr int NG = 4;                     // row groups
 constexpr int SH = 12;                    // rows a group deposits
 constexpr int WROWS = NG * SH;            // source rows 0 .. 47
@@ -560,23 +561,46 @@ __device__ __forceinline__ void walk_one_type(
 }
 
 
-// Shift block of a window's groups: the larger spread of n over the
-// window's emitting sources, at most SPMAX.
-__device__ __forceinline__ int block_of(const GStats& st) {
-  const float s = fmaxf(st.nxmax - st.nxmin, st.nymax - st.nymin) + 1.0f;
+// Shift block of a window's groups: per axis the spread of n over the
+// window's emitting sources, at most SPMAX, raised to the next block the
+// group walk is built for (1x1, 2x2, 2x3, 3x2, 3x3, 3x4, 4x3, 4x4).  A
+// block that holds a window's shifts deposits what the tightest one
+// deposits, so raising it changes no result; a window wider than SPMAX on
+// an axis keeps exactly SPMAX there (its groups are then split on that
+// axis, and the split must not change).
+struct Blk {
+  int sx, sy;
+};
+__device__ __forceinline__ Blk blk_pick(int sx, int sy) {
+  if (sx <= 1 && sy <= 1) return Blk{1, 1};
+  if (sx <= 2 && sy <= 2) return Blk{2, 2};
+  if (sx <= 2 && sy <= 3) return Blk{2, 3};
+  if (sx <= 3 && sy <= 2) return Blk{3, 2};
+  if (sx <= 3 && sy <= 3) return Blk{3, 3};
+  if (sx <= 3) return Blk{3, 4};
+  if (sy <= 3) return Blk{4, 3};
+  return Blk{4, 4};
+}
+__device__ __forceinline__ int spread_axis(float lo, float hi) {
+  const float s = hi - lo + 1.0f;
   return s <= 1.0f ? 1 : (s >= (float)SPMAX ? SPMAX : (int)s);
+}
+__device__ __forceinline__ Blk block_of(const GStats& st) {
+  return blk_pick(spread_axis(st.nxmin, st.nxmax),
+                  spread_axis(st.nymin, st.nymax));
 }
 
 // Per-tile record a step leaves for the next: 0 when the window held one
 // type (or nothing), else bit 31 with the window's smallest c1 and shift and
-// its block size, or bit 31 and bit 30 when those do not fit the record.
+// its block, or bit 31 and bit 30 when those do not fit the record.
 constexpr unsigned kRecUnknown = 0xc0000000u;
 __device__ __forceinline__ unsigned rec_encode(float c1min, float nxmin,
-                                               float nymin, int S) {
+                                               float nymin, Blk B) {
   if (!(c1min <= 63.0f && nxmin >= -128.0f && nxmin <= 127.0f &&
         nymin >= -128.0f && nymin <= 127.0f))
     return kRecUnknown;
-  return 0x80000000u | ((unsigned)(S - 1) << 24) | ((unsigned)c1min << 16) |
+  return 0x80000000u | ((unsigned)(B.sy - 1) << 26) |
+         ((unsigned)(B.sx - 1) << 24) | ((unsigned)c1min << 16) |
          ((unsigned)((int)nxmin + 128) << 8) | (unsigned)((int)nymin + 128);
 }
 __device__ __forceinline__ unsigned rec_of(const GStats& st) {
@@ -622,36 +646,37 @@ __device__ __forceinline__ void walk_stats(const StepArgs& a, float* rbase,
 }
 
 // A group walk's view of one source: its level records (zero unless the
-// source is in the group) and its hat weights over offsets 0 .. S per axis.
-template <int S>
+// source is in the group) and its hat weights over offsets 0 .. SX and
+// 0 .. SY.
+template <int SX, int SY>
 struct GSrc {
   float4 l1, l2;
-  float ax[S + 1], ay[S + 1];
+  float ax[SX + 1], ay[SY + 1];
 };
 
-// Group walk (S = shift block): deposits the sources of group G, i.e. c1 =
-// c1m + Gc and n in {a .. a+S-1} x {b .. b+S-1} with a = nxm + S GX,
-// b = nym + S GY (G = Gc 65536 + GX 256 + GY):
-//   D(q) = sum over the group's sources s and offsets o in {0 .. S}^2 of
+// Group walk (block SX x SY): deposits the sources of group G, i.e. c1 =
+// c1m + Gc and n in {a .. a+SX-1} x {b .. b+SY-1} with a = nxm + SX GX,
+// b = nym + SY GY (G = Gc 65536 + GX 256 + GY):
+//   D(q) = sum over the group's sources s and offsets o of
 //          h_x(o_x) h_y(o_y) L(s),  q = s + o,
 // h the hat weights of eq 29 at dn = n - (a, b): (1 - f) at dn, f at dn + 1.
-// Deposit row t takes the sources of rows t - S .. t of this column (kept
-// from the rows walked before) and, for o_x > 0, those of the columns to
-// the left (shuffles by o_x).  Also gathers the window statistics and the
-// next group above G.
-template <int S, bool INT>
+// Deposit row t takes the sources of rows t - SY .. t of this column (kept
+// from the rows walked before), oldest first, and, for o_x > 0, those of the
+// columns to the left (shuffles by o_x).  Also gathers the window
+// statistics and the next group above G.
+template <int SX, int SY, bool INT>
 __device__ __forceinline__ void walk_group(
     const StepArgs& a, float4* __restrict__ D1, float4* __restrict__ D2,
     float* rbase, int x0, int y0, int R, int TX, int TY,
     float G, float c1m, float nxm, float nym, bool count_clamps,
     GStats& st) {
   const Column col = column_of(a, x0, R, TX, INT);
-  const int ly0 = SH * col.g - (S - 1);
-  constexpr int LAST = SH + S - 1;
+  const int ly0 = SH * col.g - (SY - 1);
+  constexpr int LAST = SH + SY - 1;
   const float kq = a.k.kq_f;
   // rows of this walk whose node the tile owns and that lie in the group's
   // deposit rows (each owned node counted by one walk)
-  const int own_lo = max(S, R - ly0);
+  const int own_lo = max(SY, R - ly0);
   const int own_hi = col.col_own && count_clamps
                          ? min(min(LAST, R + TY - 1 - ly0), a.ny - 1 - (y0 - R) - ly0)
                          : -1;
@@ -659,14 +684,18 @@ __device__ __forceinline__ void walk_group(
   const float Gr = __fmaf_rn(-65536.0f, Gc, G);
   const float GX = floorf(Gr * (1.0f / 256.0f));
   const float GY = __fmaf_rn(-256.0f, GX, Gr);
-  const float Sf = (float)S, rS = 1.0f / (float)S;   // rS >= 1/S: exact floors
+  // 1/SX, 1/SY rounded up (1/3 rounds up in FP32): exact floors of the
+  // small integers they divide
+  constexpr float rX = 1.0f / (float)SX, rY = 1.0f / (float)SY;
   // h[k]: the source k + 1 rows above the current one
-  GSrc<S> h[S];
+  GSrc<SX, SY> h[SY];
 #pragma unroll
-  for (int k = 0; k < S; ++k) {
+  for (int k = 0; k < SY; ++k) {
     h[k].l1 = h[k].l2 = f4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int o = 0; o <= S; ++o) h[k].ax[o] = h[k].ay[o] = 0.0f;
+    for (int o = 0; o <= SX; ++o) h[k].ax[o] = 0.0f;
+#pragma unroll
+    for (int o = 0; o <= SY; ++o) h[k].ay[o] = 0.0f;
   }
   SrcRing ring = ring_of(a, rbase);
 #pragma unroll
@@ -693,7 +722,7 @@ __device__ __forceinline__ void walk_group(
     // the source's group, relative to the assumed minima
     const float dc = __fsub_rn(q.c1, c1m);
     const float dx = __fsub_rn(q.nxf, nxm), dy = __fsub_rn(q.nyf, nym);
-    const float gx = floorf(dx * rS), gy = floorf(dy * rS);
+    const float gx = floorf(dx * rX), gy = floorf(dy * rY);
     const float gid = q.emits ? __fmaf_rn(65536.0f, dc, __fmaf_rn(256.0f, gx, gy))
                               : kNoType;
     const bool mine = gid == G;
@@ -701,29 +730,34 @@ __device__ __forceinline__ void walk_group(
     st.tnext = fminf(st.tnext, gid > G ? gid : kNoType);
     gstats_add(st, q.emits, q.c1, q.nxf, q.nyf);
     if (q.clamp && r >= own_lo && r <= own_hi) st.clamps += 1;
-    GSrc<S> cur;
+    GSrc<SX, SY> cur;
     const float4 v4 = f4(1.0f, q.Vx, q.Vy, q.Eb);
     cur.l1 = mul4(mine ? q.d1 : 0.0f, v4);
     cur.l2 = mul4(mine ? q.d2 : 0.0f, v4);
-    const float dnx = __fmaf_rn(-Sf, gx, dx), dny = __fmaf_rn(-Sf, gy, dy);
+    const float dnx = __fmaf_rn(-(float)SX, gx, dx);
+    const float dny = __fmaf_rn(-(float)SY, gy, dy);
     const float gx1 = __fsub_rn(1.0f, q.fx), gy1 = __fsub_rn(1.0f, q.fy);
 #pragma unroll
-    for (int o = 0; o <= S; ++o) {
+    for (int o = 0; o <= SX; ++o) {
       const float of = (float)o;
       cur.ax[o] = dnx == of ? gx1 : (dnx == of - 1.0f ? q.fx : 0.0f);
+    }
+#pragma unroll
+    for (int o = 0; o <= SY; ++o) {
+      const float of = (float)o;
       cur.ay[o] = dny == of ? gy1 : (dny == of - 1.0f ? q.fy : 0.0f);
     }
     // deposit row ly: the part of this column's sources landing o_x columns
     // to the right, summed over their rows, then moved right by shuffles
     float4 D1r = f4(0.f, 0.f, 0.f, 0.f), D2r = D1r;
 #pragma unroll
-    for (int ox = 0; ox <= S; ++ox) {
-      // oldest source first, the current one last: with S = 1 the one-type
-      // walk's operations in its order, so both give the same bits
-      const float wl = __fmul_rn(h[S - 1].ax[ox], h[S - 1].ay[S]);
-      float4 t1 = mul4(wl, h[S - 1].l1), t2 = mul4(wl, h[S - 1].l2);
+    for (int ox = 0; ox <= SX; ++ox) {
+      // oldest source first, the current one last: with a 1 x 1 block the
+      // one-type walk's operations in its order, so both give the same bits
+      const float wl = __fmul_rn(h[SY - 1].ax[ox], h[SY - 1].ay[SY]);
+      float4 t1 = mul4(wl, h[SY - 1].l1), t2 = mul4(wl, h[SY - 1].l2);
 #pragma unroll
-      for (int k = S - 2; k >= 0; --k) {
+      for (int k = SY - 2; k >= 0; --k) {
         const float w = __fmul_rn(h[k].ax[ox], h[k].ay[k + 1]);
         t1 = fma4(w, h[k].l1, t1);
         t2 = fma4(w, h[k].l2, t2);
@@ -743,13 +777,45 @@ __device__ __forceinline__ void walk_group(
       }
     }
 #pragma unroll
-    for (int k = S - 1; k > 0; --k) h[k] = h[k - 1];
+    for (int k = SY - 1; k > 0; --k) h[k] = h[k - 1];
     h[0] = cur;
-    if (r >= S && col.store_col) {
+    if (r >= SY && col.store_col) {
       D1[ly * DP + col.lx] = D1r;
       D2[ly * DP + col.lx] = D2r;
     }
   }
+}
+
+// The group walk for block B (the blocks blk_pick returns).
+template <bool INT>
+__device__ __forceinline__ void walk_group_blk(
+    Blk B, const StepArgs& a, float4* __restrict__ D1,
+    float4* __restrict__ D2, float* rbase, int x0, int y0, int R, int TX,
+    int TY, float G, float c1m, float nxm, float nym, bool cc, GStats& st) {
+  if (B.sx == 1)
+    walk_group<1, 1, INT>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m, nxm,
+                                  nym, cc, st);
+  else if (B.sx == 2 && B.sy == 2)
+    walk_group<2, 2, INT>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m, nxm,
+                                  nym, cc, st);
+  else if (B.sx == 2)
+    walk_group<2, 3, INT>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m, nxm,
+                                  nym, cc, st);
+  else if (B.sx == 3 && B.sy == 2)
+    walk_group<3, 2, INT>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m, nxm,
+                                  nym, cc, st);
+  else if (B.sx == 3 && B.sy == 3)
+    walk_group<3, 3, INT>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m, nxm,
+                                  nym, cc, st);
+  else if (B.sx == 3)
+    walk_group<3, 4, INT>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m, nxm,
+                                  nym, cc, st);
+  else if (B.sy == 3)
+    walk_group<4, 3, INT>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m, nxm,
+                                  nym, cc, st);
+  else
+    walk_group<4, 4, INT>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m, nxm,
+                                  nym, cc, st);
 }
 
 // Arrivals of the four packets of one level with speed c (template C >= 0;
@@ -980,7 +1046,7 @@ __device__ __forceinline__ void finish_tile(const StepArgs& a, int x0, int y0,
 
 // Every packet of a one-type walk (slack 0) or of a group walk (slack 1:
 // its base may lie below its sources' shift) within reach R reads deposits
-// that lie in rows 1 .. 48 and columns 1 .. 60.
+// that lie in rows 1 .. 48 and columns 1 .. 59.
 __device__ __forceinline__ bool type_fits(Type ty, int R, int slack) {
   const int c2 = ty.c1 + 1;
   return ty.nx <= R - 1 - c2 && -ty.nx <= R - c2 + slack &&
@@ -1186,10 +1252,10 @@ __device__ __forceinline__ void ds_mixed_tile(const StepArgs& a, int b,
                           y0 - R >= 0 && y0 - R + WROWS <= a.ny;
     const unsigned rec = a.hint[b];
     float c1m, nxm, nym;
-    int S;
+    Blk B;
     bool counted = false, checked = false;
     if ((rec & 0xc0000000u) == 0x80000000u) {
-      S = min((int)((rec >> 24) & 3u) + 1, SPMAX);
+      B = blk_pick((int)((rec >> 24) & 3u) + 1, (int)((rec >> 26) & 3u) + 1);
       c1m = (float)((rec >> 16) & 0xffu);
       nxm = (float)((int)((rec >> 8) & 0xffu) - 128);
       nym = (float)((int)(rec & 0xffu) - 128);
@@ -1205,79 +1271,66 @@ __device__ __forceinline__ void ds_mixed_tile(const StepArgs& a, int b,
       c1m = s0.c1min;
       nxm = s0.nxmin;
       nym = s0.nymin;
-      S = block_of(s0);
+      B = block_of(s0);
       checked = true;
     }
-    TileOut to = tile_out_init();
-    GStats fin = gstats_init();
     float G = 0.0f;  // (c1m, blocks (0, 0)); possibly empty
     bool first = true;
     while (true) {
       __syncthreads();  // the previous gather and statistics are done
       GStats s2 = gstats_init();
       const bool cc = !counted;
-      if (interior) {
-        if (S == 1)
-          walk_group<1, true>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m,
+      if (interior)
+        walk_group_blk<true>(B, a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m,
+                             nxm, nym, cc, s2);
+      else
+        walk_group_blk<false>(B, a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m,
                               nxm, nym, cc, s2);
-        else if (S == 2)
-          walk_group<2, true>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m,
-                              nxm, nym, cc, s2);
-        else
-          walk_group<3, true>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m,
-                              nxm, nym, cc, s2);
-      } else {
-        if (S == 1)
-          walk_group<1, false>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m,
-                               nxm, nym, cc, s2);
-        else if (S == 2)
-          walk_group<2, false>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m,
-                               nxm, nym, cc, s2);
-        else
-          walk_group<3, false>(a, D1, D2, rbase, x0, y0, R, TX, TY, G, c1m,
-                               nxm, nym, cc, s2);
-      }
       if (!counted) commit_clamps(a, s2.clamps);
       counted = true;
       reduce_gstats(s2, red);
       if (!checked) {
-        // the result must follow from this step's state alone.  A window
-        // whose shifts span at most SPMAX per axis takes one group per c1,
-        // in ascending c1 order, and any block that holds all its shifts
-        // deposits the same values (offsets outside the sources' range add
-        // exact zeros in the same order), so minima and block taken from an
-        // earlier step stand when the c1 minimum is not above the state's
-        // and the block holds the window's shifts.  Wider windows take the
-        // blocks from the state's minima.
+        // the result must follow from this step's state alone.  Groups go
+        // in ascending c1, and on an axis where the window's shifts span
+        // at most SPMAX any block that holds them all deposits the same
+        // values (offsets outside the sources' range add exact zeros in
+        // the same order), so minima and block taken from an earlier step
+        // stand when the c1 minimum is not above the state's and each axis
+        // holds its shifts; a wider axis needs blocks of SPMAX from the
+        // state's minimum.  (And the packets of the largest level speed
+        // must stay within the deposits, which a block based below the
+        // state's minima can miss.)
         checked = true;
-        const bool wide_n = fmaxf(s2.nxmax - s2.nxmin, s2.nymax - s2.nymin) >=
-                            (float)SPMAX;
-        // (and its packets of the largest level speed stay within the
-        // deposits, which a block based below the state's minima can miss)
+        const bool wx = s2.nxmax - s2.nxmin >= (float)SPMAX;
+        const bool wy = s2.nymax - s2.nymin >= (float)SPMAX;
+        const bool okx = wx ? (nxm == s2.nxmin && B.sx == SPMAX)
+                            : (nxm <= s2.nxmin &&
+                               s2.nxmax <= nxm + (float)(B.sx - 1));
+        const bool oky = wy ? (nym == s2.nymin && B.sy == SPMAX)
+                            : (nym <= s2.nymin &&
+                               s2.nymax <= nym + (float)(B.sy - 1));
         const bool holds =
-            c1m <= s2.c1min && nxm <= s2.nxmin &&
-            s2.nxmax <= nxm + (float)(S - 1) && nym <= s2.nymin &&
-            s2.nymax <= nym + (float)(S - 1) &&
+            c1m <= s2.c1min && okx && oky &&
             type_fits(Type{(int)nxm, (int)nym, (int)s2.c1max}, R, 1);
-        const bool same = c1m == s2.c1min && nxm == s2.nxmin &&
-                          nym == s2.nymin && S == SPMAX;
-        if (s2.c1max >= 0.0f && !(wide_n ? same : holds)) {
+        if (s2.c1max >= 0.0f && !holds) {
           c1m = s2.c1min;
           nxm = s2.nxmin;
           nym = s2.nymin;
-          S = block_of(s2);
+          B = block_of(s2);
           G = 0.0f;
           continue;
         }
       }
-      fin = s2;
       const bool last = !(s2.tnext < kNoType);
+      // the node ends and totals of the last pass (nothing held across
+      // the walks)
+      TileOut to = tile_out_init();
       const float Gc = floorf(G * (1.0f / 65536.0f));
       const float Gr = __fmaf_rn(-65536.0f, Gc, G);
       const float GX = floorf(Gr * (1.0f / 256.0f));
       const float GY = __fmaf_rn(-256.0f, GX, Gr);
-      const Type ty{(int)__fmaf_rn((float)S, GX, nxm),
-                    (int)__fmaf_rn((float)S, GY, nym), (int)(c1m + Gc)};
+      const Type ty{(int)__fmaf_rn((float)B.sx, GX, nxm),
+                    (int)__fmaf_rn((float)B.sy, GY, nym), (int)(c1m + Gc)};
       if (s2.any && type_fits(ty, R, 1)) {
         gather_dispatch<KAHAN>(a, D1, D2, x0, y0, R, TX, TY, ty, first, last,
                                to);
@@ -1286,11 +1339,13 @@ __device__ __forceinline__ void ds_mixed_tile(const StepArgs& a, int b,
         if (s2.any && tid == 0) atomicOr(&a.scr->flags, kFlagReach);
         if (last) finish_tile(a, x0, y0, TX, TY, first, to);
       }
-      if (last) break;
+      if (last) {
+        if (tid == 0) a.hint[b] = rec_of(s2);
+        tile_publish(a, b, to, *sm.tred);
+        break;
+      }
       G = s2.tnext;
     }
-    if (tid == 0) a.hint[b] = rec_of(fin);
-    tile_publish(a, b, to, *sm.tred);
   }
 }
 template <bool KAHAN>
