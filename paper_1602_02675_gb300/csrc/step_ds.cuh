@@ -592,8 +592,10 @@ __device__ __forceinline__ Blk block_of(const GStats& st) {
 
 // Per-tile record a step leaves for the next: 0 when the window held one
 // type (or nothing), else bit 31 with the window's smallest c1 and shift and
-// its block, or bit 31 and bit 30 when those do not fit the record.
+// its block, or bit 31 and bit 30 when those do not fit the record; bit 28
+// marks a tile whose carried-over block had to be redone.
 constexpr unsigned kRecUnknown = 0xc0000000u;
+constexpr unsigned kRecRedone = 0x10000000u;  // block redone at that step
 __device__ __forceinline__ unsigned rec_encode(float c1min, float nxmin,
                                                float nymin, Blk B) {
   if (!(c1min <= 63.0f && nxmin >= -128.0f && nxmin <= 127.0f &&
@@ -1253,8 +1255,10 @@ __device__ __forceinline__ void ds_mixed_tile(const StepArgs& a, int b,
     const unsigned rec = a.hint[b];
     float c1m, nxm, nym;
     Blk B;
-    bool counted = false, checked = false;
-    if ((rec & 0xc0000000u) == 0x80000000u) {
+    bool counted = false, checked = false, redone = false;
+    // a tile whose carried-over block failed at the last step starts with
+    // the statistics walk (cheaper than a group walk redone)
+    if ((rec & 0xd0000000u) == 0x80000000u) {
       B = blk_pick((int)((rec >> 24) & 3u) + 1, (int)((rec >> 26) & 3u) + 1);
       c1m = (float)((rec >> 16) & 0xffu);
       nxm = (float)((int)((rec >> 8) & 0xffu) - 128);
@@ -1313,6 +1317,7 @@ __device__ __forceinline__ void ds_mixed_tile(const StepArgs& a, int b,
             c1m <= s2.c1min && okx && oky &&
             type_fits(Type{(int)nxm, (int)nym, (int)s2.c1max}, R, 1);
         if (s2.c1max >= 0.0f && !holds) {
+          redone = true;
           c1m = s2.c1min;
           nxm = s2.nxmin;
           nym = s2.nymin;
@@ -1340,7 +1345,10 @@ __device__ __forceinline__ void ds_mixed_tile(const StepArgs& a, int b,
         if (last) finish_tile(a, x0, y0, TX, TY, first, to);
       }
       if (last) {
-        if (tid == 0) a.hint[b] = rec_of(s2);
+        if (tid == 0) {
+          const unsigned r = rec_of(s2);
+          a.hint[b] = r != 0u && redone ? (r | kRecRedone) : r;
+        }
         tile_publish(a, b, to, *sm.tred);
         break;
       }
