@@ -306,7 +306,7 @@ def run_cylinder(args, rank, world):
             "frac_of_nominal": round(achieved / 7900.0, 4),
             "duration": "CUDA events around lbm_step over the whole timed "
                         "solve: the one-type tile kernel, the mixed-window "
-                        "kernel and the one-block finalize kernel"}
+                        "kernel and the finalize kernel"}
     peak32 = L.lbm_measure_fma_peak(L.F32, stream.cuda_stream)
     peak64 = L.lbm_measure_fma_peak(L.F64, stream.cuda_stream)
     alu = {"flop_per_node_update": 256,
