@@ -17,14 +17,14 @@
  *    doubles with x fastest, and are not retained after the call returns.
  *  - All device memory is owned by the handle and allocated in lbm_create:
  *    two moment buffers (4 fields x n x 4 or 8 bytes each), a few scratch
- *    words, and for an F32 square-lattice handle with kahan = 0 and
- *    max_reach <= 6 two sets of per-node equilibrium records (24 bytes per
- *    node each), which carry each node's equilibrium (Section III.B) from
- *    the step that produced the node to the step that uses it; an F64
- *    square-lattice handle holds one set of source records (248 bytes per
- *    node of the grid padded by max_reach on every side: each source's
- *    packets, level densities and corner weights), rewritten from the
- *    moments at the start of every step.
+ *    words and per-block partial totals; an F32 square-lattice handle with
+ *    max_reach <= 6 adds 8 bytes per tile of its deposit kernel (a record
+ *    of the tile's window at the last step, a starting guess only, and a
+ *    queue slot; a tile holds about 2000 nodes); an F64 square-lattice
+ *    handle holds one set of source records (248 bytes per node of the
+ *    grid padded by max_reach on every side: each source's packets, level
+ *    densities and corner weights), rewritten from the moments at the start
+ *    of every step.
  *  - Work is issued on the stream given in lbm_config.stream (a
  *    cudaStream_t, or NULL for the default stream), in call order.
  *    lbm_step returns before the GPU finishes; lbm_moments, lbm_conservation,
