@@ -238,7 +238,11 @@ struct SrcEq {
   bool emits, clamp;
   float c1, nxf, nyf, fx, fy, d1, d2, Vx, Vy, Eb;
 };
-__device__ __forceinline__ SrcEq source_eq(float4 m, float kq) {
+// kg: the level constants of the walk's group when every member shares
+// them (the densities of sources outside the group are never used), else
+// null: each source's own.
+__device__ __forceinline__ SrcEq source_eq(float4 m, float kq,
+                                           const LevelK* kg = nullptr) {
   SrcEq q;
   const float rho = m.x;
   const EqCore c = eq_core(rho, m.y, m.z, m.w, kq);
@@ -250,7 +254,7 @@ __device__ __forceinline__ SrcEq source_eq(float4 m, float kq) {
   q.c1 = (c.X >= 1.0f ? 1.0f : 0.0f) + (c.X >= 4.0f ? 1.0f : 0.0f) +
          (c.X >= 9.0f ? 1.0f : 0.0f);
   if (wide) q.c1 = c.X < 16.0f ? q.c1 : c1_of(c.X);
-  level_dens(rho, c.X, q.emits, level_k(q.c1), q.d1, q.d2);
+  level_dens(rho, c.X, q.emits, kg ? *kg : level_k(q.c1), q.d1, q.d2);
   // phi = e - X / 2 (eq 15 with D/2 (gamma - 1) e = X / 2)
   const float phi = __fmaf_rn(-0.5f, c.X, fmaxf(c.eraw, 0.0f));
   q.Eb = q.emits ? __fmaf_rn(0.5f, c.kin2, phi) : 0.0f;
@@ -689,6 +693,10 @@ __device__ __forceinline__ void walk_group(
   // 1/SX, 1/SY rounded up (1/3 rounds up in FP32): exact floors of the
   // small integers they divide
   constexpr float rX = 1.0f / (float)SX, rY = 1.0f / (float)SY;
+  // the group's level constants (its members' densities), where the
+  // registers allow; larger blocks form them per source
+  constexpr bool kGroupK = SX * SY <= 9;
+  const LevelK lk = level_k(__fadd_rn(c1m, Gc));
   // h[k]: the source k + 1 rows above the current one
   GSrc<SX, SY> h[SY];
 #pragma unroll
@@ -709,7 +717,7 @@ __device__ __forceinline__ void walk_group(
       cp_async_wait<0>();
     const float4 m = ring.template take<INT>(a, col, y0, R, ly0 + r, slot);
     if (r + PF <= LAST) ring.template issue<INT>(a, col, y0, R, ly0 + r + PF, slot);
-    return source_eq(m, kq);
+    return source_eq(m, kq, kGroupK ? &lk : nullptr);
   };
   SrcEq qn = row_eq(0, 0);
   int slot = 1;
@@ -739,16 +747,20 @@ __device__ __forceinline__ void walk_group(
     const float dnx = __fmaf_rn(-(float)SX, gx, dx);
     const float dny = __fmaf_rn(-(float)SY, gy, dy);
     const float gx1 = __fsub_rn(1.0f, q.fx), gy1 = __fsub_rn(1.0f, q.fy);
+    // hat weights: (1 - f) at dn, f at dn + 1 (one comparison per offset)
+    bool px[SX], py[SY];
 #pragma unroll
-    for (int o = 0; o <= SX; ++o) {
-      const float of = (float)o;
-      cur.ax[o] = dnx == of ? gx1 : (dnx == of - 1.0f ? q.fx : 0.0f);
-    }
+    for (int o = 0; o < SX; ++o) px[o] = dnx == (float)o;
 #pragma unroll
-    for (int o = 0; o <= SY; ++o) {
-      const float of = (float)o;
-      cur.ay[o] = dny == of ? gy1 : (dny == of - 1.0f ? q.fy : 0.0f);
-    }
+    for (int o = 0; o < SY; ++o) py[o] = dny == (float)o;
+    cur.ax[0] = px[0] ? gx1 : 0.0f;
+#pragma unroll
+    for (int o = 1; o < SX; ++o) cur.ax[o] = px[o] ? gx1 : (px[o - 1] ? q.fx : 0.0f);
+    cur.ax[SX] = px[SX - 1] ? q.fx : 0.0f;
+    cur.ay[0] = py[0] ? gy1 : 0.0f;
+#pragma unroll
+    for (int o = 1; o < SY; ++o) cur.ay[o] = py[o] ? gy1 : (py[o - 1] ? q.fy : 0.0f);
+    cur.ay[SY] = py[SY - 1] ? q.fy : 0.0f;
     // deposit row ly: the part of this column's sources landing o_x columns
     // to the right, summed over their rows, then moved right by shuffles
     float4 D1r = f4(0.f, 0.f, 0.f, 0.f), D2r = D1r;
