@@ -474,12 +474,11 @@ __device__ __forceinline__ void source_type(float4 m, float kq, bool& emits,
              : kNoType;
 }
 
-// Result of a one-type walk, per thread: whether a source emits, whether an
-// emitting source has another type than the walk's, and the clamped
-// energies of owned nodes.
+// Result of a one-type walk, per thread: whether an emitting source has
+// another type than the walk's, and the clamped energies of owned nodes.
 struct OneTypeFlags {
   unsigned clamps;
-  bool emit, other;
+  bool other;
 };
 
 // One-type walk for the tile's guessed type T, the type of its central node
@@ -537,7 +536,6 @@ __device__ __forceinline__ void walk_one_type(
       qn = row_eq(r + 1, slot);
       slot = slot + 1 == PF ? 0 : slot + 1;
     }
-    fl.emit |= q.emits;
     fl.other |= q.emits && !q.mine;
     if (q.clamp && r >= own_lo && r <= own_hi) fl.clamps += 1;
     // level records L_v = d_v (1, V_x, V_y, E_b) of the sources of type T
@@ -1189,7 +1187,7 @@ __device__ __forceinline__ void ds_first_tile(const StepArgs& a, int b,
   // guess: the type of the tile's central node (every thread forms it; its
   // load overlaps the walk's first loads)
   float T0;
-  OneTypeFlags fl{0u, false, false};
+  OneTypeFlags fl{0u, false};
   {
     const int cx = min(x0 + TX / 2, a.nx - 1), cy = min(y0 + TY / 2, a.ny - 1);
     const long long i = (long long)cy * a.nx + cx;
@@ -1203,9 +1201,11 @@ __device__ __forceinline__ void ds_first_tile(const StepArgs& a, int b,
     else
       walk_one_type<false>(a, D1, D2, rbase, x0, y0, R, TX, TY, m, T0, fl);
   }
-  // the barriers after the deposits, with the block's flags
+  // the barrier after the deposits, with the block's flag; without another
+  // type in the window, nothing emits exactly when the central node does
+  // not (every emitting source would have another type than its kNoType)
   const bool other = __syncthreads_or(fl.other) != 0;
-  const bool none = __syncthreads_or(fl.emit) == 0;
+  const bool none = T0 == kNoType;
   if (other) {
     // the mixed-window kernel finds the window's minima and counts its
     // clamps
