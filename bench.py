@@ -204,12 +204,12 @@ class Clocks:
 # our arm
 # --------------------------------------------------------------------------
 def fp32_kernel_name(kahan):
-    return "lbm::ds::step2d_ds<%s>" % ("false" if kahan == 0 else "true")
+    return "lbm::ds::step2d_ds_fused<%s>" % ("false" if kahan == 0 else "true")
 
 
-# launches of ours per 2-D FP32 step: the one-type tile kernel, the
-# persistent mixed-tile kernel and the one-block finalize kernel
-DS_LAUNCHES_PER_STEP = 3
+# launches of ours per 2-D FP32 step: the persistent deposit kernel and the
+# finalize kernel
+DS_LAUNCHES_PER_STEP = 2
 
 
 def run_cylinder(args, rank, world):
@@ -305,8 +305,7 @@ def run_cylinder(args, rank, world):
             "nominal_peak": 7900.0,
             "frac_of_nominal": round(achieved / 7900.0, 4),
             "duration": "CUDA events around lbm_step over the whole timed "
-                        "solve: the one-type tile kernel, the mixed-window "
-                        "kernel and the finalize kernel"}
+                        "solve: the deposit kernel and the finalize kernel"}
     peak32 = L.lbm_measure_fma_peak(L.F32, stream.cuda_stream)
     peak64 = L.lbm_measure_fma_peak(L.F64, stream.cuda_stream)
     alu = {"flop_per_node_update": 256,

@@ -1153,10 +1153,11 @@ struct DsSmem {
   int* red;
   TileRed* tred;
 };
-// Tile b of the grid a describes; `item` is what the mixed-window queue
-// (count qn, list ql) receives for it.
+// Tile b of the grid a describes, if its window holds one type; returns
+// true when the tile is left for the mixed-window path (then queued as
+// `item` in the queue of count qn and list ql, when ql is given).
 template <bool KAHAN>
-__device__ __forceinline__ void ds_first_tile(const StepArgs& a, int b,
+__device__ __forceinline__ bool ds_first_tile(const StepArgs& a, int b,
                                               int item, unsigned* qn,
                                               int* ql, const DsSmem& sm) {
   float4* D1 = sm.D1;
@@ -1169,14 +1170,14 @@ __device__ __forceinline__ void ds_first_tile(const StepArgs& a, int b,
     if (a.do_cons && tid < 4)
       reinterpret_cast<float2*>(a.part)[(long long)b * 4 + tid] =
           make_float2(0.f, 0.f);
-    return;
+    return false;
   }
   auto enqueue = [&]() {
-    if (tid == 0) ql[atomicAdd(qn, 1u)] = item;
+    if (ql && tid == 0) ql[atomicAdd(qn, 1u)] = item;
   };
   if (a.hint[b]) {
     enqueue();
-    return;
+    return true;
   }
   const int R = g.R, TX = g.TX, TY = g.TY;
   const int ty_i = b / g.tiles_x, tx_i = b - ty_i * g.tiles_x;
@@ -1211,7 +1212,7 @@ __device__ __forceinline__ void ds_first_tile(const StepArgs& a, int b,
     // clamps
     if (tid == 0) a.hint[b] = kRecUnknown;
     enqueue();
-    return;
+    return true;
   }
   commit_clamps(a, fl.clamps);
   TileOut to = tile_out_init();
@@ -1227,6 +1228,7 @@ __device__ __forceinline__ void ds_first_tile(const StepArgs& a, int b,
     }
   }
   tile_publish(a, b, to, *sm.tred);
+  return false;
 }
 template <bool KAHAN>
 __global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
@@ -1385,6 +1387,35 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds_mixed(const StepArgs a) {
     if (k >= nq) break;
     ds_mixed_tile<KAHAN>(a, a.mixed_list[k], sm);
     __syncthreads();  // the next tile reuses the deposits and the ring
+  }
+}
+
+// The step in one persistent kernel: blocks take tiles by ticket (all the
+// tiles of the largest reach); a tile whose window held several types at
+// the last step, or turns out to hold several now, goes on to the group
+// walks in the same block.  No queue, no second launch, and no idle tail
+// between the one-type and the mixed tiles.  Same tile code, so the same
+// results as the two kernels.
+template <bool KAHAN>
+__global__ void __launch_bounds__(NTHR, 2) step2d_ds_fused(const StepArgs a) {
+  extern __shared__ __align__(16) float4 dsm[];
+  __shared__ int red[NGSTAT * NWARP];
+  __shared__ TileRed tred;
+  __shared__ int s_k;
+  const DsSmem sm{dsm, dsm + PLANE, reinterpret_cast<float*>(dsm + 2 * PLANE),
+                  red, &tred};
+  if (threadIdx.x == 0) s_k = (int)atomicAdd(&a.scr->mixed_ticket, 1u);
+  while (true) {
+    __syncthreads();
+    const int k = s_k;
+    __syncthreads();
+    if (k >= a.nblocks) break;
+    // the next ticket, taken now: its latency hides behind this tile
+    if (threadIdx.x == 0) s_k = (int)atomicAdd(&a.scr->mixed_ticket, 1u);
+    if (ds_first_tile<KAHAN>(a, k, k, nullptr, nullptr, sm)) {
+      __syncthreads();  // the walk's deposits and record are settled
+      ds_mixed_tile<KAHAN>(a, k, sm);
+    }
   }
 }
 

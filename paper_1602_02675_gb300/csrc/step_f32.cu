@@ -47,17 +47,14 @@ cudaError_t launch_step_f32(int dim, const StepArgs& a, size_t smem,
     // step's tile count exit
     StepArgs b = a;
     b.nblocks = ds::tiles_for(a.nx, a.ny, a.r_cap);
-    if (!b.hint || !b.mixed_list) return cudaErrorInvalidValue;
-    // the mixed-window kernel: persistent, two blocks per multiprocessor
-    int nb2 = 2 * device_sm_count();
-    if (nb2 > b.nblocks) nb2 = b.nblocks;
-    if (a.kahan) {
-      ds::step2d_ds<true><<<(unsigned)b.nblocks, ds::NTHR, ds::smem_bytes(), s>>>(b);
-      ds::step2d_ds_mixed<true><<<(unsigned)nb2, ds::NTHR, ds::smem_bytes(), s>>>(b);
-    } else {
-      ds::step2d_ds<false><<<(unsigned)b.nblocks, ds::NTHR, ds::smem_bytes(), s>>>(b);
-      ds::step2d_ds_mixed<false><<<(unsigned)nb2, ds::NTHR, ds::smem_bytes(), s>>>(b);
-    }
+    if (!b.hint) return cudaErrorInvalidValue;
+    // one persistent kernel, two blocks per multiprocessor
+    int nb = 2 * device_sm_count();
+    if (nb > b.nblocks) nb = b.nblocks;
+    if (a.kahan)
+      ds::step2d_ds_fused<true><<<(unsigned)nb, ds::NTHR, ds::smem_bytes(), s>>>(b);
+    else
+      ds::step2d_ds_fused<false><<<(unsigned)nb, ds::NTHR, ds::smem_bytes(), s>>>(b);
     ds::finalize2d<<<ds::FIN_BLOCKS, ds::NTHR, 0, s>>>(b.scr, b.part, b.nblocks,
                                                        b.do_cons);
   }
@@ -101,10 +98,8 @@ cudaError_t step_prepare_f32(int dim, size_t smem) {
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // two blocks per multiprocessor need the largest shared-memory carveout
-  for (const void* fn : {(const void*)ds::step2d_ds<false>,
-                         (const void*)ds::step2d_ds<true>,
-                         (const void*)ds::step2d_ds_mixed<false>,
-                         (const void*)ds::step2d_ds_mixed<true>}) {
+  for (const void* fn : {(const void*)ds::step2d_ds_fused<false>,
+                         (const void*)ds::step2d_ds_fused<true>}) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
@@ -128,13 +123,13 @@ cudaError_t step_raise_smem_f32(int dim, size_t smem) {
       dim == 1 ? (const void*)step_kernel<float, 1, false>
                : (const void*)step_kernel<float, 2, false>,
       dim == 1 ? (const void*)step_kernel<float, 1, true, 32>
-               : (const void*)ds::step2d_ds<true>,
+               : (const void*)ds::step2d_ds_fused<true>,
       dim == 1 ? (const void*)step_kernel<float, 1, false, 32>
-               : (const void*)ds::step2d_ds<false>,
+               : (const void*)ds::step2d_ds_fused<false>,
       dim == 1 ? (const void*)step_kernel<float, 1, true, 32, 16>
-               : (const void*)ds::step2d_ds<false>,
+               : (const void*)ds::step2d_ds_fused<false>,
       dim == 1 ? (const void*)step_kernel<float, 1, false, 32, 16>
-               : (const void*)ds::step2d_ds<false>};
+               : (const void*)ds::step2d_ds_fused<false>};
   for (const void* fn : fns) {
     cudaFuncAttributes at;
     cudaError_t e = cudaFuncGetAttributes(&at, fn);
