@@ -513,7 +513,7 @@ def run_batch2d(args):
     planar Riemann jumps with the served requests' states: left (1, 0, 1),
     pressure ratio log-uniform 2..100, density ratio 1..10, end time
     0.05..0.25; transmissive x, reflecting y; FP32) solved to their end
-    times, once as one lbm_batch2d (three launches per lattice step for the
+    times, once as one lbm_batch2d (two launches per lattice step for the
     whole batch) and once grid by grid through lbm_step on one stream (the
     one-solve-at-a-time path).  Both timed with CUDA events, creation and
     initial states excluded."""
@@ -568,7 +568,7 @@ def run_batch2d(args):
             "one_at_a_time": {"value": nu / t_alone, "s": round(t_alone, 4),
                               "solves_per_s": count / t_alone},
             "speedup": round(t_alone / t_batch, 3),
-            "gpu_launches": 3 * steps_batch}
+            "gpu_launches": DS_LAUNCHES_PER_STEP * steps_batch}
 
 
 PATCH_N = 4096

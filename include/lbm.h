@@ -268,11 +268,10 @@ void lbm_batch_destroy(lbm_batch* b);
  *
  * Many independent square-lattice grids (Section IV.B; each with its own
  * size, boundaries, time step, initial state and step count) advanced
- * together in FP32: a lattice step is three launches for the whole batch --
- * the deposit kernel over the tiles of every grid that still has steps to
- * take, the mixed-window kernel over one queue of the batch's mixed tiles,
- * and the finalize kernel (each grid's totals and reach) -- instead of three
- * per grid.  Each grid's step is the step lbm_step takes on a handle of the
+ * together in FP32: a lattice step is two launches for the whole batch --
+ * the persistent deposit kernel over the tiles of every grid that still has
+ * steps to take, and the finalize kernel (each grid's totals and reach) --
+ * instead of two per grid.  Each grid's step is the step lbm_step takes on a handle of the
  * grid's configuration (same kernels and arithmetic), so every grid's
  * result equals that handle's bit for bit.
  */

@@ -1,15 +1,14 @@
 // Batched small 2-D grids: many independent square-lattice grids advanced
-// together by the deposit kernels (step_ds.cuh), three launches per lattice
-// step for the whole batch instead of three per grid.  Contract:
+// together by the deposit kernel (step_ds.cuh), two launches per lattice
+// step for the whole batch instead of two per grid.  Contract:
 // include/lbm.h.
 //
 // Each grid is an ordinary FP32 square-lattice handle (its own buffers,
 // per-tile records, partial totals and scratch); the batch adds a table of
-// the grids' step arguments for both state parities, the first tile of each
-// grid in one batch-wide tile numbering, and one queue of mixed-window
-// tiles.  A block of the first kernel finds its grid from the tile number;
-// the mixed-window kernel's persistent blocks take tiles of any grid from
-// the shared queue; the finalize kernel runs FIN_BLOCKS blocks per grid.
+// the grids' step arguments for both state parities and the first tile of
+// each grid in one batch-wide tile numbering.  The persistent deposit
+// kernel's blocks take batch tiles by ticket and find each tile's grid from
+// its number; the finalize kernel runs FIN_BLOCKS blocks per grid.
 // A grid that has taken its steps is left as it is.  Every grid's tiles do
 // exactly what lbm_step does on that grid's handle, so its results are the
 // same bit for bit.
@@ -33,8 +32,7 @@ struct B2Args {
   const int* cons_every;    // [ngrids]
   int ngrids;
   long long step;           // the batch step this launch takes
-  unsigned* q;              // [2]: tiles queued, tiles taken
-  int* ql;                  // queued batch tile numbers
+  unsigned* q;              // [2]: unused, tiles taken
 };
 
 // Largest g with tile_base[g] <= item.
@@ -75,25 +73,12 @@ __device__ __forceinline__ const StepArgs& grid_args(const B2Args& B, int g,
   return a;
 }
 
+// The whole batch step in one persistent kernel: blocks take batch tiles by
+// ticket (the next one taken ahead) and finish each in the same block, the
+// one-type walk first and the group walks when the window is mixed.
 template <bool KAHAN>
-__global__ void __launch_bounds__(ds::NTHR, 2) b2_first(const B2Args B) {
-  extern __shared__ __align__(16) float4 dsm[];
-  __shared__ int red[ds::NGSTAT * ds::NWARP];
-  __shared__ ds::TileRed tred;
-  const ds::DsSmem sm{dsm, dsm + ds::PLANE,
-                      reinterpret_cast<float*>(dsm + 2 * ds::PLANE), red,
-                      &tred};
-  __shared__ __align__(16) unsigned raw[sizeof(StepArgs) / sizeof(unsigned)];
-  const int item = blockIdx.x;
-  const int g = grid_of(B.tile_base, B.ngrids, item);
-  if (!grid_active(B, g)) return;
-  const StepArgs& a = grid_args(B, g, raw);
-  ds::ds_first_tile<KAHAN>(a, item - __ldg(B.tile_base + g), item, B.q, B.ql,
-                           sm);
-}
-
-template <bool KAHAN>
-__global__ void __launch_bounds__(ds::NTHR, 2) b2_mixed(const B2Args B) {
+__global__ void __launch_bounds__(ds::NTHR, 2) b2_fused(const B2Args B,
+                                                        int total) {
   extern __shared__ __align__(16) float4 dsm[];
   __shared__ int red[ds::NGSTAT * ds::NWARP];
   __shared__ ds::TileRed tred;
@@ -102,19 +87,21 @@ __global__ void __launch_bounds__(ds::NTHR, 2) b2_mixed(const B2Args B) {
   const ds::DsSmem sm{dsm, dsm + ds::PLANE,
                       reinterpret_cast<float*>(dsm + 2 * ds::PLANE), red,
                       &tred};
-  const int nq = (int)B.q[0];
+  if (threadIdx.x == 0) s_k = (int)atomicAdd(&B.q[1], 1u);
   while (true) {
+    __syncthreads();
+    const int item = s_k;
+    __syncthreads();
+    if (item >= total) break;
     if (threadIdx.x == 0) s_k = (int)atomicAdd(&B.q[1], 1u);
-    __syncthreads();
-    const int k = s_k;
-    __syncthreads();
-    if (k >= nq) break;
-    const int item = B.ql[k];
     const int g = grid_of(B.tile_base, B.ngrids, item);
-    // (only grids that take this step queue tiles)
+    if (!grid_active(B, g)) continue;
     const StepArgs& a = grid_args(B, g, raw);
-    ds::ds_mixed_tile<KAHAN>(a, item - __ldg(B.tile_base + g), sm);
-    __syncthreads();  // the next tile reuses the deposits and the ring
+    const int b = item - __ldg(B.tile_base + g);
+    if (ds::ds_first_tile<KAHAN>(a, b, item, nullptr, nullptr, sm)) {
+      __syncthreads();  // the walk's deposits and record are settled
+      ds::ds_mixed_tile<KAHAN>(a, b, sm);
+    }
   }
 }
 
@@ -146,7 +133,6 @@ struct lbm_batch2d {
   long long* d_nsteps = nullptr;
   int* d_every = nullptr;
   unsigned* d_q = nullptr;
-  int* d_ql = nullptr;
   bool broken = false;
   std::string err;
 };
@@ -174,7 +160,6 @@ void b2free(lbm_batch2d* b) {
   cudaFree(b->d_nsteps);
   cudaFree(b->d_every);
   cudaFree(b->d_q);
-  cudaFree(b->d_ql);
   for (lbm_handle* h : b->h) lbm_destroy(h);
   b->h.clear();
 }
@@ -237,11 +222,8 @@ lbm_status lbm_batch2d_create(const lbm_grid2d* grids, int32_t count,
   up(reinterpret_cast<void**>(&b->d_every), every.data(), sizeof(int) * every.size());
   const unsigned zero[2] = {0u, 0u};
   up(reinterpret_cast<void**>(&b->d_q), zero, sizeof(zero));
-  if (e == cudaSuccess)
-    e = cudaMalloc(&b->d_ql, sizeof(int) * (size_t)std::max(1, b->total_tiles));
   const int smem = (int)ds::smem_bytes();
-  const void* fns[4] = {(const void*)b2_first<false>, (const void*)b2_first<true>,
-                        (const void*)b2_mixed<false>, (const void*)b2_mixed<true>};
+  const void* fns[2] = {(const void*)b2_fused<false>, (const void*)b2_fused<true>};
   for (const void* fn : fns)
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -263,21 +245,18 @@ lbm_status lbm_batch2d_run(lbm_batch2d* b, int64_t max_steps) {
   if (max_steps >= 0 && max_steps < todo) todo = max_steps;
   if (todo <= 0) return LBM_OK;
   B2Args B{b->d_args, b->d_base, b->d_nsteps, b->d_every, (int)b->h.size(),
-           0, b->d_q, b->d_ql};
+           0, b->d_q};
   const size_t smem = ds::smem_bytes();
-  int nmix = 2 * device_sm_count();
-  if (nmix > b->total_tiles) nmix = b->total_tiles;
+  int nb = 2 * device_sm_count();
+  if (nb > b->total_tiles) nb = b->total_tiles;
   const unsigned nfin = (unsigned)(ds::FIN_BLOCKS * b->h.size());
   const long long s0 = b->step;
   for (long long s = 0; s < todo; ++s) {
     B.step = s0 + s;
-    if (b->kahan) {
-      b2_first<true><<<(unsigned)b->total_tiles, ds::NTHR, smem, b->stream>>>(B);
-      b2_mixed<true><<<(unsigned)nmix, ds::NTHR, smem, b->stream>>>(B);
-    } else {
-      b2_first<false><<<(unsigned)b->total_tiles, ds::NTHR, smem, b->stream>>>(B);
-      b2_mixed<false><<<(unsigned)nmix, ds::NTHR, smem, b->stream>>>(B);
-    }
+    if (b->kahan)
+      b2_fused<true><<<(unsigned)nb, ds::NTHR, smem, b->stream>>>(B, b->total_tiles);
+    else
+      b2_fused<false><<<(unsigned)nb, ds::NTHR, smem, b->stream>>>(B, b->total_tiles);
     b2_finalize<<<nfin, ds::NTHR, 0, b->stream>>>(B);
   }
   const cudaError_t e = cudaGetLastError();

@@ -20,9 +20,10 @@
 // and data that vary along x only stay so bit for bit (their y-momentum
 // arrivals from rows +-c cancel exactly).
 //
-// Layout: one block per tile.  The block's window is 59 x 48 sources
-// (WCOLS x WROWS); with the step's reach R the tile is the window minus R on
-// every side, (59 - 2R) x (48 - 2R) destinations.
+// Layout: persistent blocks take tiles by ticket, one at a time.  A block's
+// window is 59 x 48 sources (WCOLS x WROWS); with the step's reach R the
+// tile is the window minus R on every side, (59 - 2R) x (48 - 2R)
+// destinations.
 //  * Phase 1 (window).  Thread (lane, wx, g) owns window column
 //    lane + 28 wx (the two warps of a row overlap by four columns; column 59
 //    holds deposits only) and walks the rows of group g (12 deposit rows,
@@ -39,18 +40,18 @@
 //    (+x, -x, +y, -y packets), and writes the new moments; then the new
 //    node's reach and the block's compensated partial totals.
 // The window's sources are all of one type in most tiles early in a flow:
-// the first kernel deposits for the type of the tile's central node and
-// checks that every source had that type.  Otherwise the tile goes to the
-// second kernel, which groups the sources by c1 and by blocks of SX x SY
+// the one-type walk deposits for the type of the tile's central node and
+// checks that every source had that type.  Otherwise the tile goes on to
+// the group walks, which group the sources by c1 and by blocks of SX x SY
 // lattice shifts (SX, SY up to 4, from the spread of n over the window):
 // n in {a .. a+SX-1} x {b .. b+SY-1}.  Relative to the base (a, b) such a
 // source lands at s + dn + k, dn in {0 .. SX-1} x {0 .. SY-1}, so the
 // deposit weights become hat functions over SX + 1 and SY + 1 offsets (one
-// walk per group),
-// and the gather is the one-type gather at shift (a, b).  Groups are done in
-// ascending order, each adding its arrivals to the destinations.  The
-// smallest c1 and shift of a window are taken from the tile's previous step
-// and checked during its first walk (redone when a source lies below them).
+// walk per group), and the gather is the one-type gather at shift (a, b).
+// Groups are done in ascending order, each adding its arrivals to the
+// destinations.  The smallest c1 and shift of a window and its block are
+// taken from the tile's previous step and checked during its first walk
+// (redone when the block does not hold the window).
 #pragma once
 
 #include <cstdint>

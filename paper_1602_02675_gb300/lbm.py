@@ -418,7 +418,7 @@ def make_grid2d(cfg, inner, outer, geom=PLANAR_X, a0=0.5, a1=0.5,
 
 class Batch2D:
     """Many independent small 2-D grids advanced together (lbm_batch2d_*):
-    three launches per lattice step for the whole batch."""
+    two launches per lattice step for the whole batch."""
 
     def __init__(self, grids, stream=None):
         lib = load()

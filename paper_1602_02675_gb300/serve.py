@@ -9,7 +9,7 @@ Section V.C) arrive over time.  Every tick the server
 2. advances every admitted solve by up to ``steps_per_tick`` steps: all 1-D
    tubes together with one ``lbm_pool_run`` call (a launch per step); the
    FP32 2-D grids admitted in the same round together as one batch
-   (``lbm_batch2d_run``: three launches per lattice step for the whole
+   (``lbm_batch2d_run``: two launches per lattice step for the whole
    batch), each batch and each FP64 grid (``lbm_step``) on its own CUDA
    stream, so their kernels overlap on the device;
 3. retires the solves that reached their step count, reading their moments
