@@ -28,10 +28,8 @@ struct lbm_handle {
   // FP64 square lattice: source records of the state being stepped,
   // rewritten before every step.
   void* src = nullptr;
-  // FP32 square lattice: per-tile window records and the mixed-tile queue
-  // of the deposit kernel.
+  // FP32 square lattice: per-tile window records of the deposit kernel.
   unsigned* hint = nullptr;
-  int* mixed_list = nullptr;
   Scratch* scr = nullptr;
   double* part = nullptr;
   int part_cap = 0;
@@ -122,7 +120,7 @@ namespace lbm {
 
 bool handle_ds_args(lbm_handle* h, int parity, StepArgs* a) {
   if (!h || h->broken || h->dim != 2 || h->f64 || h->r_cap > ds_rmax() ||
-      !h->hint || !h->mixed_list)
+      !h->hint)
     return false;
   a->nx = h->nx;
   a->ny = h->ny;
@@ -138,7 +136,6 @@ bool handle_ds_args(lbm_handle* h, int parity, StepArgs* a) {
   a->part = h->part;
   a->src = nullptr;
   a->hint = h->hint;
-  a->mixed_list = h->mixed_list;
   for (int f = 0; f < 4; ++f) {
     a->in[f] = h->buf[parity][f];
     a->out[f] = h->buf[parity ^ 1][f];
@@ -243,8 +240,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
          cudaSuccess;
   const int dst = (c.dim == 2 && !h->f64) ? ds_tiles(h->nx, h->ny, h->r_cap) : 0;
   if (ok && dst > 0) {
-    ok = cudaMalloc(&h->hint, sizeof(unsigned) * (size_t)dst) == cudaSuccess &&
-         cudaMalloc(&h->mixed_list, sizeof(int) * (size_t)dst) == cudaSuccess;
+    ok = cudaMalloc(&h->hint, sizeof(unsigned) * (size_t)dst) == cudaSuccess;
     if (ok)
       ok = cudaMemsetAsync(h->hint, 0, sizeof(unsigned) * (size_t)dst,
                            h->stream) == cudaSuccess;
@@ -373,7 +369,6 @@ lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
   a.part = h->part;
   a.src = h->src;
   a.hint = h->hint;
-  a.mixed_list = h->mixed_list;
   for (int64_t s = 0; s < nsteps; ++s) {
     for (int f = 0; f < 4; ++f) {
       a.in[f] = h->buf[h->cur][f];
@@ -502,7 +497,6 @@ void lbm_destroy(lbm_handle* h) {
       if (h->buf[b][f]) cudaFree(h->buf[b][f]);
   if (h->src) cudaFree(h->src);
   if (h->hint) cudaFree(h->hint);
-  if (h->mixed_list) cudaFree(h->mixed_list);
   if (h->scr) cudaFree(h->scr);
   if (h->part) cudaFree(h->part);
   if (h->staging) cudaFree(h->staging);

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(ds::NTHR, 2) b2_fused(const B2Args B,
     if (!grid_active(B, g)) continue;
     const StepArgs& a = grid_args(B, g, raw);
     const int b = item - __ldg(B.tile_base + g);
-    if (ds::ds_first_tile<KAHAN>(a, b, item, nullptr, nullptr, sm)) {
+    if (ds::ds_first_tile<KAHAN>(a, b, sm)) {
       __syncthreads();  // the walk's deposits and record are settled
       ds::ds_mixed_tile<KAHAN>(a, b, sm);
     }

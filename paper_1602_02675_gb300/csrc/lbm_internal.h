@@ -20,8 +20,8 @@ struct Scratch {
   unsigned ticket;         // blocks finished in the running launch
   unsigned long long eclamps;  // nodes whose e < 0 was clamped to 0
   double cons[4];          // FP64 totals (lattice units) of the last sum
-  unsigned mixed_n;        // FP32 square lattice: tiles queued for the
-  unsigned mixed_ticket;   // mixed-window kernel, and taken by it
+  unsigned spare_;
+  unsigned mixed_ticket;   // FP32 square lattice: tiles taken this step
 };
 
 // Constants of the equilibrium (Section III.B) for one lattice and gas.
@@ -59,11 +59,9 @@ struct StepArgs {
   double* part;       // [nblocks * 4] FP64 partial sums
   // FP32 square lattice (deposit kernel): per tile, the record of its
   // window at the last step (0: one type; else the window's smallest c1 and
-  // shift and its group block, a starting guess only), and the queue of
-  // tiles the mixed-window kernel takes; both sized for the tiles of the
-  // largest reach.
+  // shift and its group block, a starting guess only), sized for the tiles
+  // of the largest reach.
   unsigned* hint = nullptr;
-  int* mixed_list = nullptr;
   // FP64 square lattice: source records of the input state over the grid
   // padded by r_cap (layout in step_kernel.cuh), written by the launcher's
   // records pass before each step, or null.

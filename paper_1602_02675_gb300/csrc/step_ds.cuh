@@ -615,7 +615,7 @@ __device__ __forceinline__ unsigned rec_of(const GStats& st) {
   return rec_encode(st.c1min, st.nxmin, st.nymin, block_of(st));
 }
 
-// Statistics walk of a queued tile without a usable record: c1 and shifts
+// Statistics walk of a mixed tile without a usable record: c1 and shifts
 // of every window source and the clamped energies of the owned nodes,
 // without deposits.
 template <bool INT>
@@ -1139,12 +1139,6 @@ __device__ __forceinline__ void commit_clamps(const StepArgs& a, unsigned c) {
     atomicAdd(&a.scr->eclamps, (unsigned long long)cl);
 }
 
-// The step, first kernel: one block per tile of the reach the step runs
-// with (the grid holds the tiles of the largest reach; blocks beyond the
-// step's count only clear their partial totals).  A tile whose window
-// holds one type is done here; a tile whose window held several types at
-// the last step, or turns out to hold several now, is queued for the
-// mixed-window kernel and left to it.
 // Shared memory of a deposit block: the two deposit planes and the source
 // ring (dynamic), the statistics and totals scratch (static).
 struct DsSmem {
@@ -1154,13 +1148,14 @@ struct DsSmem {
   int* red;
   TileRed* tred;
 };
-// Tile b of the grid a describes, if its window holds one type; returns
-// true when the tile is left for the mixed-window path (then queued as
-// `item` in the queue of count qn and list ql, when ql is given).
+// Tile b of the grid a describes (the tiles of the largest reach are
+// numbered; those beyond the step's count only clear their partial totals),
+// if its window holds one type; returns true when the tile is left for the
+// group walks (ds_mixed_tile): its window held several types at the last
+// step, or turns out to hold several now.
 template <bool KAHAN>
 __device__ __forceinline__ bool ds_first_tile(const StepArgs& a, int b,
-                                              int item, unsigned* qn,
-                                              int* ql, const DsSmem& sm) {
+                                              const DsSmem& sm) {
   float4* D1 = sm.D1;
   float4* D2 = sm.D2;
   float* rbase = sm.rbase;
@@ -1173,13 +1168,7 @@ __device__ __forceinline__ bool ds_first_tile(const StepArgs& a, int b,
           make_float2(0.f, 0.f);
     return false;
   }
-  auto enqueue = [&]() {
-    if (ql && tid == 0) ql[atomicAdd(qn, 1u)] = item;
-  };
-  if (a.hint[b]) {
-    enqueue();
-    return true;
-  }
+  if (a.hint[b]) return true;
   const int R = g.R, TX = g.TX, TY = g.TY;
   const int ty_i = b / g.tiles_x, tx_i = b - ty_i * g.tiles_x;
   const int x0 = tx_i * TX, y0 = ty_i * TY;
@@ -1209,10 +1198,8 @@ __device__ __forceinline__ bool ds_first_tile(const StepArgs& a, int b,
   const bool other = __syncthreads_or(fl.other) != 0;
   const bool none = T0 == kNoType;
   if (other) {
-    // the mixed-window kernel finds the window's minima and counts its
-    // clamps
+    // the group walks find the window's minima and count its clamps
     if (tid == 0) a.hint[b] = kRecUnknown;
-    enqueue();
     return true;
   }
   commit_clamps(a, fl.clamps);
@@ -1231,26 +1218,15 @@ __device__ __forceinline__ bool ds_first_tile(const StepArgs& a, int b,
   tile_publish(a, b, to, *sm.tred);
   return false;
 }
-template <bool KAHAN>
-__global__ void __launch_bounds__(NTHR, 2) step2d_ds(const StepArgs a) {
-  extern __shared__ __align__(16) float4 dsm[];
-  __shared__ int red[NGSTAT * NWARP];
-  __shared__ TileRed tred;
-  const DsSmem sm{dsm, dsm + PLANE, reinterpret_cast<float*>(dsm + 2 * PLANE),
-                  red, &tred};
-  ds_first_tile<KAHAN>(a, blockIdx.x, blockIdx.x, &a.scr->mixed_n,
-                       a.mixed_list, sm);
-}
 
-// The step, second kernel: persistent blocks take the tiles the first
-// kernel queued, one at a time.  A tile's sources are grouped by c1 and by
-// shift blocks (c1 relative to the window's smallest, n relative to the
-// smallest shift in blocks of S per axis); one group walk per group, in
-// ascending group order, each gather adding its arrivals.  The minima and S
-// come from the tile's record of the previous step (or this step's first
-// kernel); when the first walk finds a source below them, the walks restart
-// from the true minima.  What a tile computes depends only on the state and
-// on the minima and S it ends with, not on the queue order.
+// Tile b whose window holds several types: its sources are grouped by c1
+// and by shift blocks (c1 relative to the window's smallest, n relative to
+// the smallest shift in blocks of SX x SY); one group walk per group, in
+// ascending group order, each gather adding its arrivals.  The minima and
+// block come from the tile's record of the previous step; when the first
+// walk finds that the block does not hold the window, the walks restart
+// from the window's own minima and block.  What a tile computes depends
+// only on the state.
 template <bool KAHAN>
 __device__ __forceinline__ void ds_mixed_tile(const StepArgs& a, int b,
                                               const DsSmem& sm) {
@@ -1371,25 +1347,6 @@ __device__ __forceinline__ void ds_mixed_tile(const StepArgs& a, int b,
     }
   }
 }
-template <bool KAHAN>
-__global__ void __launch_bounds__(NTHR, 2) step2d_ds_mixed(const StepArgs a) {
-  extern __shared__ __align__(16) float4 dsm[];
-  __shared__ int red[NGSTAT * NWARP];
-  __shared__ TileRed tred;
-  __shared__ int s_k;
-  const DsSmem sm{dsm, dsm + PLANE, reinterpret_cast<float*>(dsm + 2 * PLANE),
-                  red, &tred};
-  const int nq = (int)a.scr->mixed_n;
-  while (true) {
-    if (threadIdx.x == 0) s_k = (int)atomicAdd(&a.scr->mixed_ticket, 1u);
-    __syncthreads();
-    const int k = s_k;
-    __syncthreads();
-    if (k >= nq) break;
-    ds_mixed_tile<KAHAN>(a, a.mixed_list[k], sm);
-    __syncthreads();  // the next tile reuses the deposits and the ring
-  }
-}
 
 // The step in one persistent kernel: blocks take tiles by ticket (all the
 // tiles of the largest reach); a tile whose window held several types at
@@ -1413,7 +1370,7 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds_fused(const StepArgs a) {
     if (k >= a.nblocks) break;
     // the next ticket, taken now: its latency hides behind this tile
     if (threadIdx.x == 0) s_k = (int)atomicAdd(&a.scr->mixed_ticket, 1u);
-    if (ds_first_tile<KAHAN>(a, k, k, nullptr, nullptr, sm)) {
+    if (ds_first_tile<KAHAN>(a, k, sm)) {
       __syncthreads();  // the walk's deposits and record are settled
       ds_mixed_tile<KAHAN>(a, k, sm);
     }
@@ -1501,7 +1458,6 @@ __device__ __forceinline__ void ds_finalize_part(Scratch* scr,
     if (!(scr->flags & kFlagReach)) scr->reach = scr->reach_next;
     scr->reach_next = 0;
     scr->ticket = 0u;
-    scr->mixed_n = 0u;
     scr->mixed_ticket = 0u;
   }
 }
