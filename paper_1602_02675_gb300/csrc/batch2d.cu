@@ -82,18 +82,17 @@ __global__ void __launch_bounds__(ds::NTHR, 2) b2_fused(const B2Args B,
   extern __shared__ __align__(16) float4 dsm[];
   __shared__ int red[ds::NGSTAT * ds::NWARP];
   __shared__ ds::TileRed tred;
-  __shared__ int s_k;
+  __shared__ int s_k[2];
   __shared__ __align__(16) unsigned raw[sizeof(StepArgs) / sizeof(unsigned)];
   const ds::DsSmem sm{dsm, dsm + ds::PLANE,
                       reinterpret_cast<float*>(dsm + 2 * ds::PLANE), red,
                       &tred};
-  if (threadIdx.x == 0) s_k = (int)atomicAdd(&B.q[1], 1u);
-  while (true) {
-    __syncthreads();
-    const int item = s_k;
-    __syncthreads();
+  if (threadIdx.x == 0) s_k[0] = (int)atomicAdd(&B.q[1], 1u);
+  for (int it = 0;; ++it) {
+    __syncthreads();  // the ticket is visible; the last tile is done
+    const int item = s_k[it & 1];
     if (item >= total) break;
-    if (threadIdx.x == 0) s_k = (int)atomicAdd(&B.q[1], 1u);
+    if (threadIdx.x == 0) s_k[(it + 1) & 1] = (int)atomicAdd(&B.q[1], 1u);
     const int g = grid_of(B.tile_base, B.ngrids, item);
     if (!grid_active(B, g)) continue;
     const StepArgs& a = grid_args(B, g, raw);

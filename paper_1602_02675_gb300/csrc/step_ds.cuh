@@ -1359,17 +1359,18 @@ __global__ void __launch_bounds__(NTHR, 2) step2d_ds_fused(const StepArgs a) {
   extern __shared__ __align__(16) float4 dsm[];
   __shared__ int red[NGSTAT * NWARP];
   __shared__ TileRed tred;
-  __shared__ int s_k;
+  __shared__ int s_k[2];
   const DsSmem sm{dsm, dsm + PLANE, reinterpret_cast<float*>(dsm + 2 * PLANE),
                   red, &tred};
-  if (threadIdx.x == 0) s_k = (int)atomicAdd(&a.scr->mixed_ticket, 1u);
-  while (true) {
-    __syncthreads();
-    const int k = s_k;
-    __syncthreads();
+  if (threadIdx.x == 0) s_k[0] = (int)atomicAdd(&a.scr->mixed_ticket, 1u);
+  for (int it = 0;; ++it) {
+    __syncthreads();  // the ticket is visible; the last tile is done
+    const int k = s_k[it & 1];
     if (k >= a.nblocks) break;
-    // the next ticket, taken now: its latency hides behind this tile
-    if (threadIdx.x == 0) s_k = (int)atomicAdd(&a.scr->mixed_ticket, 1u);
+    // the next ticket, taken now into the other slot: its latency hides
+    // behind this tile
+    if (threadIdx.x == 0)
+      s_k[(it + 1) & 1] = (int)atomicAdd(&a.scr->mixed_ticket, 1u);
     if (ds_first_tile<KAHAN>(a, k, sm)) {
       __syncthreads();  // the walk's deposits and record are settled
       ds_mixed_tile<KAHAN>(a, k, sm);
