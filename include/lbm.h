@@ -289,8 +289,9 @@ typedef struct {
 
 /* Create a batch of count grids (device memory for each, initial states,
    first reach), all on `stream`.  LBM_EINVAL for a grid the deposit kernel
-   does not take (1-D, FP64, a reach limit above 6) or a negative step
-   count.  Grids keep the caller's indices.  Synchronous. */
+   does not take (1-D, FP64, a reach limit above 6), a negative step count,
+   or grids that differ in cfg.kahan (one summation form per batch).  Grids
+   keep the caller's indices.  Synchronous. */
 lbm_status lbm_batch2d_create(const lbm_grid2d* grids, int32_t count,
                               void* stream, lbm_batch2d** out);
 
