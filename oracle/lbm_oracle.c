@@ -1,7 +1,9 @@
 /*
  * Plain FP64 CPU oracle of the tau = 1 semi-discrete lattice Boltzmann step
  * (Komeili, Mirzaei, Shabouei, "Performance of 1-D and 2-D Lattice Boltzmann
- * (LB) in Solution of the Shock Tube Problem").
+ * (LB) in Solution of the Shock Tube Problem"), and, at the end of the file,
+ * of the step with a general relaxation time tau (eqs 4-5) on a per-packet
+ * state.
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
  * statement of what the GPU path computes.  Only the tests, the smoke check
@@ -429,4 +431,294 @@ int ora_packets_probe(const ora_params* P, double rho, double mx, double my,
     out[6 * p + 5] = d * (0.5 * (cbx * cbx + cby * cby) + q.phi);
   }
   return np;
+}
+
+/* ==========================================================================
+ * General relaxation time tau (eqs 4-5) with per-packet storage.
+ *
+ * With tau != 1 the distribution no longer collapses to its equilibrium, so
+ * a node's state is the set of packets it holds: one slot j per entry of
+ * the velocity set (1-D: 5 slots, 2-D: 8 slots, in the table order of
+ * ora_packets), each slot carrying mass, momentum and energy (the integrand
+ * eta f of eq 6 summed over one migrating velocity).  Fields per slot:
+ * NF = dim + 2, i.e. (mass, m_x, energy) in 1-D and (mass, m_x, m_y, energy)
+ * in 2-D.  Array layout: f[(j * NF + c) * N + i], node i x fastest.
+ *
+ * One step, per node:
+ *   Y = sum_j f_j (eq 6), slots in table order;
+ *   f_eq_j from Y exactly as in the tau = 1 step (Section III.B);
+ *   collision (eqs 4-5): f*_j = f_j - (f_j - f_eq_j)/tau, evaluated as the
+ *     blend (1 - 1/tau) f_j + (1/tau) f_eq_j, which at tau = 1 is f_eq_j
+ *     exactly (eq 10);
+ *   migration: slot j moves with the node's migrating velocity V + c'_j of
+ *     the same table entry (c' from the node's own c1, eq 26) and splits over
+ *     the nodes s + n + c'_j + k with the weights of eqs 28-29;
+ *   every destination's slot j is the sum of the slot-j arrivals.
+ * Per destination and slot the arrivals are added in ascending source order
+ * (y-major, x fastest), then corner order.  New slot contents are a
+ * function of the arrivals alone, so conservation of sum_j f_j over the
+ * domain follows from sum_j f*_j = Y.
+ *
+ * Additional points (Section V.B) hold the supplying node's packets:
+ * transmissive and periodic copy them; a reflecting wall mirrors them: the
+ * slot whose c' points the other way along the wall normal, with the normal
+ * momentum negated.  The additional point's moments are the supplying
+ * node's with that component negated (not re-summed in mirrored order), so
+ * its packets and equilibrium are the exact mirror images.
+ * ========================================================================== */
+
+static int ora_slots(const ora_params* P) { return P->dim == 1 ? 5 : 8; }
+
+/* Slot of the mirrored packet across a wall normal to `axis`. */
+static int ora_mirror_slot(int dim, int axis, int j) {
+  if (dim == 1) {
+    if (j == 0) return 0;
+    return (j % 2 == 1) ? j + 1 : j - 1; /* +c1 <-> -c1, +c2 <-> -c2 */
+  }
+  const int dir = j & 3; /* 0: +x, 1: -x, 2: +y, 3: -y */
+  if (axis == 0 && dir < 2) return j ^ 1;
+  if (axis == 1 && dir >= 2) return j ^ 1;
+  return j;
+}
+
+/* Moments of node i from its slots (eq 6), slots in table order. */
+static void ora_bgk_node_moments(const ora_params* P, const double* f,
+                                 int64_t N, int64_t i, double Y[4]) {
+  const int NF = P->dim + 2, NP = ora_slots(P);
+  double r = 0.0, x = 0.0, y = 0.0, e = 0.0;
+  for (int j = 0; j < NP; ++j) {
+    const double* s = f + (int64_t)j * NF * N;
+    r = r + s[0 * N + i];
+    x = x + s[1 * N + i];
+    if (P->dim == 2) y = y + s[2 * N + i];
+    e = e + s[(NF - 1) * N + i];
+  }
+  Y[0] = r;
+  Y[1] = x;
+  Y[2] = y;
+  Y[3] = e;
+}
+
+/* Equilibrium packet j of q as (mass, m_x, m_y, energy); zero if q emits
+   nothing. */
+static void ora_eq_packet(const ora_params* P, const ora_eq* q, int j,
+                          double out[4]) {
+  out[0] = out[1] = out[2] = out[3] = 0.0;
+  if (!q->emits) return;
+  ora_packet pk[8];
+  ora_packets(P, q, pk);
+  const double d = q->dlev[pk[j].lev];
+  const double cbx = q->V[0] + (double)pk[j].cx; /* eq 12 */
+  const double cby = q->V[1] + (double)pk[j].cy;
+  out[0] = d;                                            /* eq 31 */
+  out[1] = d * cbx;                                      /* eq 32 */
+  out[2] = (P->dim == 2) ? d * cby : 0.0;
+  out[3] = d * (0.5 * (cbx * cbx + cby * cby) + q->phi); /* eq 33 */
+}
+
+/* f = f_eq of the given moments at every node (the state a tau = 1 step
+   would migrate).  my may be NULL in 1-D. */
+int ora_bgk_equilibrium(const ora_params* P, const double* rho,
+                        const double* mx, const double* my,
+                        const double* rhoE, double* f) {
+  int st = ora_check_params(P);
+  if (st != ORA_OK) return st;
+  const int NF = P->dim + 2, NP = ora_slots(P);
+  const int64_t N = P->nx * P->ny;
+  for (int64_t i = 0; i < N; ++i) {
+    ora_eq q;
+    st = ora_equilibrium(P, rho[i], mx[i], P->dim == 2 ? my[i] : 0.0,
+                         rhoE[i], &q);
+    if (st != ORA_OK) return st;
+    for (int j = 0; j < NP; ++j) {
+      double pj[4];
+      ora_eq_packet(P, &q, j, pj);
+      double* s = f + (int64_t)j * NF * N;
+      s[0 * N + i] = pj[0];
+      s[1 * N + i] = pj[1];
+      if (P->dim == 2) s[2 * N + i] = pj[2];
+      s[(NF - 1) * N + i] = pj[3];
+    }
+  }
+  return ORA_OK;
+}
+
+/* Moments of every node from its slots (eq 6).  my may be NULL in 1-D. */
+int ora_bgk_moments(const ora_params* P, const double* f, double* rho,
+                    double* mx, double* my, double* rhoE) {
+  int st = ora_check_params(P);
+  if (st != ORA_OK) return st;
+  const int64_t N = P->nx * P->ny;
+  for (int64_t i = 0; i < N; ++i) {
+    double Y[4];
+    ora_bgk_node_moments(P, f, N, i, Y);
+    rho[i] = Y[0];
+    mx[i] = Y[1];
+    if (P->dim == 2) my[i] = Y[2];
+    rhoE[i] = Y[3];
+  }
+  return ORA_OK;
+}
+
+/* One source of the tau != 1 step: its equilibrium and its post-collision
+   packets (mass, m_x, m_y, energy per slot). */
+typedef struct {
+  ora_eq q;
+  double fs[8][4];
+} ora_bgk_src;
+
+/*
+ * One step with relaxation time tau (eqs 4-5) of the per-packet state f
+ * (layout above) into f_out.  eclamp_out (nullable): interior nodes whose
+ * e < 0 was clamped; reach_out (nullable): the reach R of the source window.
+ */
+int ora_bgk_step(const ora_params* P, double tau, const double* f,
+                 double* f_out, int64_t* eclamp_out, int64_t* reach_out) {
+  int st = ora_check_params(P);
+  if (st != ORA_OK) return st;
+  if (!(tau > 0.5) || !isfinite(tau)) return ORA_EINVAL;
+  const int dim = P->dim, NF = dim + 2, NP = ora_slots(P);
+  const int64_t nx = P->nx, ny = P->ny, N = nx * ny;
+  const double omega = 1.0 / tau;
+  const double keep = 1.0 - omega;
+
+  /* moments and equilibrium of every node, and the reach */
+  double* Y = (double*)malloc(sizeof(double) * 4 * (size_t)N);
+  ora_eq* nq = (ora_eq*)malloc(sizeof(ora_eq) * (size_t)N);
+  if (!Y || !nq) {
+    free(Y);
+    free(nq);
+    return ORA_EINVAL;
+  }
+  int64_t R = 0, eclamps = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    ora_bgk_node_moments(P, f, N, i, Y + 4 * i);
+    st = ora_equilibrium(P, Y[4 * i], Y[4 * i + 1], Y[4 * i + 2],
+                         Y[4 * i + 3], &nq[i]);
+    if (st != ORA_OK) {
+      free(Y);
+      free(nq);
+      return st;
+    }
+    eclamps += nq[i].eclamp;
+    const int64_t r = ora_node_reach(P, &nq[i]);
+    if (r > R) R = r;
+  }
+  if (reach_out) *reach_out = R;
+
+  /* every source coordinate within R of the domain: collision (eqs 4-5) */
+  const int64_t Ry = (dim == 2) ? R : 0;
+  const int64_t wx = nx + 2 * R, wy = ny + 2 * Ry;
+  ora_bgk_src* src =
+      (ora_bgk_src*)malloc(sizeof(ora_bgk_src) * (size_t)(wx * wy));
+  if (!src) {
+    free(Y);
+    free(nq);
+    return ORA_EINVAL;
+  }
+  for (int64_t sy = -Ry; sy < ny + Ry; ++sy) {
+    for (int64_t sx = -R; sx < nx + R; ++sx) {
+      double flx, fly = 1.0;
+      const int64_t gx = ora_virtual_axis(P->bc_x, nx, sx, &flx);
+      const int64_t gy = (dim == 2) ? ora_virtual_axis(P->bc_y, ny, sy, &fly)
+                                    : 0;
+      const int64_t g = gy * nx + gx;
+      ora_bgk_src* S = &src[(sy + Ry) * wx + (sx + R)];
+      /* the additional point's moments: the node's, normal momentum
+         negated across a reflecting wall */
+      const double* Yg = Y + 4 * g;
+      if (flx == 1.0 && fly == 1.0) {
+        S->q = nq[g];
+      } else {
+        st = ora_equilibrium(P, Yg[0], flx * Yg[1], fly * Yg[2], Yg[3],
+                             &S->q);
+        if (st != ORA_OK) {
+          free(Y);
+          free(nq);
+          free(src);
+          return st;
+        }
+      }
+      for (int j = 0; j < NP; ++j) {
+        /* the node's slot that this source's slot j mirrors */
+        int jg = j;
+        if (flx < 0.0) jg = ora_mirror_slot(dim, 0, jg);
+        if (fly < 0.0) jg = ora_mirror_slot(dim, 1, jg);
+        const double* s = f + (int64_t)jg * NF * N;
+        double fj[4];
+        fj[0] = s[0 * N + g];
+        fj[1] = flx * s[1 * N + g];
+        fj[2] = (dim == 2) ? fly * s[2 * N + g] : 0.0;
+        fj[3] = s[(NF - 1) * N + g];
+        double feq[4];
+        ora_eq_packet(P, &S->q, j, feq);
+        for (int c = 0; c < 4; ++c)
+          S->fs[j][c] = keep * fj[c] + omega * feq[c];
+      }
+    }
+  }
+
+  /* migration: each destination's slot j sums its slot-j arrivals,
+     sources ascending (y-major, x fastest), then corners */
+  const int nk = (dim == 1) ? 2 : 4;
+  for (int64_t dy = 0; dy < ny; ++dy) {
+    for (int64_t dx = 0; dx < nx; ++dx) {
+      const int64_t t = dy * nx + dx;
+      for (int j = 0; j < NP; ++j) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int64_t sy = dy - Ry; sy <= dy + Ry; ++sy) {
+          for (int64_t sx = dx - R; sx <= dx + R; ++sx) {
+            const ora_bgk_src* S = &src[(sy + Ry) * wx + (sx + R)];
+            const ora_eq* q = &S->q;
+            if (!q->emits) continue;
+            ora_packet pk[8];
+            ora_packets(P, q, pk);
+            const double wxk[2] = {1.0 - q->f[0], q->f[0]};
+            const double wyk[2] = {1.0 - q->f[1], q->f[1]};
+            for (int k = 0; k < nk; ++k) {
+              const int64_t kx = k & 1, ky = k >> 1;
+              if (sx + q->n[0] + pk[j].cx + kx != dx) continue;
+              if (dim == 2 && sy + q->n[1] + pk[j].cy + ky != dy) continue;
+              const double a = (dim == 1) ? wxk[kx] : wxk[kx] * wyk[ky];
+              for (int c = 0; c < 4; ++c) acc[c] = acc[c] + a * S->fs[j][c];
+            }
+          }
+        }
+        double* o = f_out + (int64_t)j * NF * N;
+        o[0 * N + t] = acc[0];
+        o[1 * N + t] = acc[1];
+        if (dim == 2) o[2 * N + t] = acc[2];
+        o[(NF - 1) * N + t] = acc[3];
+      }
+    }
+  }
+  free(src);
+  free(Y);
+  free(nq);
+  if (eclamp_out) *eclamp_out = eclamps;
+  return ORA_OK;
+}
+
+/* nsteps tau != 1 steps of f in place. */
+int ora_bgk_run(const ora_params* P, double tau, double* f, int64_t nsteps,
+                int64_t* eclamp_total) {
+  const int64_t N = P->nx * P->ny;
+  const size_t bytes = sizeof(double) * (size_t)((P->dim + 2) *
+                                                 ora_slots(P)) * (size_t)N;
+  double* buf = (double*)malloc(bytes);
+  if (!buf) return ORA_EINVAL;
+  int64_t total = 0;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    int64_t ec = 0;
+    const int st = ora_bgk_step(P, tau, f, buf, &ec, NULL);
+    if (st != ORA_OK) {
+      free(buf);
+      return st;
+    }
+    total += ec;
+    memcpy(f, buf, bytes);
+  }
+  free(buf);
+  if (eclamp_total) *eclamp_total = total;
+  return ORA_OK;
 }

@@ -8,7 +8,9 @@ the method that sit outside the step:
 * physical <-> lattice units (lattice velocity V = u*lambda, energies per unit
   mass scale with lambda^2, lambda = dt/dx);
 * the Sod / cylindrical Riemann initial states of Section V.C;
-* pressure recovery P = (gamma-1) rho e (eq 27).
+* pressure recovery P = (gamma-1) rho e (eq 27);
+* the per-packet state of the relaxation-time step (tau != 1, eqs 4-5):
+  equilibrium packets of given moments, moments of packets, steps.
 
 It shares no code with the CUDA library.
 """
@@ -67,8 +69,15 @@ def _load():
                                               ctypes.c_double, dp]
         lib.ora_packets_probe.argtypes = [pp, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, dp]
+        lib.ora_bgk_equilibrium.argtypes = [pp, dp, dp, dp, dp, dp]
+        lib.ora_bgk_moments.argtypes = [pp, dp, dp, dp, dp, dp]
+        lib.ora_bgk_step.argtypes = [pp, ctypes.c_double, dp, dp, i64p, i64p]
+        lib.ora_bgk_run.argtypes = [pp, ctypes.c_double, dp, ctypes.c_int64,
+                                    i64p]
         for f in (lib.ora_step, lib.ora_run, lib.ora_reach,
-                  lib.ora_equilibrium_probe, lib.ora_packets_probe):
+                  lib.ora_equilibrium_probe, lib.ora_packets_probe,
+                  lib.ora_bgk_equilibrium, lib.ora_bgk_moments,
+                  lib.ora_bgk_step, lib.ora_bgk_run):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -186,6 +195,79 @@ def packets(P: Params, rho, mx, my, rhoE) -> np.ndarray:
     p = P.c()
     n = lib.ora_packets_probe(ctypes.byref(p), rho, mx, my, rhoE, _dp(out))
     return out[:6 * n].reshape(n, 6)
+
+
+# ----------------------------------------------------------------------------
+# relaxation time tau != 1 (eqs 4-5): per-packet state
+# ----------------------------------------------------------------------------
+
+def slots(dim: int) -> int:
+    """Packet slots per node: the velocity set's entries (Section IV)."""
+    return 5 if dim == 1 else 8
+
+
+def packet_fields(dim: int) -> int:
+    """Fields per slot: mass, momentum per axis, energy."""
+    return dim + 2
+
+
+def bgk_equilibrium(P: Params, s: State) -> np.ndarray:
+    """Per-packet state at equilibrium with the moments s, shaped
+    (slots, fields, nodes)."""
+    lib = _load()
+    r, x, y, e = _arrays(P, s)
+    n = r.size
+    f = np.zeros((slots(P.dim), packet_fields(P.dim), n))
+    p = P.c()
+    st = lib.ora_bgk_equilibrium(ctypes.byref(p), _dp(r), _dp(x),
+                                 _dp(y) if P.dim == 2 else None, _dp(e),
+                                 _dp(f))
+    if st != 0:
+        raise OracleError(f"ora_bgk_equilibrium status {st}")
+    return f
+
+
+def bgk_moments(P: Params, f: np.ndarray) -> State:
+    """Moments of every node, the sum of its slots (eq 6)."""
+    lib = _load()
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    n = f.shape[-1]
+    r, x, e = (np.empty(n) for _ in range(3))
+    y = np.empty(n) if P.dim == 2 else None
+    p = P.c()
+    st = lib.ora_bgk_moments(ctypes.byref(p), _dp(f), _dp(r), _dp(x),
+                             _dp(y) if y is not None else None, _dp(e))
+    if st != 0:
+        raise OracleError(f"ora_bgk_moments status {st}")
+    return State(r, x, y, e)
+
+
+def bgk_step(P: Params, tau: float, f: np.ndarray):
+    """One step with relaxation time tau.  Returns (new f, e-clamp count,
+    reach used)."""
+    lib = _load()
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.empty_like(f)
+    ec, R = ctypes.c_int64(0), ctypes.c_int64(0)
+    p = P.c()
+    st = lib.ora_bgk_step(ctypes.byref(p), float(tau), _dp(f), _dp(out),
+                          ctypes.byref(ec), ctypes.byref(R))
+    if st != 0:
+        raise OracleError(f"ora_bgk_step status {st}")
+    return out, ec.value, R.value
+
+
+def bgk_run(P: Params, tau: float, f: np.ndarray, nsteps: int):
+    """nsteps steps with relaxation time tau; returns (f, e-clamp count)."""
+    lib = _load()
+    f = np.array(f, dtype=np.float64, order="C", copy=True)
+    ec = ctypes.c_int64(0)
+    p = P.c()
+    st = lib.ora_bgk_run(ctypes.byref(p), float(tau), _dp(f), int(nsteps),
+                         ctypes.byref(ec))
+    if st != 0:
+        raise OracleError(f"ora_bgk_run status {st}")
+    return f, ec.value
 
 
 # ----------------------------------------------------------------------------
