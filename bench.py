@@ -37,7 +37,8 @@ Other workloads (one JSON line each): --workload sod2d (the shock tube as
 the main line), sod1d (1-D Sod time to solution, plain and CUDA-graph),
 tubes (4096 batched 1-D tubes vs plain FP64 one at a time), serve
 (continuous batching: capacity and Poisson sweep vs plain FP64 one at a
-time).
+time), patch2d, batch2d, bgk2d (the relaxation-time step, tau != 1, on its
+per-packet state).
 
 --impl reference times the oracle alone (the CPU reference arm).
 Multi-GPU (torchrun): independent replicas, one per rank (weak scaling).
@@ -630,6 +631,73 @@ def run_patch2d(args):
             "clocks": clk}
 
 
+BGK_N = 2048
+
+
+def run_bgk2d(args):
+    """--workload bgk2d: the relaxation-time step (tau != 1, eqs 4-5) on
+    its per-packet state: the periodic cylinder of Section V.C on a 2048 x
+    2048 grid (circle r < 0.4 about the centre, inner (1, 0, 0, 1), outer
+    (0.125, 0, 0, 0.1)), tau = --tau, FP32.  K steps after W warm-up steps,
+    timed as one block with CUDA events around lbm_bgk_step (its collision
+    and gather kernels); the state, 537 MB per packet set, is larger than
+    L2.  Algorithmic bytes: 8 slots x 4 fields x 4 bytes read and written,
+    256 B per node update."""
+    import torch
+    from paper_1602_02675_gb300 import lbm as L
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.Stream()
+    n = BGK_N
+    K = args.steps if args.steps > 0 else 100
+    cfg = L.make_config(2, n, n, dt=1.0 / n, precision=L.F32,
+                        bc_x=L.PERIODIC, bc_y=L.PERIODIC,
+                        stream=stream.cuda_stream)
+    with L.Bgk(cfg, args.tau) as g, torch.cuda.stream(stream):
+        g.init_riemann((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1),
+                       L.CIRCLE, 0.5, 0.5, 0.4)
+        t0 = g.conservation()
+        g.step(args.warmup)
+        stream.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+        a.record(stream)
+        g.step(K)
+        b.record(stream)
+        stream.synchronize()
+        clk = clocks.stop()
+        ms = a.elapsed_time(b)
+        g.synchronize()
+        diag = g.diagnostics()
+        t1 = g.conservation()
+    mean_ms = ms / K
+    peak, peak_kind = load_peaks()
+    achieved = 256 * n * n / (mean_ms / 1e3) / 1e9
+    drift = [float(abs(x - y) / max(abs(t0[0]), abs(t0[3])))
+             for x, y in zip(t1, t0)]
+    return {"metric": METRIC, "value": n * n * K / (ms / 1e3),
+            "unit": "node-updates/s", "n_gpus": 1, "steps": K,
+            "warmup": args.warmup, "ms_per_step": round(mean_ms, 5),
+            "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic (cylindrical Riemann problem, Section V.C "
+                    "states)",
+            "config": {"workload": f"bgk_cylinder_2d_{n}x{n}_periodic",
+                       "tau": args.tau, "nx": n, "ny": n,
+                       "timed": f"steps {args.warmup + 1}-{args.warmup + K}",
+                       "l2": "state (537 MB per packet set) larger than L2; "
+                             "no flush"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1),
+                         "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4),
+                         "peak_kind": peak_kind,
+                         "bytes_per_node_update": 256,
+                         "duration": "CUDA events around lbm_bgk_step: the "
+                                     "collision and gather kernels"},
+            "gpu_launches": 2 * K,
+            "conservation_drift": drift,
+            "end_state": diag, "clocks": clk}
+
+
 # --------------------------------------------------------------------------
 # the oracle on the host: CPU baseline and reference arm
 # --------------------------------------------------------------------------
@@ -958,7 +1026,10 @@ def main():
     ap.add_argument("--precision-steps", type=int, default=100)
     ap.add_argument("--workload", default="cylinder2d",
                     choices=sorted(WORKLOADS) + ["tubes", "serve", "sod1d",
-                                                 "patch2d", "batch2d"])
+                                                 "patch2d", "batch2d",
+                                                 "bgk2d"])
+    ap.add_argument("--tau", type=float, default=1.5,
+                    help="bgk2d: relaxation time (eqs 4-5)")
     ap.add_argument("--repeats", type=int, default=100,
                     help="sod1d: solves timed")
     ap.add_argument("--requests", type=int, default=2000)
@@ -1001,6 +1072,9 @@ def main():
         return
     if args.workload == "batch2d":
         print(json.dumps(run_batch2d(args)))
+        return
+    if args.workload == "bgk2d":
+        print(json.dumps(run_bgk2d(args)))
         return
     if args.impl == "reference":
         line = run_reference(args, rank, world)

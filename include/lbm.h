@@ -357,6 +357,87 @@ const char* lbm_pool_last_error(const lbm_pool* p);
 
 void lbm_pool_destroy(lbm_pool* p);
 
+/* ---- general relaxation time tau (eqs 4-5) ------------------------------
+ *
+ * With tau != 1 the collision f*_j = f_j - (f_j - f_eq_j)/tau (eqs 4-5)
+ * keeps part of what arrived, so the state is per packet: every node holds
+ * one slot per entry of its velocity set (Section IV; 1-D: 5 slots in the
+ * order 0, +c1, -c1, +c2, -c2; 2-D: 8 slots +c1 x, -c1 x, +c1 y, -c1 y,
+ * then the same with c2), each slot carrying NF = dim + 2 fields: mass,
+ * momentum per axis, energy.  Per step and node: Y = sum_j f_j (eq 6), the
+ * equilibrium of Y as in the tau = 1 step (Section III.B), the collision,
+ * evaluated as (1 - 1/tau) f_j + (1/tau) f_eq_j (exactly eq 10 at tau = 1);
+ * slot j then migrates with the node's V + c'_j (the same landings and
+ * weights as at tau = 1, eqs 23, 28-29) into the same slot of the nodes it
+ * lands on, whose slot j is the sum of its arrivals (sources in ascending
+ * order, y-major, then corners).  Additional points (Section V.B) copy the
+ * supplying node's slots, or mirror them across a reflecting wall (slot of
+ * the opposite c' along the normal, normal momentum negated).  A node whose
+ * slot masses sum to 0 emits nothing.
+ *
+ * Packet arrays at the ABI: NP * NF arrays of n doubles, array j * NF + c
+ * for slot j and field c, nodes x fastest (NP * NF * n doubles in all),
+ * physical units (momentum = lattice momentum / lambda, energy = lattice
+ * energy / lambda^2).  Device memory per handle: two packet sets
+ * (NP * NF * n elements each), a moments buffer (4 fields), source records
+ * over the grid padded by max_reach (8 bytes plus NP * NF + 2 elements per
+ * padded node, rewritten every step), 5 n doubles of staging, scratch.
+ * Both precisions; kahan and cons_every are ignored.  Conventions of
+ * lbm_create otherwise (stream order, errors, not thread-safe). */
+typedef struct lbm_bgk lbm_bgk;
+
+/* Validate cfg and tau (tau > 0.5, finite) and allocate.  tau < 1
+   over-relaxes: packets may then carry negative mass, and a state far from
+   equilibrium next to a reflecting wall need not stay positive (reported as
+   LBM_ESTATE).  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_bgk_create(const lbm_config* cfg, double tau, lbm_bgk** out);
+
+/* Riemann initial state as lbm_init_riemann; the packets start at the
+   equilibrium of the moments.  Stream-ordered, does not wait. */
+lbm_status lbm_bgk_init_riemann(lbm_bgk* h, const lbm_prim* inner,
+                                const lbm_prim* outer, int32_t geom, double a0,
+                                double a1, double radius);
+
+/* Packets at the equilibrium of host conserved arrays (physical units, as
+   lbm_set_moments; my may be NULL in 1-D).  Waits for the copies. */
+lbm_status lbm_bgk_set_moments(lbm_bgk* h, const double* rho, const double* mx,
+                               const double* my, const double* rhoE,
+                               int64_t n);
+
+/* Set / read every node's packets (layout above, NP * NF * n doubles; n must
+   be nx * ny).  lbm_bgk_packets waits and reports device errors; with
+   lbm_bgk_set_packets it is checkpoint / restart of the tau != 1 state. */
+lbm_status lbm_bgk_set_packets(lbm_bgk* h, const double* f, int64_t n);
+lbm_status lbm_bgk_packets(lbm_bgk* h, double* f, int64_t n);
+
+/* Advance nsteps steps: per step a collision pass over the padded grid and
+   a gather pass over the nodes.  Stream-ordered, does not wait; LBM_ESTATE
+   and LBM_EREACH (the state is then left as it was) arrive at the next
+   waiting call. */
+lbm_status lbm_bgk_step(lbm_bgk* h, int64_t nsteps);
+
+/* Moments Y = sum_j f_j of every node, physical units, as lbm_moments
+   (p nullable).  Waits. */
+lbm_status lbm_bgk_moments(lbm_bgk* h, double* rho, double* mx, double* my,
+                           double* rhoE, double* p, int64_t n);
+
+/* FP64 totals of the moments, as lbm_conservation.  Waits. */
+lbm_status lbm_bgk_conservation(lbm_bgk* h, double out[4]);
+
+/* Steps since the state was set, clamped energies (e < 0 set to 0), the
+   reach R of the last step, device flags (bit 0 LBM_ESTATE, bit 1
+   LBM_EREACH).  Any pointer may be NULL.  Waits. */
+lbm_status lbm_bgk_diagnostics(lbm_bgk* h, int64_t* steps, int64_t* eclamps,
+                               int32_t* reach, uint32_t* flags);
+
+/* Wait for queued work and report device-side errors. */
+lbm_status lbm_bgk_synchronize(lbm_bgk* h);
+
+const char* lbm_bgk_last_error(const lbm_bgk* h);
+
+/* Free the handle and its device memory.  NULL-safe.  Waits first. */
+void lbm_bgk_destroy(lbm_bgk* h);
+
 /* ---- allocation-free single step --------------------------------------
  *
  * The paper has no counterpart to this entry point; it exists for callers

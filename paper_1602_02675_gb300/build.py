@@ -18,7 +18,8 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
           "-I", INCLUDE, "-I", CSRC]
 # Units whose arithmetic must round operation by operation (FP64 step and
 # the unit conversions) are built without floating-point contraction.
-NO_FMA = {"step_f64.cu", "aux_kernels.cu", "abi.cu", "batch.cu", "pool.cu"}
+NO_FMA = {"step_f64.cu", "aux_kernels.cu", "abi.cu", "batch.cu", "pool.cu",
+          "bgk.cu"}
 
 
 def nvcc() -> str:

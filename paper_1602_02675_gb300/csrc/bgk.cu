@@ -1,0 +1,823 @@
+// Relaxation-time step (general tau, eqs 4-5) on a per-packet state.
+//
+// With tau != 1 the collision keeps part of the distribution that arrived,
+// so a node's state is the set of packets it holds rather than its moments:
+// one slot j per entry of the velocity set (Section IV; 1-D: 5 slots, 2-D:
+// 8 slots in the table order of packet<DIM>), each slot carrying mass,
+// momentum and energy (the integrand of eq 6 for one migrating velocity).
+// One step, per node:
+//   Y = sum_j f_j (eq 6), slots in table order;
+//   f_eq_j of Y (Section III.B, eqs 11-26), as in the tau = 1 step;
+//   collision (eqs 4-5): f*_j = (1 - 1/tau) f_j + (1/tau) f_eq_j, which is
+//     f_eq_j exactly at tau = 1 (eq 10);
+//   migration: slot j moves with the node's V + c'_j and splits over
+//     s + n + c'_j + k with the weights of eqs 23, 28-29;
+//   the destination's slot j is the sum of its slot-j arrivals, sources in
+//   ascending order (y-major, x fastest), then corners.
+// Additional points (Section V.B) hold the supplying node's packets: copied
+// (transmissive, periodic) or mirrored across a reflecting wall (the slot
+// whose c' points the other way along the normal, normal momentum negated,
+// moments the node's with that component negated).
+//
+// Two kernels per step:
+//  * collide: one thread per source of the grid padded by the reach limit
+//    r_cap (additional points included): moments, equilibrium, post-collision
+//    packets, split fractions and a word (c1, n) into the source records;
+//    clamps, bad states and the step's reach of the grid's nodes are
+//    reduced on the device;
+//  * gather: one thread per destination, every source of the (2R + 1)^D
+//    window tested once, all slots' sums in registers, in the order above.
+// This unit is built without floating-point contraction, so the FP64
+// instance reproduces a plain evaluation of the same formulas bit for bit.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+#include "step_kernel.cuh"
+
+namespace lbm {
+namespace bgk {
+
+template <int DIM>
+struct Shape {
+  static constexpr int NP = DIM == 1 ? 5 : 8;  // slots
+  static constexpr int NF = DIM + 2;           // mass, momentum, energy
+};
+
+struct Args {
+  const void* f;   // packets in: element (j * NF + c) * n + i
+  void* fo;        // packets out, same layout
+  void* rec;       // source records (layout: rec_layout)
+  void* mom[4];    // moments buffer: rho, m_x, m_y (2-D), rhoE
+  int nx, ny, bc_x, bc_y, rc;
+  long long n;
+  double omega, keep;     // 1/tau, 1 - 1/tau
+  float omega_f, keep_f;  // the same rounded to FP32 on the host
+  EqConst k;
+  Scratch* scr;
+};
+
+// Source records over the padded grid (PX = nx + 2 rc, PY = ny + 2 rc in
+// 2-D, 1 in 1-D; cap = PX PY sources, source (x, y) at (y + rc) PX + x + rc
+// in 2-D, x + rc in 1-D): first one 64-bit word per source (c1, n_x, n_y as
+// 16-bit fields; c1 = -1: the source emits nothing), then NP * NF arrays of
+// the post-collision packets (slot j field c at array j * NF + c) and the
+// split fractions f_x, f_y (arrays NP * NF and NP * NF + 1).
+template <typename T, int DIM>
+struct RecView {
+  long long cap;
+  long long* word;
+  T* v;
+  __device__ __forceinline__ T& fs(int j, int c, long long i) const {
+    return v[(long long)(j * Shape<DIM>::NF + c) * cap + i];
+  }
+  __device__ __forceinline__ T& frac(int a, long long i) const {
+    return v[(long long)(Shape<DIM>::NP * Shape<DIM>::NF + a) * cap + i];
+  }
+};
+template <typename T, int DIM>
+__device__ __forceinline__ RecView<T, DIM> rec_view(const Args& a) {
+  const long long PX = (long long)a.nx + 2 * a.rc;
+  const long long PY = DIM == 2 ? (long long)a.ny + 2 * a.rc : 1;
+  RecView<T, DIM> r;
+  r.cap = PX * PY;
+  r.word = static_cast<long long*>(a.rec);
+  r.v = reinterpret_cast<T*>(r.word + r.cap);
+  return r;
+}
+
+// Bytes of the records of an nx x ny grid with reach limit rc.
+inline size_t rec_bytes(int dim, int nx, int ny, int rc, size_t es) {
+  const size_t PX = (size_t)nx + 2 * (size_t)rc;
+  const size_t PY = dim == 2 ? (size_t)ny + 2 * (size_t)rc : 1;
+  const int arrays = dim == 1 ? 5 * 3 + 2 : 8 * 4 + 2;
+  return PX * PY * (8 + arrays * es);
+}
+
+// Slot of the packet mirrored across a wall normal to `axis`.
+template <int DIM>
+__device__ __forceinline__ int mirror_slot(int axis, int j) {
+  if (DIM == 1) return j == 0 ? 0 : ((j & 1) ? j + 1 : j - 1);
+  const int dir = j & 3;  // 0: +x, 1: -x, 2: +y, 3: -y
+  if (axis == 0 && dir < 2) return j ^ 1;
+  if (axis == 1 && dir >= 2) return j ^ 1;
+  return j;
+}
+
+template <typename T>
+__device__ __forceinline__ T rel_const(double d, float f);
+template <>
+__device__ __forceinline__ double rel_const<double>(double d, float) {
+  return d;
+}
+template <>
+__device__ __forceinline__ float rel_const<float>(double, float f) {
+  return f;
+}
+
+// Equilibrium packet j of q as (mass, m_x, [m_y,] energy).
+template <typename T, int DIM>
+__device__ __forceinline__ void eq_packet(const Equil<T>& q, int j,
+                                          T (&out)[Shape<DIM>::NF]) {
+  int cx, cy, lev;
+  packet<DIM>(j, q.c1, &cx, &cy, &lev);
+  const T d = DIM == 1 ? (lev == 0 ? q.d0 : (lev == 1 ? q.d1 : q.d2))
+                       : (lev == 0 ? q.d1 : q.d2);
+  T px, py, pe;
+  packet_fields<T, DIM>(q, j, &px, &py, &pe);
+  out[0] = d;
+  out[1] = px;
+  if (DIM == 2) out[2] = py;
+  out[Shape<DIM>::NF - 1] = pe;
+}
+
+// Migration reach floor(|V_a|) + 1 + c2 of a node (0 if it emits nothing).
+template <typename T>
+__device__ __forceinline__ int node_reach(const Equil<T>& q) {
+  if (!q.emits) return 0;
+  const T a0 = q.V0 < T(0) ? -q.V0 : q.V0;
+  const T a1 = q.V1 < T(0) ? -q.V1 : q.V1;
+  const T v = dev_floor(a0 > a1 ? a0 : a1);
+  if (!(v < T(1.0e8))) return 100000000;
+  return (int)v + 2 + q.c1;
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ void node_moments(const T* f, long long n,
+                                             long long g, T (&Y)[4]) {
+  constexpr int NP = Shape<DIM>::NP, NF = Shape<DIM>::NF;
+  Y[0] = Y[1] = Y[2] = Y[3] = T(0);
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    Y[0] = Y[0] + f[(long long)(j * NF) * n + g];
+    Y[1] = Y[1] + f[(long long)(j * NF + 1) * n + g];
+    if (DIM == 2) Y[2] = Y[2] + f[(long long)(j * NF + 2) * n + g];
+    Y[3] = Y[3] + f[(long long)(j * NF + NF - 1) * n + g];
+  }
+}
+
+__device__ __forceinline__ void flag_warp(Scratch* scr, unsigned long long c,
+                                          bool bad, int rmax) {
+  const unsigned wc = __reduce_add_sync(0xffffffffu, (unsigned)c);
+  const bool wb = __any_sync(0xffffffffu, bad);
+  const int wr = __reduce_max_sync(0xffffffffu, rmax);
+  if ((threadIdx.x & 31) == 0) {
+    if (wc) atomicAdd(&scr->eclamps, (unsigned long long)wc);
+    if (wb) atomicOr(&scr->flags, kFlagState);
+    if (wr) atomicMax(&scr->reach_next, wr);
+  }
+}
+
+// Collision of every source of the padded grid into the records.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) collide(const Args a) {
+  constexpr int NP = Shape<DIM>::NP, NF = Shape<DIM>::NF;
+  const RecView<T, DIM> r = rec_view<T, DIM>(a);
+  const T* f = static_cast<const T*>(a.f);
+  const T omega = rel_const<T>(a.omega, a.omega_f);
+  const T keep = rel_const<T>(a.keep, a.keep_f);
+  const long long PX = (long long)a.nx + 2 * a.rc;
+  const long long PY = DIM == 2 ? (long long)a.ny + 2 * a.rc : 1;
+  unsigned long long clamps = 0;
+  bool bad = false;
+  int rmax = 0;
+  const long long px = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (long long py = blockIdx.y; py < PY && px < PX; py += gridDim.y) {
+    const long long sx = px - a.rc, sy = DIM == 2 ? py - a.rc : 0;
+    bool flx = false, fly = false;
+    const int gx = virtual_axis(a.bc_x, a.nx, sx, &flx);
+    const int gy = DIM == 2 ? virtual_axis(a.bc_y, a.ny, sy, &fly) : 0;
+    const long long g = (long long)gy * a.nx + gx;
+    // the supplying node's moments (eq 6); across a reflecting wall its
+    // normal momentum negated
+    T Y[4];
+    node_moments<T, DIM>(f, a.n, g, Y);
+    if (flx) Y[1] = -Y[1];
+    if (fly) Y[2] = -Y[2];
+    const Equil<T> q = equilibrium<T, DIM>(Y[0], Y[1], Y[2], Y[3], a.k);
+    if (sx >= 0 && sx < a.nx && sy >= 0 && sy < a.ny) {
+      clamps += q.clamp ? 1 : 0;
+      bad |= q.bad;
+      rmax = max(rmax, node_reach(q));
+    }
+    const long long i = py * PX + px;
+    long long w = s64_word(-1, 0, 0);
+    if (q.emits) {
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        int jg = j;
+        if (flx) jg = mirror_slot<DIM>(0, jg);
+        if (fly) jg = mirror_slot<DIM>(1, jg);
+        T fj[NF];
+#pragma unroll
+        for (int c = 0; c < NF; ++c)
+          fj[c] = f[(long long)(jg * NF + c) * a.n + g];
+        if (flx) fj[1] = -fj[1];
+        if (DIM == 2 && fly) fj[2] = -fj[2];
+        T feq[NF];
+        eq_packet<T, DIM>(q, j, feq);
+        // eqs 4-5 as the blend (1 - 1/tau) f + (1/tau) f_eq
+#pragma unroll
+        for (int c = 0; c < NF; ++c) r.fs(j, c, i) = keep * fj[c] + omega * feq[c];
+      }
+      r.frac(0, i) = q.f0;
+      if (DIM == 2) r.frac(1, i) = q.f1;
+      w = s64_word(q.c1, q.n0, q.n1);
+    }
+    r.word[i] = w;
+  }
+  flag_warp(a.scr, clamps, bad, rmax);
+}
+
+// Gather of every destination's slots from the records.  A reach beyond
+// the records' padding leaves the state as it was (copied through) and
+// flags LBM_EREACH.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) gather(const Args a) {
+  constexpr int NP = Shape<DIM>::NP, NF = Shape<DIM>::NF;
+  const RecView<T, DIM> r = rec_view<T, DIM>(a);
+  const T* fin = static_cast<const T*>(a.f);
+  T* fo = static_cast<T*>(a.fo);
+  const int R = a.scr->reach_next;
+  int dx, dy;
+  if (DIM == 1) {
+    dx = blockIdx.x * blockDim.x + threadIdx.x;
+    dy = 0;
+  } else {
+    dx = blockIdx.x * 32 + (threadIdx.x & 31);
+    dy = blockIdx.y * 8 + (threadIdx.x >> 5);
+  }
+  if (dx >= a.nx || dy >= a.ny) return;
+  const long long d = (long long)dy * a.nx + dx;
+  if (R > a.rc) {
+    if (d == 0) atomicOr(&a.scr->flags, kFlagReach);
+    for (int q = 0; q < NP * NF; ++q) fo[q * a.n + d] = fin[q * a.n + d];
+    return;
+  }
+  const long long PX = (long long)a.nx + 2 * a.rc;
+  const int Ry = DIM == 2 ? R : 0;
+  T acc[NP][NF];
+#pragma unroll
+  for (int j = 0; j < NP; ++j)
+#pragma unroll
+    for (int c = 0; c < NF; ++c) acc[j][c] = T(0);
+  for (int oyo = -Ry; oyo <= Ry; ++oyo) {
+    const int sy = dy + oyo;
+    const long long row = DIM == 2 ? (long long)(sy + a.rc) * PX : 0;
+    for (int oxo = -R; oxo <= R; ++oxo) {
+      const int sx = dx + oxo;
+      const long long i = row + sx + a.rc;
+      int c1, n0, n1;
+      const long long w = r.word[i];
+      c1 = (short)(w & 0xffff);
+      n0 = (short)((w >> 16) & 0xffff);
+      n1 = (short)((w >> 32) & 0xffff);
+      if (c1 < 0) continue;
+      // destination relative to the source's lattice shift
+      const int ox = -oxo - n0;
+      const int oy = DIM == 2 ? -oyo - n1 : 0;
+      const int c2 = c1 + 1;
+      if (ox < -c2 || ox > c2 + 1 || oy < -c2 || oy > c2 + 1) continue;
+      // split weights (1 - f, f) per axis (eqs 28-29)
+      const T f0 = r.frac(0, i);
+      const T g0 = T(1) - f0;
+      const T f1 = DIM == 2 ? r.frac(1, i) : T(0);
+      const T g1 = T(1) - f1;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        int cx, cy, lev;
+        packet<DIM>(j, c1, &cx, &cy, &lev);
+        const int kx = ox - cx, ky = oy - cy;
+        if (kx < 0 || kx > 1) continue;
+        if (DIM == 2 && (ky < 0 || ky > 1)) continue;
+        const T ax = kx ? f0 : g0;
+        const T al = DIM == 1 ? ax : ax * (ky ? f1 : g1);
+#pragma unroll
+        for (int c = 0; c < NF; ++c) acc[j][c] = acc[j][c] + al * r.fs(j, c, i);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NP; ++j)
+#pragma unroll
+    for (int c = 0; c < NF; ++c) fo[(long long)(j * NF + c) * a.n + d] = acc[j][c];
+}
+
+// Moments of every node (eq 6) into the moments buffer.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) moments(const Args a) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  T Y[4];
+  node_moments<T, DIM>(static_cast<const T*>(a.f), a.n, i, Y);
+  static_cast<T*>(a.mom[0])[i] = Y[0];
+  static_cast<T*>(a.mom[1])[i] = Y[1];
+  if (DIM == 2) static_cast<T*>(a.mom[2])[i] = Y[2];
+  static_cast<T*>(a.mom[3])[i] = Y[3];
+}
+
+// Equilibrium packets of the moments buffer into the packets (fo).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) from_moments(const Args a) {
+  constexpr int NP = Shape<DIM>::NP, NF = Shape<DIM>::NF;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  bool bad = false;
+  if (i < a.n) {
+    const T rho = static_cast<const T*>(a.mom[0])[i];
+    const T mx = static_cast<const T*>(a.mom[1])[i];
+    const T my = DIM == 2 ? static_cast<const T*>(a.mom[2])[i] : T(0);
+    const T rE = static_cast<const T*>(a.mom[3])[i];
+    const Equil<T> q = equilibrium<T, DIM>(rho, mx, my, rE, a.k);
+    bad = q.bad;
+    T* fo = static_cast<T*>(a.fo);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      T p[NF];
+#pragma unroll
+      for (int c = 0; c < NF; ++c) p[c] = T(0);
+      if (q.emits) eq_packet<T, DIM>(q, j, p);
+#pragma unroll
+      for (int c = 0; c < NF; ++c) fo[(long long)(j * NF + c) * a.n + i] = p[c];
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
+    atomicOr(&a.scr->flags, kFlagState);
+}
+
+// One packet array between host doubles (physical units) and the state
+// (lattice units): x_lattice = x_physical * scale.
+template <typename T>
+__global__ void __launch_bounds__(256) to_lattice(const double* src, T* dst,
+                                                  long long n, double scale) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (T)(src[i] * scale);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) to_physical(const T* src, double* dst,
+                                                   long long n, double inv) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (double)src[i] * inv;
+}
+
+}  // namespace bgk
+}  // namespace lbm
+
+// ---------------------------------------------------------------------------
+// C ABI (include/lbm.h: lbm_bgk_*)
+// ---------------------------------------------------------------------------
+
+using namespace lbm;
+
+struct lbm_bgk {
+  lbm_config cfg;
+  cudaStream_t stream = nullptr;
+  bool f64 = true;
+  int dim = 1, np = 5, nf = 3;
+  int nx = 1, ny = 1;
+  int64_t n = 0;
+  double dx = 0.0, lambda = 0.0, tau = 1.0;
+  EqConst k{};
+  int r_cap = 0;
+  void* f[2] = {nullptr, nullptr};
+  int cur = 0;
+  void* mom[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* rec = nullptr;
+  Scratch* scr = nullptr;
+  double* part = nullptr;
+  int part_cap = 0;
+  double* staging = nullptr;  // 5 n doubles
+  int64_t steps = 0;
+  bool broken = false;
+  std::string err;
+};
+
+namespace {
+
+lbm_status bfail(lbm_bgk* h, lbm_status st, const std::string& msg) {
+  if (h) {
+    h->err = msg;
+    if (st != LBM_EINVAL) h->broken = true;
+  }
+  return st;
+}
+
+lbm_status bcuda(lbm_bgk* h, cudaError_t e, const char* what) {
+  return bfail(h, LBM_ECUDA,
+               std::string("lbm_bgk: ") + what + ": " + cudaGetErrorString(e));
+}
+
+#define BGK_CUDA(h, call, what)                              \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return bcuda((h), e_, (what));    \
+  } while (0)
+
+lbm_status busable(lbm_bgk* h) {
+  if (!h) return LBM_EINVAL;
+  if (h->broken)
+    return bfail(h, LBM_ECUDA, "lbm_bgk: handle is in an error state: " + h->err);
+  return LBM_OK;
+}
+
+size_t bes(const lbm_bgk* h) { return h->f64 ? 8 : 4; }
+
+bgk::Args args_of(const lbm_bgk* h) {
+  bgk::Args a;
+  a.f = h->f[h->cur];
+  a.fo = h->f[h->cur ^ 1];
+  a.rec = h->rec;
+  for (int i = 0; i < 4; ++i) a.mom[i] = h->mom[i];
+  a.nx = h->nx;
+  a.ny = h->ny;
+  a.bc_x = h->cfg.bc_x;
+  a.bc_y = h->dim == 2 ? h->cfg.bc_y : 0;
+  a.rc = h->r_cap;
+  a.n = h->n;
+  a.omega = 1.0 / h->tau;
+  a.keep = 1.0 - a.omega;
+  a.omega_f = (float)a.omega;
+  a.keep_f = (float)a.keep;
+  a.k = h->k;
+  a.scr = h->scr;
+  return a;
+}
+
+unsigned blocks_1d(long long n) { return (unsigned)((n + 255) / 256); }
+
+template <typename T, int DIM>
+cudaError_t launch_step_t(const bgk::Args& a, cudaStream_t s) {
+  const long long PX = (long long)a.nx + 2 * a.rc;
+  const long long PY = DIM == 2 ? (long long)a.ny + 2 * a.rc : 1;
+  dim3 cg((unsigned)((PX + 255) / 256), (unsigned)(PY < 65535 ? PY : 65535));
+  bgk::collide<T, DIM><<<cg, 256, 0, s>>>(a);
+  if (DIM == 1) {
+    bgk::gather<T, 1><<<blocks_1d(a.nx), 256, 0, s>>>(a);
+  } else {
+    dim3 gg((unsigned)((a.nx + 31) / 32), (unsigned)((a.ny + 7) / 8));
+    bgk::gather<T, 2><<<gg, 256, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t bgk_launch_step(const lbm_bgk* h, const bgk::Args& a) {
+  if (h->f64)
+    return h->dim == 1 ? launch_step_t<double, 1>(a, h->stream)
+                       : launch_step_t<double, 2>(a, h->stream);
+  return h->dim == 1 ? launch_step_t<float, 1>(a, h->stream)
+                     : launch_step_t<float, 2>(a, h->stream);
+}
+
+// Moments of the current packets into the moments buffer.
+cudaError_t launch_moments(const lbm_bgk* h) {
+  const bgk::Args a = args_of(h);
+  const unsigned g = blocks_1d(h->n);
+  if (h->f64) {
+    if (h->dim == 1) bgk::moments<double, 1><<<g, 256, 0, h->stream>>>(a);
+    else bgk::moments<double, 2><<<g, 256, 0, h->stream>>>(a);
+  } else {
+    if (h->dim == 1) bgk::moments<float, 1><<<g, 256, 0, h->stream>>>(a);
+    else bgk::moments<float, 2><<<g, 256, 0, h->stream>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// Equilibrium packets of the moments buffer into the current packets.
+cudaError_t launch_from_moments(const lbm_bgk* h) {
+  bgk::Args a = args_of(h);
+  a.fo = h->f[h->cur];
+  const unsigned g = blocks_1d(h->n);
+  if (h->f64) {
+    if (h->dim == 1) bgk::from_moments<double, 1><<<g, 256, 0, h->stream>>>(a);
+    else bgk::from_moments<double, 2><<<g, 256, 0, h->stream>>>(a);
+  } else {
+    if (h->dim == 1) bgk::from_moments<float, 1><<<g, 256, 0, h->stream>>>(a);
+    else bgk::from_moments<float, 2><<<g, 256, 0, h->stream>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+lbm_status bcheck_flags(lbm_bgk* h) {
+  Scratch s;
+  cudaError_t e = cudaMemcpyAsync(&s, h->scr, sizeof(Scratch),
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return bcuda(h, e, "synchronize");
+  if (s.flags & kFlagState)
+    return bfail(h, LBM_ESTATE,
+                 "lbm_bgk: a node reached rho < 0 or a non-finite moment");
+  if (s.flags & kFlagReach)
+    return bfail(h, LBM_EREACH,
+                 "lbm_bgk: migration reach exceeded max_reach (raise "
+                 "lbm_config.max_reach)");
+  return LBM_OK;
+}
+
+// Moments were written into the moments buffer: the packets at equilibrium.
+lbm_status seed_from_moments(lbm_bgk* h) {
+  BGK_CUDA(h, cudaMemsetAsync(h->scr, 0, sizeof(Scratch), h->stream),
+           "scratch clear");
+  BGK_CUDA(h, launch_from_moments(h), "equilibrium kernel");
+  h->steps = 0;
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_bgk_create(const lbm_config* cfg, double tau, lbm_bgk** out) {
+  if (!cfg || !out) return LBM_EINVAL;
+  *out = nullptr;
+  const lbm_config& c = *cfg;
+  if (c.dim != 1 && c.dim != 2) return LBM_EINVAL;
+  if (c.precision != LBM_F32 && c.precision != LBM_F64) return LBM_EINVAL;
+  if (c.nx < 1 || c.ny < 1 || (c.dim == 1 && c.ny != 1)) return LBM_EINVAL;
+  if (c.nx * c.ny > (int64_t)INT32_MAX || c.nx > INT32_MAX || c.ny > INT32_MAX)
+    return LBM_EINVAL;
+  if (c.bc_x < 0 || c.bc_x > 2 || (c.dim == 2 && (c.bc_y < 0 || c.bc_y > 2)))
+    return LBM_EINVAL;
+  if (!(c.x1 > c.x0) || !(c.gamma > 1.0) || !(c.dt > 0.0)) return LBM_EINVAL;
+  if (!std::isfinite(c.x0) || !std::isfinite(c.x1) || !std::isfinite(c.y0) ||
+      !std::isfinite(c.dt) || !std::isfinite(c.gamma))
+    return LBM_EINVAL;
+  if (c.dim == 1 && !(c.theta >= 0.0 && c.theta < 1.0)) return LBM_EINVAL;
+  if (c.dim == 2 && c.theta != 0.0) return LBM_EINVAL;
+  if (c.max_reach < 0 || c.max_reach > 1024) return LBM_EINVAL;
+  // the 2-D gather launch takes 8 rows per block along grid y
+  if (c.dim == 2 && (c.ny + 7) / 8 > 65535) return LBM_EINVAL;
+  if (!(tau > 0.5) || !std::isfinite(tau)) return LBM_EINVAL;
+
+  lbm_bgk* h = new (std::nothrow) lbm_bgk();
+  if (!h) return LBM_ENOMEM;
+  h->cfg = c;
+  h->stream = (cudaStream_t)c.stream;
+  h->f64 = c.precision == LBM_F64;
+  h->dim = c.dim;
+  h->np = c.dim == 1 ? 5 : 8;
+  h->nf = c.dim + 2;
+  h->nx = (int)c.nx;
+  h->ny = (int)(c.dim == 2 ? c.ny : 1);
+  h->n = (int64_t)h->nx * h->ny;
+  h->dx = (c.x1 - c.x0) / (double)c.nx;
+  h->lambda = c.dt / h->dx;
+  h->tau = tau;
+  const double D = (double)c.dim;
+  h->k.theta = c.dim == 1 ? c.theta : 0.0;
+  h->k.kq = D * (c.gamma - 1.0);
+  h->k.kphi = 1.0 - 0.5 * D * (c.gamma - 1.0);
+  h->k.b1 = c.dim == 1 ? 2.0 : 4.0;
+  h->k.kreach = h->k.kq / (1.0 - h->k.theta);
+  h->k.set_fp32_copies();
+  h->r_cap = c.max_reach > 0 ? c.max_reach : (c.dim == 1 ? 64 : 6);
+  h->part_cap = totals_blocks(h->n);
+  const size_t fb = bes(h) * (size_t)h->n * (size_t)(h->np * h->nf);
+  bool ok = true;
+  for (int b = 0; b < 2 && ok; ++b) ok = cudaMalloc(&h->f[b], fb) == cudaSuccess;
+  for (int i = 0; i < 4 && ok; ++i) {
+    if (i == 2 && c.dim == 1) continue;
+    ok = cudaMalloc(&h->mom[i], bes(h) * (size_t)h->n) == cudaSuccess;
+  }
+  ok = ok && cudaMalloc(&h->rec, bgk::rec_bytes(h->dim, h->nx, h->ny, h->r_cap,
+                                                bes(h))) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->scr, sizeof(Scratch)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->part, sizeof(double) * 4 * (size_t)h->part_cap) ==
+                 cudaSuccess;
+  ok = ok && cudaMalloc(&h->staging, sizeof(double) * 5 * (size_t)h->n) ==
+                 cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    lbm_bgk_destroy(h);
+    return LBM_ENOMEM;
+  }
+  for (int b = 0; b < 2; ++b) cudaMemsetAsync(h->f[b], 0, fb, h->stream);
+  cudaMemsetAsync(h->scr, 0, sizeof(Scratch), h->stream);
+  const cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    const lbm_status st = bcuda(h, e, "initial clear");
+    lbm_bgk_destroy(h);
+    return st;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+lbm_status lbm_bgk_init_riemann(lbm_bgk* h, const lbm_prim* inner,
+                                const lbm_prim* outer, int32_t geom, double a0,
+                                double a1, double radius) {
+  lbm_status st = busable(h);
+  if (st != LBM_OK) return st;
+  if (!inner || !outer || (geom != LBM_PLANAR_X && geom != LBM_CIRCLE))
+    return bfail(h, LBM_EINVAL, "lbm_bgk_init_riemann: bad argument");
+  if (!(inner->rho >= 0.0) || !(outer->rho >= 0.0) || !(inner->p >= 0.0) ||
+      !(outer->p >= 0.0))
+    return bfail(h, LBM_EINVAL, "lbm_bgk_init_riemann: negative rho or p");
+  InitArgs a;
+  for (int i = 0; i < 4; ++i) a.f[i] = h->mom[i];
+  a.nx = h->nx;
+  a.ny = h->ny;
+  a.dim = h->dim;
+  a.x0 = h->cfg.x0;
+  a.y0 = h->cfg.y0;
+  a.dx = h->dx;
+  a.lambda = h->lambda;
+  a.gamma = h->cfg.gamma;
+  a.geom = geom;
+  a.a0 = a0;
+  a.a1 = a1;
+  a.radius = radius;
+  const lbm_prim* s[2] = {inner, outer};
+  for (int j = 0; j < 2; ++j) {
+    double* d = j == 0 ? a.in_ : a.out_;
+    d[0] = s[j]->rho;
+    d[1] = s[j]->u;
+    d[2] = h->dim == 2 ? s[j]->v : 0.0;
+    d[3] = s[j]->p;
+  }
+  BGK_CUDA(h, launch_init(h->f64, a, h->stream), "init kernel");
+  return seed_from_moments(h);
+}
+
+lbm_status lbm_bgk_set_moments(lbm_bgk* h, const double* rho, const double* mx,
+                               const double* my, const double* rhoE,
+                               int64_t n) {
+  lbm_status st = busable(h);
+  if (st != LBM_OK) return st;
+  if (!rho || !mx || !rhoE || (h->dim == 2 && !my) || n != h->n)
+    return bfail(h, LBM_EINVAL, "lbm_bgk_set_moments: bad arrays or size");
+  const size_t nb = sizeof(double) * (size_t)n;
+  const double* src[4] = {rho, mx, h->dim == 2 ? my : nullptr, rhoE};
+  for (int i = 0; i < 4; ++i)
+    if (src[i])
+      BGK_CUDA(h, cudaMemcpyAsync(h->staging + (size_t)i * n, src[i], nb,
+                                  cudaMemcpyHostToDevice, h->stream),
+               "copy to device");
+  BGK_CUDA(h, launch_from_host_layout(h->f64, 1, h->dim, h->staging, h->mom, n,
+                                      h->lambda, h->cfg.gamma, h->stream),
+           "convert kernel");
+  st = seed_from_moments(h);
+  if (st != LBM_OK) return st;
+  BGK_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
+  return LBM_OK;
+}
+
+// Unit scale of packet field c (lattice = physical * scale): mass 1,
+// momentum lambda, energy lambda^2.
+static double field_scale(const lbm_bgk* h, int c) {
+  if (c == 0) return 1.0;
+  if (c == h->nf - 1) return h->lambda * h->lambda;
+  return h->lambda;
+}
+
+lbm_status lbm_bgk_set_packets(lbm_bgk* h, const double* f, int64_t n) {
+  lbm_status st = busable(h);
+  if (st != LBM_OK) return st;
+  if (!f || n != h->n)
+    return bfail(h, LBM_EINVAL, "lbm_bgk_set_packets: bad array or size");
+  const size_t nb = sizeof(double) * (size_t)n;
+  for (int q = 0; q < h->np * h->nf; ++q) {
+    BGK_CUDA(h, cudaMemcpyAsync(h->staging, f + (size_t)q * n, nb,
+                                cudaMemcpyHostToDevice, h->stream),
+             "copy to device");
+    const double sc = field_scale(h, q % h->nf);
+    if (h->f64)
+      bgk::to_lattice<double><<<blocks_1d(n), 256, 0, h->stream>>>(
+          h->staging, static_cast<double*>(h->f[h->cur]) + (size_t)q * n, n, sc);
+    else
+      bgk::to_lattice<float><<<blocks_1d(n), 256, 0, h->stream>>>(
+          h->staging, static_cast<float*>(h->f[h->cur]) + (size_t)q * n, n, sc);
+    BGK_CUDA(h, cudaGetLastError(), "convert kernel");
+  }
+  BGK_CUDA(h, cudaMemsetAsync(h->scr, 0, sizeof(Scratch), h->stream),
+           "scratch clear");
+  h->steps = 0;
+  BGK_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
+  return LBM_OK;
+}
+
+lbm_status lbm_bgk_packets(lbm_bgk* h, double* f, int64_t n) {
+  lbm_status st = busable(h);
+  if (st != LBM_OK) return st;
+  if (!f || n != h->n)
+    return bfail(h, LBM_EINVAL, "lbm_bgk_packets: bad array or size");
+  const size_t nb = sizeof(double) * (size_t)n;
+  for (int q = 0; q < h->np * h->nf; ++q) {
+    const double inv = 1.0 / field_scale(h, q % h->nf);
+    if (h->f64)
+      bgk::to_physical<double><<<blocks_1d(n), 256, 0, h->stream>>>(
+          static_cast<const double*>(h->f[h->cur]) + (size_t)q * n, h->staging,
+          n, inv);
+    else
+      bgk::to_physical<float><<<blocks_1d(n), 256, 0, h->stream>>>(
+          static_cast<const float*>(h->f[h->cur]) + (size_t)q * n, h->staging,
+          n, inv);
+    BGK_CUDA(h, cudaGetLastError(), "convert kernel");
+    BGK_CUDA(h, cudaMemcpyAsync(f + (size_t)q * n, h->staging, nb,
+                                cudaMemcpyDeviceToHost, h->stream),
+             "copy to host");
+    // the staging buffer is reused by the next array
+    BGK_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
+  }
+  return bcheck_flags(h);
+}
+
+lbm_status lbm_bgk_step(lbm_bgk* h, int64_t nsteps) {
+  lbm_status st = busable(h);
+  if (st != LBM_OK) return st;
+  if (nsteps < 0) return bfail(h, LBM_EINVAL, "lbm_bgk_step: nsteps < 0");
+  for (int64_t s = 0; s < nsteps; ++s) {
+    const bgk::Args a = args_of(h);
+    BGK_CUDA(h, cudaMemsetAsync(&h->scr->reach_next, 0, sizeof(int), h->stream),
+             "reach clear");
+    BGK_CUDA(h, bgk_launch_step(h, a), "step kernels");
+    h->cur ^= 1;
+    h->steps += 1;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_bgk_moments(lbm_bgk* h, double* rho, double* mx, double* my,
+                           double* rhoE, double* p, int64_t n) {
+  lbm_status st = busable(h);
+  if (st != LBM_OK) return st;
+  if (!rho || !mx || !rhoE || n != h->n)
+    return bfail(h, LBM_EINVAL, "lbm_bgk_moments: bad arrays or size");
+  BGK_CUDA(h, launch_moments(h), "moments kernel");
+  BGK_CUDA(h, launch_to_host_layout(h->f64, h->dim, h->mom, h->staging, n,
+                                    h->lambda, h->cfg.gamma, h->stream),
+           "readback kernel");
+  const size_t nb = sizeof(double) * (size_t)n;
+  double* dst[5] = {rho, mx, h->dim == 2 ? my : nullptr, rhoE, p};
+  for (int i = 0; i < 5; ++i)
+    if (dst[i])
+      BGK_CUDA(h, cudaMemcpyAsync(dst[i], h->staging + (size_t)i * n, nb,
+                                  cudaMemcpyDeviceToHost, h->stream),
+               "copy to host");
+  return bcheck_flags(h);
+}
+
+lbm_status lbm_bgk_conservation(lbm_bgk* h, double out[4]) {
+  lbm_status st = busable(h);
+  if (st != LBM_OK) return st;
+  if (!out) return bfail(h, LBM_EINVAL, "lbm_bgk_conservation: NULL out");
+  BGK_CUDA(h, launch_moments(h), "moments kernel");
+  BGK_CUDA(h, launch_totals(h->f64, h->dim, h->mom, h->n, h->part, h->part_cap,
+                            h->scr, h->stream),
+           "totals kernel");
+  st = bcheck_flags(h);
+  if (st != LBM_OK) return st;
+  Scratch sc;
+  BGK_CUDA(h, cudaMemcpyAsync(&sc, h->scr, sizeof(Scratch),
+                              cudaMemcpyDeviceToHost, h->stream),
+           "copy totals");
+  BGK_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
+  out[0] = sc.cons[0];
+  out[1] = sc.cons[1] / h->lambda;
+  out[2] = sc.cons[2] / h->lambda;
+  out[3] = sc.cons[3] / (h->lambda * h->lambda);
+  return LBM_OK;
+}
+
+lbm_status lbm_bgk_diagnostics(lbm_bgk* h, int64_t* steps, int64_t* eclamps,
+                               int32_t* reach, uint32_t* flags) {
+  if (!h) return LBM_EINVAL;
+  Scratch s;
+  cudaError_t e = cudaMemcpyAsync(&s, h->scr, sizeof(Scratch),
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return bcuda(h, e, "diagnostics");
+  if (steps) *steps = h->steps;
+  if (eclamps) *eclamps = (int64_t)s.eclamps;
+  if (reach) *reach = s.reach_next;
+  if (flags) *flags = s.flags;
+  return LBM_OK;
+}
+
+lbm_status lbm_bgk_synchronize(lbm_bgk* h) {
+  lbm_status st = busable(h);
+  if (st != LBM_OK) return st;
+  return bcheck_flags(h);
+}
+
+const char* lbm_bgk_last_error(const lbm_bgk* h) {
+  return h ? h->err.c_str() : "lbm_bgk: NULL handle";
+}
+
+void lbm_bgk_destroy(lbm_bgk* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  for (int b = 0; b < 2; ++b)
+    if (h->f[b]) cudaFree(h->f[b]);
+  for (int i = 0; i < 4; ++i)
+    if (h->mom[i]) cudaFree(h->mom[i]);
+  if (h->rec) cudaFree(h->rec);
+  if (h->scr) cudaFree(h->scr);
+  if (h->part) cudaFree(h->part);
+  if (h->staging) cudaFree(h->staging);
+  cudaGetLastError();
+  delete h;
+}
+
+}  // extern "C"

@@ -147,6 +147,28 @@ def load() -> ctypes.CDLL:
                                  ctypes.c_int64], ctypes.c_int),
         "lbm_batch2d_last_error": ([_H], ctypes.c_char_p),
         "lbm_batch2d_destroy": ([_H], None),
+        "lbm_bgk_create": ([ctypes.POINTER(lbm_config), ctypes.c_double,
+                            ctypes.POINTER(_H)], ctypes.c_int),
+        "lbm_bgk_init_riemann": ([_H, ctypes.POINTER(lbm_prim),
+                                  ctypes.POINTER(lbm_prim), ctypes.c_int32,
+                                  ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double], ctypes.c_int),
+        "lbm_bgk_set_moments": ([_H, _DP, _DP, _DP, _DP, ctypes.c_int64],
+                                ctypes.c_int),
+        "lbm_bgk_set_packets": ([_H, _DP, ctypes.c_int64], ctypes.c_int),
+        "lbm_bgk_packets": ([_H, _DP, ctypes.c_int64], ctypes.c_int),
+        "lbm_bgk_step": ([_H, ctypes.c_int64], ctypes.c_int),
+        "lbm_bgk_moments": ([_H, _DP, _DP, _DP, _DP, _DP, ctypes.c_int64],
+                            ctypes.c_int),
+        "lbm_bgk_conservation": ([_H, _DP], ctypes.c_int),
+        "lbm_bgk_diagnostics": ([_H, ctypes.POINTER(ctypes.c_int64),
+                                 ctypes.POINTER(ctypes.c_int64),
+                                 ctypes.POINTER(ctypes.c_int32),
+                                 ctypes.POINTER(ctypes.c_uint32)],
+                                ctypes.c_int),
+        "lbm_bgk_synchronize": ([_H], ctypes.c_int),
+        "lbm_bgk_last_error": ([_H], ctypes.c_char_p),
+        "lbm_bgk_destroy": ([_H], None),
         "lbm_step_noalloc": ([ctypes.POINTER(lbm_noalloc_desc),
                               ctypes.c_void_p * 4, ctypes.c_void_p * 4,
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -288,6 +310,97 @@ class Solver:
 
     def synchronize(self):
         _check(self.h, load().lbm_synchronize(self.h))
+
+
+class Bgk:
+    """One relaxation-time (tau != 1, eqs 4-5) handle of the C ABI: the
+    state is per packet, shaped (slots, fields, nodes) at this binding
+    (slots 5 / 8, fields dim + 2), physical units."""
+
+    def __init__(self, cfg: lbm_config, tau: float):
+        lib = load()
+        self.cfg = cfg
+        self.n = cfg.nx * cfg.ny
+        self.dim = cfg.dim
+        self.slots = 5 if cfg.dim == 1 else 8
+        self.fields = cfg.dim + 2
+        h = _H()
+        st = lib.lbm_bgk_create(ctypes.byref(cfg), float(tau), ctypes.byref(h))
+        if st != OK:
+            raise LbmError(st, "lbm_bgk_create")
+        self.h = h
+
+    def _check(self, st):
+        if st != OK:
+            msg = load().lbm_bgk_last_error(self.h)
+            raise LbmError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbm_bgk_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init_riemann(self, inner, outer, geom=PLANAR_X, a0=0.5, a1=0.5,
+                     radius=0.0):
+        a, b = lbm_prim(*_prim4(inner)), lbm_prim(*_prim4(outer))
+        self._check(load().lbm_bgk_init_riemann(self.h, ctypes.byref(a),
+                                                ctypes.byref(b), geom, a0, a1,
+                                                radius))
+
+    def set_moments(self, rho, mx, my, rhoE):
+        n = self.n
+        rho, mx, my, rhoE = (_f64(x, n) for x in (rho, mx, my, rhoE))
+        self._check(load().lbm_bgk_set_moments(self.h, _dp(rho), _dp(mx),
+                                               _dp(my), _dp(rhoE), n))
+
+    def set_packets(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        if f.shape != (self.slots, self.fields, self.n):
+            raise ValueError(f"packets of shape {f.shape}")
+        self._check(load().lbm_bgk_set_packets(self.h, _dp(f), self.n))
+
+    def packets(self) -> np.ndarray:
+        f = np.empty((self.slots, self.fields, self.n))
+        self._check(load().lbm_bgk_packets(self.h, _dp(f), self.n))
+        return f
+
+    def step(self, nsteps=1):
+        self._check(load().lbm_bgk_step(self.h, int(nsteps)))
+
+    def moments(self) -> dict:
+        n = self.n
+        out = {k: np.empty(n) for k in ("rho", "mx", "rhoE", "p")}
+        if self.dim == 2:
+            out["my"] = np.empty(n)
+        self._check(load().lbm_bgk_moments(
+            self.h, _dp(out["rho"]), _dp(out["mx"]), _dp(out.get("my")),
+            _dp(out["rhoE"]), _dp(out["p"]), n))
+        return out
+
+    def conservation(self) -> np.ndarray:
+        out = np.zeros(4)
+        self._check(load().lbm_bgk_conservation(self.h, _dp(out)))
+        return out
+
+    def diagnostics(self) -> dict:
+        s, e = ctypes.c_int64(0), ctypes.c_int64(0)
+        r, f = ctypes.c_int32(0), ctypes.c_uint32(0)
+        self._check(load().lbm_bgk_diagnostics(self.h, ctypes.byref(s),
+                                               ctypes.byref(e), ctypes.byref(r),
+                                               ctypes.byref(f)))
+        return {"steps": s.value, "eclamps": e.value, "reach": r.value,
+                "flags": f.value}
+
+    def synchronize(self):
+        self._check(load().lbm_bgk_synchronize(self.h))
 
 
 def lbm_step_noalloc(desc: lbm_noalloc_desc, inputs, outputs, totals=0,

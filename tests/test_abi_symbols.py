@@ -60,3 +60,18 @@ def test_binding_names_match_the_abi():
     lib = L.load()
     for n in _declared():
         assert getattr(lib, n).argtypes is not None or n == "lbm_abi_version"
+
+
+def test_bgk_create_checks_tau_before_any_cuda_call():
+    """tau must be finite and above 1/2 (eqs 4-5); the check comes before
+    any allocation, so it runs here without a GPU."""
+    from paper_1602_02675_gb300 import lbm as L
+    lib = L.load()
+    cfg = L.make_config(1, 64, bc_x=L.PERIODIC)
+    h = ctypes.c_void_p()
+    for tau in (0.5, 0.25, -1.0, float("nan"), float("inf")):
+        assert lib.lbm_bgk_create(ctypes.byref(cfg), tau,
+                                  ctypes.byref(h)) == L.EINVAL
+        assert not h.value
+    lib.lbm_bgk_destroy(None)
+    assert lib.lbm_bgk_last_error(None)
