@@ -22,11 +22,14 @@
 // Two kernels per step:
 //  * collide: one thread per source of the grid padded by the reach limit
 //    r_cap (additional points included): moments, equilibrium, post-collision
-//    packets, split fractions and a word (c1, n) into the source records;
+//    packets, corner weights and a word (c1, n) into the source records;
 //    clamps, bad states and the step's reach of the grid's nodes are
 //    reduced on the device;
-//  * gather: one thread per destination, every source of the (2R + 1)^D
-//    window tested once, all slots' sums in registers, in the order above.
+//  * gather: one thread per destination of a 32 x 8 tile.  A tile whose
+//    source window holds one type (c1, n) reads each slot's four arriving
+//    corners directly; otherwise every source of the (2R + 1)^D window is
+//    tested once, all slots' sums in registers.  Either way in the order
+//    above.
 // This unit is built without floating-point contraction, so the FP64
 // instance reproduces a plain evaluation of the same formulas bit for bit.
 #include <cmath>
@@ -58,14 +61,23 @@ struct Args {
   float omega_f, keep_f;  // the same rounded to FP32 on the host
   EqConst k;
   Scratch* scr;
+  int rs;  // reach slot of this step: scr->reach (0) or scr->reach_next (1)
 };
+
+// The two reach slots alternate between steps: the collision of a step
+// max-reduces into its slot, the gather reads it and clears the other one
+// for the next step (no gather of the previous step still reads it).
+__device__ __forceinline__ int* reach_slot(Scratch* scr, int rs) {
+  return rs ? &scr->reach_next : &scr->reach;
+}
 
 // Source records over the padded grid (PX = nx + 2 rc, PY = ny + 2 rc in
 // 2-D, 1 in 1-D; cap = PX PY sources, source (x, y) at (y + rc) PX + x + rc
 // in 2-D, x + rc in 1-D): first one 64-bit word per source (c1, n_x, n_y as
 // 16-bit fields; c1 = -1: the source emits nothing), then NP * NF arrays of
 // the post-collision packets (slot j field c at array j * NF + c) and the
-// split fractions f_x, f_y (arrays NP * NF and NP * NF + 1).
+// corner weights of eqs 28-29 (arrays NP * NF + k: 1-D k = 0, 1 for
+// (1 - f, f); 2-D k = kx + 2 ky for (1 - f_x or f_x) (1 - f_y or f_y)).
 template <typename T, int DIM>
 struct RecView {
   long long cap;
@@ -74,8 +86,8 @@ struct RecView {
   __device__ __forceinline__ T& fs(int j, int c, long long i) const {
     return v[(long long)(j * Shape<DIM>::NF + c) * cap + i];
   }
-  __device__ __forceinline__ T& frac(int a, long long i) const {
-    return v[(long long)(Shape<DIM>::NP * Shape<DIM>::NF + a) * cap + i];
+  __device__ __forceinline__ T& wt(int k, long long i) const {
+    return v[(long long)(Shape<DIM>::NP * Shape<DIM>::NF + k) * cap + i];
   }
 };
 template <typename T, int DIM>
@@ -93,7 +105,7 @@ __device__ __forceinline__ RecView<T, DIM> rec_view(const Args& a) {
 inline size_t rec_bytes(int dim, int nx, int ny, int rc, size_t es) {
   const size_t PX = (size_t)nx + 2 * (size_t)rc;
   const size_t PY = dim == 2 ? (size_t)ny + 2 * (size_t)rc : 1;
-  const int arrays = dim == 1 ? 5 * 3 + 2 : 8 * 4 + 2;
+  const int arrays = dim == 1 ? 5 * 3 + 2 : 8 * 4 + 4;
   return PX * PY * (8 + arrays * es);
 }
 
@@ -159,21 +171,23 @@ __device__ __forceinline__ void node_moments(const T* f, long long n,
   }
 }
 
-__device__ __forceinline__ void flag_warp(Scratch* scr, unsigned long long c,
-                                          bool bad, int rmax) {
+__device__ __forceinline__ void flag_warp(Scratch* scr, int rs,
+                                          unsigned long long c, bool bad,
+                                          int rmax) {
   const unsigned wc = __reduce_add_sync(0xffffffffu, (unsigned)c);
   const bool wb = __any_sync(0xffffffffu, bad);
   const int wr = __reduce_max_sync(0xffffffffu, rmax);
   if ((threadIdx.x & 31) == 0) {
     if (wc) atomicAdd(&scr->eclamps, (unsigned long long)wc);
     if (wb) atomicOr(&scr->flags, kFlagState);
-    if (wr) atomicMax(&scr->reach_next, wr);
+    if (wr) atomicMax(reach_slot(scr, rs), wr);
   }
 }
 
 // Collision of every source of the padded grid into the records.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) collide(const Args a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
+    collide(const Args a) {
   constexpr int NP = Shape<DIM>::NP, NF = Shape<DIM>::NF;
   const RecView<T, DIM> r = rec_view<T, DIM>(a);
   const T* f = static_cast<const T*>(a.f);
@@ -206,7 +220,9 @@ __global__ void __launch_bounds__(256) collide(const Args a) {
     const long long i = py * PX + px;
     long long w = s64_word(-1, 0, 0);
     if (q.emits) {
-#pragma unroll
+      // (a rolled loop: the slot's fields are read again here rather than
+      // kept in registers from the moments)
+#pragma unroll 1
       for (int j = 0; j < NP; ++j) {
         int jg = j;
         if (flx) jg = mirror_slot<DIM>(0, jg);
@@ -223,41 +239,131 @@ __global__ void __launch_bounds__(256) collide(const Args a) {
 #pragma unroll
         for (int c = 0; c < NF; ++c) r.fs(j, c, i) = keep * fj[c] + omega * feq[c];
       }
-      r.frac(0, i) = q.f0;
-      if (DIM == 2) r.frac(1, i) = q.f1;
+      // corner weights as products of (1 - f, f) per axis (eqs 28-29)
+      const T g0 = T(1) - q.f0;
+      if (DIM == 1) {
+        r.wt(0, i) = g0;
+        r.wt(1, i) = q.f0;
+      } else {
+        const T g1 = T(1) - q.f1;
+        r.wt(0, i) = g0 * g1;
+        r.wt(1, i) = q.f0 * g1;
+        r.wt(2, i) = g0 * q.f1;
+        r.wt(3, i) = q.f0 * q.f1;
+      }
       w = s64_word(q.c1, q.n0, q.n1);
     }
     r.word[i] = w;
   }
-  flag_warp(a.scr, clamps, bad, rmax);
+  flag_warp(a.scr, a.rs, clamps, bad, rmax);
 }
 
-// Gather of every destination's slots from the records.  A reach beyond
-// the records' padding leaves the state as it was (copied through) and
-// flags LBM_EREACH.
+// Type of a source word as one comparable key: c1, n_x, n_y (c1 = 0xffff:
+// the source emits nothing).
+__device__ __forceinline__ unsigned long long word_key(long long w) {
+  return (unsigned long long)w & 0xffffffffffffull;
+}
+__device__ __forceinline__ void decode(long long w, int* c1, int* n0,
+                                       int* n1) {
+  *c1 = (short)(w & 0xffff);
+  *n0 = (short)((w >> 16) & 0xffff);
+  *n1 = (short)((w >> 32) & 0xffff);
+}
+
+// Gather of every destination's slots from the records (a 256-node row
+// segment in 1-D, a 32 x 8 tile in 2-D per block).  A reach beyond the
+// records' padding leaves the state as it was (copied through) and flags
+// LBM_EREACH.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) gather(const Args a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
+    gather(const Args a) {
   constexpr int NP = Shape<DIM>::NP, NF = Shape<DIM>::NF;
+  constexpr int NK = DIM == 1 ? 2 : 4;
+  constexpr int TXB = DIM == 1 ? 256 : 32, TYB = DIM == 1 ? 1 : 8;
+  __shared__ unsigned long long red_lo[8], red_hi[8];
   const RecView<T, DIM> r = rec_view<T, DIM>(a);
   const T* fin = static_cast<const T*>(a.f);
   T* fo = static_cast<T*>(a.fo);
-  const int R = a.scr->reach_next;
-  int dx, dy;
-  if (DIM == 1) {
-    dx = blockIdx.x * blockDim.x + threadIdx.x;
-    dy = 0;
-  } else {
-    dx = blockIdx.x * 32 + (threadIdx.x & 31);
-    dy = blockIdx.y * 8 + (threadIdx.x >> 5);
-  }
-  if (dx >= a.nx || dy >= a.ny) return;
+  const int R = *reach_slot(a.scr, a.rs);
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    *reach_slot(a.scr, a.rs ^ 1) = 0;
+  const int x0 = blockIdx.x * TXB, y0 = DIM == 2 ? blockIdx.y * TYB : 0;
+  const int dx = x0 + (DIM == 1 ? threadIdx.x : (threadIdx.x & 31));
+  const int dy = DIM == 2 ? y0 + (threadIdx.x >> 5) : 0;
+  const bool valid = dx < a.nx && dy < a.ny;
   const long long d = (long long)dy * a.nx + dx;
-  if (R > a.rc) {
+  if (R > a.rc) {  // the same for every thread of the launch
+    if (!valid) return;
     if (d == 0) atomicOr(&a.scr->flags, kFlagReach);
     for (int q = 0; q < NP * NF; ++q) fo[q * a.n + d] = fin[q * a.n + d];
     return;
   }
   const long long PX = (long long)a.nx + 2 * a.rc;
+  auto src_index = [&](int sx, int sy) -> long long {
+    return DIM == 2 ? (long long)(sy + a.rc) * PX + (sx + a.rc)
+                    : (long long)(sx + a.rc);
+  };
+  // does the window of the block's destinations hold one type only?
+  const int W = min(TXB, a.nx - x0) + 2 * R;
+  const int H = DIM == 2 ? min(TYB, a.ny - y0) + 2 * R : 1;
+  unsigned long long lo = ~0ull, hi = 0ull;
+  for (int t = threadIdx.x; t < W * H; t += 256) {
+    const int ly = t / W, lx = t - ly * W;
+    const unsigned long long k =
+        word_key(r.word[src_index(x0 - R + lx, y0 - (DIM == 2 ? R : 0) + ly)]);
+    lo = k < lo ? k : lo;
+    hi = k > hi ? k : hi;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    const unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    lo = l2 < lo ? l2 : lo;
+    hi = h2 > hi ? h2 : hi;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red_lo[threadIdx.x >> 5] = lo;
+    red_hi[threadIdx.x >> 5] = hi;
+  }
+  __syncthreads();
+  lo = red_lo[0];
+  hi = red_hi[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) {
+    lo = red_lo[w] < lo ? red_lo[w] : lo;
+    hi = red_hi[w] > hi ? red_hi[w] : hi;
+  }
+  if (!valid) return;
+  int c1, n0, n1;
+  decode((long long)lo, &c1, &n0, &n1);
+  if (lo == hi && c1 >= 0) {
+    // one type: slot j's arrivals come from the four sources d - n - c'_j
+    // - k, in ascending source order corners (1,1), (0,1), (1,0), (0,0)
+    // (1-D: 1, 0)
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      int cx, cy, lev;
+      packet<DIM>(j, c1, &cx, &cy, &lev);
+      T acc[NF];
+#pragma unroll
+      for (int c = 0; c < NF; ++c) acc[c] = T(0);
+#pragma unroll
+      for (int kk = 0; kk < NK; ++kk) {
+        const int k = NK - 1 - kk;
+        const int sx = dx - n0 - cx - (k & 1);
+        const int sy = DIM == 2 ? dy - n1 - cy - (k >> 1) : 0;
+        const long long i = src_index(sx, sy);
+        const T al = r.wt(k, i);
+#pragma unroll
+        for (int c = 0; c < NF; ++c) acc[c] = acc[c] + al * r.fs(j, c, i);
+      }
+#pragma unroll
+      for (int c = 0; c < NF; ++c)
+        fo[(long long)(j * NF + c) * a.n + d] = acc[c];
+    }
+    return;
+  }
+  // several types: every source of the window tested once
   const int Ry = DIM == 2 ? R : 0;
   T acc[NP][NF];
 #pragma unroll
@@ -265,36 +371,28 @@ __global__ void __launch_bounds__(256) gather(const Args a) {
 #pragma unroll
     for (int c = 0; c < NF; ++c) acc[j][c] = T(0);
   for (int oyo = -Ry; oyo <= Ry; ++oyo) {
-    const int sy = dy + oyo;
-    const long long row = DIM == 2 ? (long long)(sy + a.rc) * PX : 0;
     for (int oxo = -R; oxo <= R; ++oxo) {
-      const int sx = dx + oxo;
-      const long long i = row + sx + a.rc;
-      int c1, n0, n1;
-      const long long w = r.word[i];
-      c1 = (short)(w & 0xffff);
-      n0 = (short)((w >> 16) & 0xffff);
-      n1 = (short)((w >> 32) & 0xffff);
-      if (c1 < 0) continue;
-      // destination relative to the source's lattice shift
-      const int ox = -oxo - n0;
-      const int oy = DIM == 2 ? -oyo - n1 : 0;
-      const int c2 = c1 + 1;
-      if (ox < -c2 || ox > c2 + 1 || oy < -c2 || oy > c2 + 1) continue;
-      // split weights (1 - f, f) per axis (eqs 28-29)
-      const T f0 = r.frac(0, i);
-      const T g0 = T(1) - f0;
-      const T f1 = DIM == 2 ? r.frac(1, i) : T(0);
-      const T g1 = T(1) - f1;
+      const long long i = src_index(dx + oxo, dy + oyo);
+      int sc1, sn0, sn1;
+      decode(r.word[i], &sc1, &sn0, &sn1);
+      if (sc1 < 0) continue;
+      // destination relative to the source's lattice shift: an arrival
+      // needs offset 0 or 1 across the packet's axis
+      const int ox = -oxo - sn0;
+      const int oy = DIM == 2 ? -oyo - sn1 : 0;
+      const int c2 = sc1 + 1;
+      const bool xarm = (oy == 0 || oy == 1) && ox >= -c2 && ox <= c2 + 1;
+      const bool yarm = DIM == 2 && (ox == 0 || ox == 1) && oy >= -c2 &&
+                        oy <= c2 + 1;
+      if (!xarm && !yarm) continue;
 #pragma unroll
       for (int j = 0; j < NP; ++j) {
         int cx, cy, lev;
-        packet<DIM>(j, c1, &cx, &cy, &lev);
+        packet<DIM>(j, sc1, &cx, &cy, &lev);
         const int kx = ox - cx, ky = oy - cy;
         if (kx < 0 || kx > 1) continue;
         if (DIM == 2 && (ky < 0 || ky > 1)) continue;
-        const T ax = kx ? f0 : g0;
-        const T al = DIM == 1 ? ax : ax * (ky ? f1 : g1);
+        const T al = r.wt(kx + 2 * ky, i);
 #pragma unroll
         for (int c = 0; c < NF; ++c) acc[j][c] = acc[j][c] + al * r.fs(j, c, i);
       }
@@ -442,6 +540,7 @@ bgk::Args args_of(const lbm_bgk* h) {
   a.keep_f = (float)a.keep;
   a.k = h->k;
   a.scr = h->scr;
+  a.rs = 0;
   return a;
 }
 
@@ -728,9 +827,8 @@ lbm_status lbm_bgk_step(lbm_bgk* h, int64_t nsteps) {
   if (st != LBM_OK) return st;
   if (nsteps < 0) return bfail(h, LBM_EINVAL, "lbm_bgk_step: nsteps < 0");
   for (int64_t s = 0; s < nsteps; ++s) {
-    const bgk::Args a = args_of(h);
-    BGK_CUDA(h, cudaMemsetAsync(&h->scr->reach_next, 0, sizeof(int), h->stream),
-             "reach clear");
+    bgk::Args a = args_of(h);
+    a.rs = (int)(h->steps & 1);
     BGK_CUDA(h, bgk_launch_step(h, a), "step kernels");
     h->cur ^= 1;
     h->steps += 1;
@@ -790,7 +888,8 @@ lbm_status lbm_bgk_diagnostics(lbm_bgk* h, int64_t* steps, int64_t* eclamps,
   if (e != cudaSuccess) return bcuda(h, e, "diagnostics");
   if (steps) *steps = h->steps;
   if (eclamps) *eclamps = (int64_t)s.eclamps;
-  if (reach) *reach = s.reach_next;
+  // the slot of the last step (both are 0 before the first)
+  if (reach) *reach = (h->steps & 1) ? s.reach : s.reach_next;
   if (flags) *flags = s.flags;
   return LBM_OK;
 }
