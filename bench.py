@@ -639,8 +639,8 @@ def run_bgk2d(args):
     its per-packet state: the periodic cylinder of Section V.C on a 2048 x
     2048 grid (circle r < 0.4 about the centre, inner (1, 0, 0, 1), outer
     (0.125, 0, 0, 0.1)), tau = --tau, FP32.  K steps after W warm-up steps,
-    timed as one block with CUDA events around lbm_bgk_step (its collision
-    and gather kernels); the state, 537 MB per packet set, is larger than
+    timed as one block with CUDA events around lbm_bgk_step (max_reach 4:
+    one launch per step); the state, 537 MB per packet set, is larger than
     L2.  Algorithmic bytes: 8 slots x 4 fields x 4 bytes read and written,
     256 B per node update."""
     import torch
@@ -649,9 +649,13 @@ def run_bgk2d(args):
     stream = torch.cuda.Stream()
     n = BGK_N
     K = args.steps if args.steps > 0 else 100
+    # max_reach 4: the one-launch step (window collided in shared memory);
+    # --bgk-max-reach 6 takes the collision and gather kernels
     cfg = L.make_config(2, n, n, dt=1.0 / n, precision=L.F32,
                         bc_x=L.PERIODIC, bc_y=L.PERIODIC,
+                        max_reach=args.bgk_max_reach,
                         stream=stream.cuda_stream)
+    one = args.bgk_max_reach <= 4
     with L.Bgk(cfg, args.tau) as g, torch.cuda.stream(stream):
         g.init_riemann((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1),
                        L.CIRCLE, 0.5, 0.5, 0.4)
@@ -683,6 +687,7 @@ def run_bgk2d(args):
                     "states)",
             "config": {"workload": f"bgk_cylinder_2d_{n}x{n}_periodic",
                        "tau": args.tau, "nx": n, "ny": n,
+                       "max_reach": args.bgk_max_reach,
                        "timed": f"steps {args.warmup + 1}-{args.warmup + K}",
                        "l2": "state (537 MB per packet set) larger than L2; "
                              "no flush"},
@@ -691,9 +696,11 @@ def run_bgk2d(args):
                          "frac": round(achieved / peak, 4),
                          "peak_kind": peak_kind,
                          "bytes_per_node_update": 256,
-                         "duration": "CUDA events around lbm_bgk_step: the "
-                                     "collision and gather kernels"},
-            "gpu_launches": 2 * K,
+                         "kernel": ("lbm::bgk::step2d<float>" if one else
+                                    "lbm::bgk::collide<float,2> + "
+                                    "gather<float,2>"),
+                         "duration": "CUDA events around lbm_bgk_step"},
+            "gpu_launches": (1 if one else 2) * K,
             "conservation_drift": drift,
             "end_state": diag, "clocks": clk}
 
@@ -1030,6 +1037,8 @@ def main():
                                                  "bgk2d"])
     ap.add_argument("--tau", type=float, default=1.5,
                     help="bgk2d: relaxation time (eqs 4-5)")
+    ap.add_argument("--bgk-max-reach", type=int, default=4,
+                    help="bgk2d: reach limit (<= 4: one-launch step)")
     ap.add_argument("--repeats", type=int, default=100,
                     help="sod1d: solves timed")
     ap.add_argument("--requests", type=int, default=2000)

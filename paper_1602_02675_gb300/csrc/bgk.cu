@@ -61,7 +61,8 @@ struct Args {
   float omega_f, keep_f;  // the same rounded to FP32 on the host
   EqConst k;
   Scratch* scr;
-  int rs;  // reach slot of this step: scr->reach (0) or scr->reach_next (1)
+  int rs;      // reach slot of this step (see reach_slot / step2d)
+  int* rslot;  // one-launch step: three reach slots
 };
 
 // The two reach slots alternate between steps: the collision of a step
@@ -184,15 +185,122 @@ __device__ __forceinline__ void flag_warp(Scratch* scr, int rs,
   }
 }
 
+// Collision of one source (sx, sy) into entry i of a record view (the
+// padded grid's records, or a window in shared memory): the supplying
+// node's moments (eq 6; across a reflecting wall its normal momentum
+// negated), its equilibrium, the blend per slot, the corner weights and the
+// word.  `owned`: the source is a node of the grid counted by this thread
+// (clamps, bad state, reach).
+// REGS: the node's slots stay in registers from the moments to the blend
+// (one round of loads; the one-launch step, whose window sources miss L1);
+// otherwise each slot is read again at its blend (fewer registers; the
+// collision kernel, whose re-reads hit L1).
+template <typename T, int DIM, bool REGS>
+__device__ __forceinline__ void collide_one(const Args& a, const T* f,
+                                            long long sx, long long sy,
+                                            bool owned,
+                                            const RecView<T, DIM>& r,
+                                            long long i,
+                                            unsigned long long& clamps,
+                                            bool& bad, int& rmax) {
+  constexpr int NP = Shape<DIM>::NP, NF = Shape<DIM>::NF;
+  const T omega = rel_const<T>(a.omega, a.omega_f);
+  const T keep = rel_const<T>(a.keep, a.keep_f);
+  bool flx = false, fly = false;
+  const int gx = virtual_axis(a.bc_x, a.nx, sx, &flx);
+  const int gy = DIM == 2 ? virtual_axis(a.bc_y, a.ny, sy, &fly) : 0;
+  const long long g = (long long)gy * a.nx + gx;
+  // the node's moments, slots summed in table order
+  T fa[NP][NF];
+  T Y[4] = {T(0), T(0), T(0), T(0)};
+  if (REGS) {
+#pragma unroll
+    for (int j = 0; j < NP; ++j)
+#pragma unroll
+      for (int c = 0; c < NF; ++c)
+        fa[j][c] = f[(long long)(j * NF + c) * a.n + g];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      Y[0] = Y[0] + fa[j][0];
+      Y[1] = Y[1] + fa[j][1];
+      if (DIM == 2) Y[2] = Y[2] + fa[j][2];
+      Y[3] = Y[3] + fa[j][NF - 1];
+    }
+  } else {
+    node_moments<T, DIM>(f, a.n, g, Y);
+  }
+  if (flx) Y[1] = -Y[1];
+  if (fly) Y[2] = -Y[2];
+  const Equil<T> q = equilibrium<T, DIM>(Y[0], Y[1], Y[2], Y[3], a.k);
+  if (owned) {
+    clamps += q.clamp ? 1 : 0;
+    bad |= q.bad;
+    rmax = max(rmax, node_reach(q));
+  }
+  long long w = s64_word(-1, 0, 0);
+  if (q.emits && REGS) {
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      // the node's slot this source's slot j mirrors (compile-time slots,
+      // chosen by the flips)
+      const int jx = mirror_slot<DIM>(0, j), jy = mirror_slot<DIM>(1, j);
+      const int jxy = mirror_slot<DIM>(1, jx);
+      T fj[NF];
+#pragma unroll
+      for (int c = 0; c < NF; ++c)
+        fj[c] = flx ? (fly ? fa[jxy][c] : fa[jx][c])
+                    : (fly ? fa[jy][c] : fa[j][c]);
+      if (flx) fj[1] = -fj[1];
+      if (DIM == 2 && fly) fj[2] = -fj[2];
+      T feq[NF];
+      eq_packet<T, DIM>(q, j, feq);
+      // eqs 4-5 as the blend (1 - 1/tau) f + (1/tau) f_eq
+#pragma unroll
+      for (int c = 0; c < NF; ++c) r.fs(j, c, i) = keep * fj[c] + omega * feq[c];
+    }
+  } else if (q.emits) {
+#pragma unroll 1
+    for (int j = 0; j < NP; ++j) {
+      int jg = j;
+      if (flx) jg = mirror_slot<DIM>(0, jg);
+      if (fly) jg = mirror_slot<DIM>(1, jg);
+      T fj[NF];
+#pragma unroll
+      for (int c = 0; c < NF; ++c)
+        fj[c] = f[(long long)(jg * NF + c) * a.n + g];
+      if (flx) fj[1] = -fj[1];
+      if (DIM == 2 && fly) fj[2] = -fj[2];
+      T feq[NF];
+      eq_packet<T, DIM>(q, j, feq);
+      // eqs 4-5 as the blend (1 - 1/tau) f + (1/tau) f_eq
+#pragma unroll
+      for (int c = 0; c < NF; ++c) r.fs(j, c, i) = keep * fj[c] + omega * feq[c];
+    }
+  }
+  if (q.emits) {
+    // corner weights as products of (1 - f, f) per axis (eqs 28-29)
+    const T g0 = T(1) - q.f0;
+    if (DIM == 1) {
+      r.wt(0, i) = g0;
+      r.wt(1, i) = q.f0;
+    } else {
+      const T g1 = T(1) - q.f1;
+      r.wt(0, i) = g0 * g1;
+      r.wt(1, i) = q.f0 * g1;
+      r.wt(2, i) = g0 * q.f1;
+      r.wt(3, i) = q.f0 * q.f1;
+    }
+    w = s64_word(q.c1, q.n0, q.n1);
+  }
+  r.word[i] = w;
+}
+
 // Collision of every source of the padded grid into the records.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
     collide(const Args a) {
-  constexpr int NP = Shape<DIM>::NP, NF = Shape<DIM>::NF;
   const RecView<T, DIM> r = rec_view<T, DIM>(a);
   const T* f = static_cast<const T*>(a.f);
-  const T omega = rel_const<T>(a.omega, a.omega_f);
-  const T keep = rel_const<T>(a.keep, a.keep_f);
   const long long PX = (long long)a.nx + 2 * a.rc;
   const long long PY = DIM == 2 ? (long long)a.ny + 2 * a.rc : 1;
   unsigned long long clamps = 0;
@@ -201,59 +309,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
   const long long px = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   for (long long py = blockIdx.y; py < PY && px < PX; py += gridDim.y) {
     const long long sx = px - a.rc, sy = DIM == 2 ? py - a.rc : 0;
-    bool flx = false, fly = false;
-    const int gx = virtual_axis(a.bc_x, a.nx, sx, &flx);
-    const int gy = DIM == 2 ? virtual_axis(a.bc_y, a.ny, sy, &fly) : 0;
-    const long long g = (long long)gy * a.nx + gx;
-    // the supplying node's moments (eq 6); across a reflecting wall its
-    // normal momentum negated
-    T Y[4];
-    node_moments<T, DIM>(f, a.n, g, Y);
-    if (flx) Y[1] = -Y[1];
-    if (fly) Y[2] = -Y[2];
-    const Equil<T> q = equilibrium<T, DIM>(Y[0], Y[1], Y[2], Y[3], a.k);
-    if (sx >= 0 && sx < a.nx && sy >= 0 && sy < a.ny) {
-      clamps += q.clamp ? 1 : 0;
-      bad |= q.bad;
-      rmax = max(rmax, node_reach(q));
-    }
-    const long long i = py * PX + px;
-    long long w = s64_word(-1, 0, 0);
-    if (q.emits) {
-      // (a rolled loop: the slot's fields are read again here rather than
-      // kept in registers from the moments)
-#pragma unroll 1
-      for (int j = 0; j < NP; ++j) {
-        int jg = j;
-        if (flx) jg = mirror_slot<DIM>(0, jg);
-        if (fly) jg = mirror_slot<DIM>(1, jg);
-        T fj[NF];
-#pragma unroll
-        for (int c = 0; c < NF; ++c)
-          fj[c] = f[(long long)(jg * NF + c) * a.n + g];
-        if (flx) fj[1] = -fj[1];
-        if (DIM == 2 && fly) fj[2] = -fj[2];
-        T feq[NF];
-        eq_packet<T, DIM>(q, j, feq);
-        // eqs 4-5 as the blend (1 - 1/tau) f + (1/tau) f_eq
-#pragma unroll
-        for (int c = 0; c < NF; ++c) r.fs(j, c, i) = keep * fj[c] + omega * feq[c];
-      }
-      // corner weights as products of (1 - f, f) per axis (eqs 28-29)
-      const T g0 = T(1) - q.f0;
-      if (DIM == 1) {
-        r.wt(0, i) = g0;
-        r.wt(1, i) = q.f0;
-      } else {
-        const T g1 = T(1) - q.f1;
-        r.wt(0, i) = g0 * g1;
-        r.wt(1, i) = q.f0 * g1;
-        r.wt(2, i) = g0 * q.f1;
-        r.wt(3, i) = q.f0 * q.f1;
-      }
-      w = s64_word(q.c1, q.n0, q.n1);
-    }
-    r.word[i] = w;
+    const bool owned = sx >= 0 && sx < a.nx && sy >= 0 && sy < a.ny;
+    collide_one<T, DIM, false>(a, f, sx, sy, owned, r, py * PX + px, clamps,
+                               bad, rmax);
   }
   flag_warp(a.scr, a.rs, clamps, bad, rmax);
 }
@@ -270,76 +328,21 @@ __device__ __forceinline__ void decode(long long w, int* c1, int* n0,
   *n1 = (short)((w >> 32) & 0xffff);
 }
 
-// Gather of every destination's slots from the records (a 256-node row
-// segment in 1-D, a 32 x 8 tile in 2-D per block).  A reach beyond the
-// records' padding leaves the state as it was (copied through) and flags
-// LBM_EREACH.
-template <typename T, int DIM>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
-    gather(const Args a) {
+// Slots of destination (dx, dy) from a record view; idx(sx, sy) gives a
+// source's entry.  one: every source the destination can receive from
+// has type (c1, n0, n1) and emits; then slot j's arrivals come from the
+// four sources d - n - c'_j - k, in ascending source order corners (1,1),
+// (0,1), (1,0), (0,0) (1-D: 1, 0).  Otherwise every source of the (2R +
+// 1)^D window is tested once, all slots' sums in registers.  emit(j, v)
+// receives the slots in table order.
+template <typename T, int DIM, class Idx, class Emit>
+__device__ __forceinline__ void gather_one(const RecView<T, DIM>& r, Idx idx,
+                                           int dx, int dy, int R, bool one,
+                                           int c1, int n0, int n1,
+                                           Emit emit) {
   constexpr int NP = Shape<DIM>::NP, NF = Shape<DIM>::NF;
   constexpr int NK = DIM == 1 ? 2 : 4;
-  constexpr int TXB = DIM == 1 ? 256 : 32, TYB = DIM == 1 ? 1 : 8;
-  __shared__ unsigned long long red_lo[8], red_hi[8];
-  const RecView<T, DIM> r = rec_view<T, DIM>(a);
-  const T* fin = static_cast<const T*>(a.f);
-  T* fo = static_cast<T*>(a.fo);
-  const int R = *reach_slot(a.scr, a.rs);
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
-    *reach_slot(a.scr, a.rs ^ 1) = 0;
-  const int x0 = blockIdx.x * TXB, y0 = DIM == 2 ? blockIdx.y * TYB : 0;
-  const int dx = x0 + (DIM == 1 ? threadIdx.x : (threadIdx.x & 31));
-  const int dy = DIM == 2 ? y0 + (threadIdx.x >> 5) : 0;
-  const bool valid = dx < a.nx && dy < a.ny;
-  const long long d = (long long)dy * a.nx + dx;
-  if (R > a.rc) {  // the same for every thread of the launch
-    if (!valid) return;
-    if (d == 0) atomicOr(&a.scr->flags, kFlagReach);
-    for (int q = 0; q < NP * NF; ++q) fo[q * a.n + d] = fin[q * a.n + d];
-    return;
-  }
-  const long long PX = (long long)a.nx + 2 * a.rc;
-  auto src_index = [&](int sx, int sy) -> long long {
-    return DIM == 2 ? (long long)(sy + a.rc) * PX + (sx + a.rc)
-                    : (long long)(sx + a.rc);
-  };
-  // does the window of the block's destinations hold one type only?
-  const int W = min(TXB, a.nx - x0) + 2 * R;
-  const int H = DIM == 2 ? min(TYB, a.ny - y0) + 2 * R : 1;
-  unsigned long long lo = ~0ull, hi = 0ull;
-  for (int t = threadIdx.x; t < W * H; t += 256) {
-    const int ly = t / W, lx = t - ly * W;
-    const unsigned long long k =
-        word_key(r.word[src_index(x0 - R + lx, y0 - (DIM == 2 ? R : 0) + ly)]);
-    lo = k < lo ? k : lo;
-    hi = k > hi ? k : hi;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-    const unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-    lo = l2 < lo ? l2 : lo;
-    hi = h2 > hi ? h2 : hi;
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red_lo[threadIdx.x >> 5] = lo;
-    red_hi[threadIdx.x >> 5] = hi;
-  }
-  __syncthreads();
-  lo = red_lo[0];
-  hi = red_hi[0];
-#pragma unroll
-  for (int w = 1; w < 8; ++w) {
-    lo = red_lo[w] < lo ? red_lo[w] : lo;
-    hi = red_hi[w] > hi ? red_hi[w] : hi;
-  }
-  if (!valid) return;
-  int c1, n0, n1;
-  decode((long long)lo, &c1, &n0, &n1);
-  if (lo == hi && c1 >= 0) {
-    // one type: slot j's arrivals come from the four sources d - n - c'_j
-    // - k, in ascending source order corners (1,1), (0,1), (1,0), (0,0)
-    // (1-D: 1, 0)
+  if (one) {
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
       int cx, cy, lev;
@@ -350,20 +353,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
       for (int kk = 0; kk < NK; ++kk) {
         const int k = NK - 1 - kk;
-        const int sx = dx - n0 - cx - (k & 1);
-        const int sy = DIM == 2 ? dy - n1 - cy - (k >> 1) : 0;
-        const long long i = src_index(sx, sy);
+        const long long i = idx(dx - n0 - cx - (k & 1),
+                                DIM == 2 ? dy - n1 - cy - (k >> 1) : 0);
         const T al = r.wt(k, i);
 #pragma unroll
         for (int c = 0; c < NF; ++c) acc[c] = acc[c] + al * r.fs(j, c, i);
       }
-#pragma unroll
-      for (int c = 0; c < NF; ++c)
-        fo[(long long)(j * NF + c) * a.n + d] = acc[c];
+      emit(j, acc);
     }
     return;
   }
-  // several types: every source of the window tested once
   const int Ry = DIM == 2 ? R : 0;
   T acc[NP][NF];
 #pragma unroll
@@ -372,7 +371,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
     for (int c = 0; c < NF; ++c) acc[j][c] = T(0);
   for (int oyo = -Ry; oyo <= Ry; ++oyo) {
     for (int oxo = -R; oxo <= R; ++oxo) {
-      const long long i = src_index(dx + oxo, dy + oyo);
+      const long long i = idx(dx + oxo, dy + oyo);
       int sc1, sn0, sn1;
       decode(r.word[i], &sc1, &sn0, &sn1);
       if (sc1 < 0) continue;
@@ -399,9 +398,197 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
     }
   }
 #pragma unroll
-  for (int j = 0; j < NP; ++j)
+  for (int j = 0; j < NP; ++j) emit(j, acc[j]);
+}
+
+// Smallest and largest word key over a block (every thread gets them; one
+// barrier).
+__device__ __forceinline__ void block_key_range(unsigned long long& lo,
+                                                unsigned long long& hi,
+                                                unsigned long long* red) {
 #pragma unroll
-    for (int c = 0; c < NF; ++c) fo[(long long)(j * NF + c) * a.n + d] = acc[j][c];
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    const unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    lo = l2 < lo ? l2 : lo;
+    hi = h2 > hi ? h2 : hi;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = lo;
+    red[8 + (threadIdx.x >> 5)] = hi;
+  }
+  __syncthreads();
+  lo = red[0];
+  hi = red[8];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) {
+    lo = red[w] < lo ? red[w] : lo;
+    hi = red[8 + w] > hi ? red[8 + w] : hi;
+  }
+}
+
+// Gather of every destination's slots from the records (a 256-node row
+// segment in 1-D, a 32 x 8 tile in 2-D per block).  A reach beyond the
+// records' padding leaves the state as it was (copied through) and flags
+// LBM_EREACH.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
+    gather(const Args a) {
+  constexpr int NP = Shape<DIM>::NP, NF = Shape<DIM>::NF;
+  constexpr int TXB = DIM == 1 ? 256 : 32, TYB = DIM == 1 ? 1 : 8;
+  __shared__ unsigned long long red[16];
+  const RecView<T, DIM> r = rec_view<T, DIM>(a);
+  const T* fin = static_cast<const T*>(a.f);
+  T* fo = static_cast<T*>(a.fo);
+  const int R = *reach_slot(a.scr, a.rs);
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    *reach_slot(a.scr, a.rs ^ 1) = 0;
+  const int x0 = blockIdx.x * TXB, y0 = DIM == 2 ? blockIdx.y * TYB : 0;
+  const int dx = x0 + (DIM == 1 ? threadIdx.x : (threadIdx.x & 31));
+  const int dy = DIM == 2 ? y0 + (threadIdx.x >> 5) : 0;
+  const bool valid = dx < a.nx && dy < a.ny;
+  const long long d = (long long)dy * a.nx + dx;
+  if (R > a.rc) {  // the same for every thread of the launch
+    if (!valid) return;
+    if (d == 0) atomicOr(&a.scr->flags, kFlagReach);
+    for (int q = 0; q < NP * NF; ++q) fo[q * a.n + d] = fin[q * a.n + d];
+    return;
+  }
+  const long long PX = (long long)a.nx + 2 * a.rc;
+  const int rc = a.rc;
+  auto idx = [PX, rc](int sx, int sy) -> long long {
+    return DIM == 2 ? (long long)(sy + rc) * PX + (sx + rc)
+                    : (long long)(sx + rc);
+  };
+  // does the window of the block's destinations hold one type only?
+  const int W = min(TXB, a.nx - x0) + 2 * R;
+  const int H = DIM == 2 ? min(TYB, a.ny - y0) + 2 * R : 1;
+  unsigned long long lo = ~0ull, hi = 0ull;
+  for (int t = threadIdx.x; t < W * H; t += 256) {
+    const int ly = t / W, lx = t - ly * W;
+    const unsigned long long k =
+        word_key(r.word[idx(x0 - R + lx, y0 - (DIM == 2 ? R : 0) + ly)]);
+    lo = k < lo ? k : lo;
+    hi = k > hi ? k : hi;
+  }
+  block_key_range(lo, hi, red);
+  if (!valid) return;
+  int c1, n0, n1;
+  decode((long long)lo, &c1, &n0, &n1);
+  gather_one<T, DIM>(r, idx, dx, dy, R, lo == hi && c1 >= 0, c1, n0, n1,
+                     [&](int j, const T (&v)[NF]) {
+#pragma unroll
+                       for (int c = 0; c < NF; ++c)
+                         fo[(long long)(j * NF + c) * a.n + d] = v[c];
+                     });
+}
+
+// Shared memory of the one-launch step (step2d): the collided window of a
+// 32 x 8 tile at reach limit rc, (32 + 2 rc) x (8 + 2 rc) sources, each a
+// word, 32 packet fields and 4 corner weights.
+inline size_t step2d_smem(int rc, size_t es) {
+  return (size_t)(32 + 2 * rc) * (size_t)(8 + 2 * rc) * (8 + 36 * es);
+}
+// Largest reach limit the one-launch step takes (two blocks per
+// multiprocessor in FP32).
+constexpr int kStep2dRmax = 4;
+
+// Reach of every node of the state (the first step of the one-launch path
+// reads it): into slot rs of the three a step rotates through.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) reach_pass(const Args a) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int rm = 0;
+  if (i < a.n) {
+    T Y[4];
+    node_moments<T, DIM>(static_cast<const T*>(a.f), a.n, i, Y);
+    rm = node_reach(equilibrium<T, DIM>(Y[0], Y[1], Y[2], Y[3], a.k));
+  }
+  rm = __reduce_max_sync(0xffffffffu, rm);
+  if ((threadIdx.x & 31) == 0 && rm) atomicMax(&a.rslot[a.rs], rm);
+}
+
+// One-launch square-lattice step: each block collides the sources of its
+// tile's window into shared memory (the same values collide() writes), then
+// gathers its destinations (the same sums, in the same order, as gather()),
+// and forms the new nodes' reach for the next step.  The reach rotates
+// through three slots: step s reads slot s % 3, max-reduces the next
+// state's reach into slot (s + 1) % 3 and clears slot (s + 2) % 3, which
+// the previous step read.
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
+    step2d(const Args a) {
+  constexpr int NP = 8, NF = 4;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long red[16];
+  const int rc = a.rc;
+  const int WM = (32 + 2 * rc) * (8 + 2 * rc);
+  RecView<T, 2> r;
+  r.cap = WM;
+  r.word = reinterpret_cast<long long*>(smem);
+  r.v = reinterpret_cast<T*>(r.word + WM);
+  const T* fin = static_cast<const T*>(a.f);
+  T* fo = static_cast<T*>(a.fo);
+  const int rs = a.rs;
+  const int R = a.rslot[rs];
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    a.rslot[(rs + 2) % 3] = 0;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
+  const int dx = x0 + (threadIdx.x & 31), dy = y0 + (threadIdx.x >> 5);
+  const bool valid = dx < a.nx && dy < a.ny;
+  const long long d = (long long)dy * a.nx + dx;
+  if (R > rc) {  // the same for every thread of the launch
+    if (!valid) return;
+    if (d == 0) atomicOr(&a.scr->flags, kFlagReach);
+    for (int q = 0; q < NP * NF; ++q) fo[q * a.n + d] = fin[q * a.n + d];
+    return;
+  }
+  // the window, collided into shared memory
+  const int W = 32 + 2 * R, H = 8 + 2 * R;
+  unsigned long long clamps = 0, lo = ~0ull, hi = 0ull;
+  bool bad = false;
+  int rdummy = 0;
+  for (int t = threadIdx.x; t < W * H; t += 256) {
+    const int ly = t / W, lx = t - ly * W;
+    const int sx = x0 - R + lx, sy = y0 - R + ly;
+    const bool owned = lx >= R && lx < R + 32 && ly >= R && ly < R + 8 &&
+                       sx < a.nx && sy < a.ny;
+    collide_one<T, 2, true>(a, fin, sx, sy, owned, r, t, clamps, bad,
+                            rdummy);
+    const unsigned long long k = word_key(r.word[t]);
+    lo = k < lo ? k : lo;
+    hi = k > hi ? k : hi;
+  }
+  block_key_range(lo, hi, red);  // its barrier also publishes the window
+  int rm = 0;
+  if (valid) {
+    int c1, n0, n1;
+    decode((long long)lo, &c1, &n0, &n1);
+    auto idx = [W, x0, y0, R](int sx, int sy) -> long long {
+      return (long long)(sy - y0 + R) * W + (sx - x0 + R);
+    };
+    // the new node's moments (slots in table order) for its reach
+    T Y[4] = {T(0), T(0), T(0), T(0)};
+    gather_one<T, 2>(r, idx, dx, dy, R, lo == hi && c1 >= 0, c1, n0, n1,
+                     [&](int j, const T (&v)[NF]) {
+#pragma unroll
+                       for (int c = 0; c < NF; ++c)
+                         fo[(long long)(j * NF + c) * a.n + d] = v[c];
+                       Y[0] = Y[0] + v[0];
+                       Y[1] = Y[1] + v[1];
+                       Y[2] = Y[2] + v[2];
+                       Y[3] = Y[3] + v[3];
+                     });
+    rm = node_reach(equilibrium<T, 2>(Y[0], Y[1], Y[2], Y[3], a.k));
+  }
+  const unsigned wc = __reduce_add_sync(0xffffffffu, (unsigned)clamps);
+  const bool wb = __any_sync(0xffffffffu, bad);
+  const int wr = __reduce_max_sync(0xffffffffu, rm);
+  if ((threadIdx.x & 31) == 0) {
+    if (wc) atomicAdd(&a.scr->eclamps, (unsigned long long)wc);
+    if (wb) atomicOr(&a.scr->flags, kFlagState);
+    if (wr) atomicMax(&a.rslot[(rs + 1) % 3], wr);
+  }
 }
 
 // Moments of every node (eq 6) into the moments buffer.
@@ -482,7 +669,10 @@ struct lbm_bgk {
   void* f[2] = {nullptr, nullptr};
   int cur = 0;
   void* mom[4] = {nullptr, nullptr, nullptr, nullptr};
-  void* rec = nullptr;
+  void* rec = nullptr;      // two-kernel step: source records
+  bool one_launch = false;  // 2-D with max_reach <= 4: step2d
+  size_t smem = 0;          // step2d's dynamic shared memory
+  int* rslot = nullptr;     // step2d's three reach slots
   Scratch* scr = nullptr;
   double* part = nullptr;
   int part_cap = 0;
@@ -541,6 +731,7 @@ bgk::Args args_of(const lbm_bgk* h) {
   a.k = h->k;
   a.scr = h->scr;
   a.rs = 0;
+  a.rslot = h->rslot;
   return a;
 }
 
@@ -562,6 +753,14 @@ cudaError_t launch_step_t(const bgk::Args& a, cudaStream_t s) {
 }
 
 cudaError_t bgk_launch_step(const lbm_bgk* h, const bgk::Args& a) {
+  if (h->one_launch) {
+    dim3 gg((unsigned)((a.nx + 31) / 32), (unsigned)((a.ny + 7) / 8));
+    if (h->f64)
+      bgk::step2d<double><<<gg, 256, h->smem, h->stream>>>(a);
+    else
+      bgk::step2d<float><<<gg, 256, h->smem, h->stream>>>(a);
+    return cudaGetLastError();
+  }
   if (h->f64)
     return h->dim == 1 ? launch_step_t<double, 1>(a, h->stream)
                        : launch_step_t<double, 2>(a, h->stream);
@@ -614,13 +813,29 @@ lbm_status bcheck_flags(lbm_bgk* h) {
   return LBM_OK;
 }
 
-// Moments were written into the moments buffer: the packets at equilibrium.
-lbm_status seed_from_moments(lbm_bgk* h) {
+// A new state was set: scratch and step count cleared; the one-launch step
+// needs the state's reach before its first step.
+lbm_status state_was_set(lbm_bgk* h) {
   BGK_CUDA(h, cudaMemsetAsync(h->scr, 0, sizeof(Scratch), h->stream),
            "scratch clear");
-  BGK_CUDA(h, launch_from_moments(h), "equilibrium kernel");
   h->steps = 0;
+  if (h->one_launch) {
+    BGK_CUDA(h, cudaMemsetAsync(h->rslot, 0, 3 * sizeof(int), h->stream),
+             "reach clear");
+    const bgk::Args a = args_of(h);
+    if (h->f64)
+      bgk::reach_pass<double, 2><<<blocks_1d(h->n), 256, 0, h->stream>>>(a);
+    else
+      bgk::reach_pass<float, 2><<<blocks_1d(h->n), 256, 0, h->stream>>>(a);
+    BGK_CUDA(h, cudaGetLastError(), "reach kernel");
+  }
   return LBM_OK;
+}
+
+// Moments were written into the moments buffer: the packets at equilibrium.
+lbm_status seed_from_moments(lbm_bgk* h) {
+  BGK_CUDA(h, launch_from_moments(h), "equilibrium kernel");
+  return state_was_set(h);
 }
 
 }  // namespace
@@ -679,8 +894,28 @@ lbm_status lbm_bgk_create(const lbm_config* cfg, double tau, lbm_bgk** out) {
     if (i == 2 && c.dim == 1) continue;
     ok = cudaMalloc(&h->mom[i], bes(h) * (size_t)h->n) == cudaSuccess;
   }
-  ok = ok && cudaMalloc(&h->rec, bgk::rec_bytes(h->dim, h->nx, h->ny, h->r_cap,
-                                                bes(h))) == cudaSuccess;
+  // 2-D with a reach limit the one-launch step's window takes: no records
+  h->one_launch = c.dim == 2 && h->r_cap <= bgk::kStep2dRmax;
+  if (h->one_launch) {
+    h->smem = bgk::step2d_smem(h->r_cap, bes(h));
+    const cudaError_t ea =
+        h->f64 ? cudaFuncSetAttribute(bgk::step2d<double>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)h->smem)
+               : cudaFuncSetAttribute(bgk::step2d<float>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)h->smem);
+    if (ea != cudaSuccess) {
+      const lbm_status st = bcuda(h, ea, "kernel attribute");
+      lbm_bgk_destroy(h);
+      return st;
+    }
+    ok = ok && cudaMalloc(&h->rslot, 3 * sizeof(int)) == cudaSuccess;
+  } else {
+    ok = ok && cudaMalloc(&h->rec, bgk::rec_bytes(h->dim, h->nx, h->ny,
+                                                  h->r_cap, bes(h))) ==
+                   cudaSuccess;
+  }
   ok = ok && cudaMalloc(&h->scr, sizeof(Scratch)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->part, sizeof(double) * 4 * (size_t)h->part_cap) ==
                  cudaSuccess;
@@ -693,6 +928,7 @@ lbm_status lbm_bgk_create(const lbm_config* cfg, double tau, lbm_bgk** out) {
   }
   for (int b = 0; b < 2; ++b) cudaMemsetAsync(h->f[b], 0, fb, h->stream);
   cudaMemsetAsync(h->scr, 0, sizeof(Scratch), h->stream);
+  if (h->rslot) cudaMemsetAsync(h->rslot, 0, 3 * sizeof(int), h->stream);
   const cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     const lbm_status st = bcuda(h, e, "initial clear");
@@ -789,9 +1025,8 @@ lbm_status lbm_bgk_set_packets(lbm_bgk* h, const double* f, int64_t n) {
           h->staging, static_cast<float*>(h->f[h->cur]) + (size_t)q * n, n, sc);
     BGK_CUDA(h, cudaGetLastError(), "convert kernel");
   }
-  BGK_CUDA(h, cudaMemsetAsync(h->scr, 0, sizeof(Scratch), h->stream),
-           "scratch clear");
-  h->steps = 0;
+  st = state_was_set(h);
+  if (st != LBM_OK) return st;
   BGK_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
   return LBM_OK;
 }
@@ -828,7 +1063,7 @@ lbm_status lbm_bgk_step(lbm_bgk* h, int64_t nsteps) {
   if (nsteps < 0) return bfail(h, LBM_EINVAL, "lbm_bgk_step: nsteps < 0");
   for (int64_t s = 0; s < nsteps; ++s) {
     bgk::Args a = args_of(h);
-    a.rs = (int)(h->steps & 1);
+    a.rs = h->one_launch ? (int)(h->steps % 3) : (int)(h->steps & 1);
     BGK_CUDA(h, bgk_launch_step(h, a), "step kernels");
     h->cur ^= 1;
     h->steps += 1;
@@ -886,10 +1121,20 @@ lbm_status lbm_bgk_diagnostics(lbm_bgk* h, int64_t* steps, int64_t* eclamps,
                                   cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return bcuda(h, e, "diagnostics");
+  int rs[3] = {0, 0, 0};
+  if (h->one_launch) {
+    e = cudaMemcpy(rs, h->rslot, sizeof(rs), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bcuda(h, e, "diagnostics");
+  }
   if (steps) *steps = h->steps;
   if (eclamps) *eclamps = (int64_t)s.eclamps;
-  // the slot of the last step (both are 0 before the first)
-  if (reach) *reach = (h->steps & 1) ? s.reach : s.reach_next;
+  // the slot of the last step (0 before the first)
+  if (reach) {
+    if (h->one_launch)
+      *reach = h->steps > 0 ? rs[(h->steps - 1) % 3] : 0;
+    else
+      *reach = (h->steps & 1) ? s.reach : s.reach_next;
+  }
   if (flags) *flags = s.flags;
   return LBM_OK;
 }
@@ -912,6 +1157,7 @@ void lbm_bgk_destroy(lbm_bgk* h) {
   for (int i = 0; i < 4; ++i)
     if (h->mom[i]) cudaFree(h->mom[i]);
   if (h->rec) cudaFree(h->rec);
+  if (h->rslot) cudaFree(h->rslot);
   if (h->scr) cudaFree(h->scr);
   if (h->part) cudaFree(h->part);
   if (h->staging) cudaFree(h->staging);

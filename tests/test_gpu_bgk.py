@@ -74,12 +74,14 @@ CASES_2D = [
 ]
 
 
+# max_reach 6: collision and gather kernels; 4: the one-launch step
+@pytest.mark.parametrize("max_reach", [6, 4])
 @pytest.mark.parametrize("bcs,shape,tau", CASES_2D)
-def test_bgk_2d_fp64_bitwise(bcs, shape, tau):
+def test_bgk_2d_fp64_bitwise(bcs, shape, tau, max_reach):
     nx, ny = shape
     f0 = random_packets(2, nx * ny, seed=nx * 101 + ny + bcs[0])
     steps = 6
-    with L.Bgk(_cfg(2, nx, ny, *bcs, L.F64), tau) as g:
+    with L.Bgk(_cfg(2, nx, ny, *bcs, L.F64, max_reach=max_reach), tau) as g:
         g.set_packets(f0)
         g.step(steps)
         got = g.packets()
@@ -261,8 +263,9 @@ def test_bgk_benchmark_workload_sampled_fp32():
     half-width max_reach around each (a node's new slots depend only on the
     sources within the step's reach, so the patch's own edges do not reach
     its centre)."""
-    n, tau, H = 2048, 1.5, 6
-    cfg = L.make_config(2, n, n, dt=1.0 / n, precision=L.F32, bc_x=P, bc_y=P)
+    n, tau, H = 2048, 1.5, 4
+    cfg = L.make_config(2, n, n, dt=1.0 / n, precision=L.F32, bc_x=P, bc_y=P,
+                        max_reach=4)
     with L.Bgk(cfg, tau) as g:
         g.init_riemann((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1),
                        L.CIRCLE, 0.5, 0.5, 0.4)
@@ -290,3 +293,72 @@ def test_bgk_benchmark_workload_sampled_fp32():
         gv = fk1[:, :, y * n + x]
         scale = np.max(np.abs(o), axis=0)
         assert np.all(np.abs(gv - o) <= 1e-5 * scale + 1e-30), (x, y)
+
+
+@pytest.mark.parametrize("bcs,shape", [((P, P), (37, 29)), ((T, R), (130, 70)),
+                                       ((R, P), (67, 41))])
+def test_bgk_one_launch_equals_two_kernels_fp32(bcs, shape):
+    """The one-launch step (max_reach <= 4) collides each tile's window in
+    shared memory with the same arithmetic as the collision kernel and
+    gathers in the same order: FP32 results identical bit for bit."""
+    nx, ny = shape
+    f0 = random_packets(2, nx * ny, seed=nx + 7 * ny)
+    out = []
+    for mr in (6, 4):
+        with L.Bgk(_cfg(2, nx, ny, *bcs, L.F32, max_reach=mr), 1.6) as g:
+            g.set_packets(f0)
+            g.step(7)
+            out.append((g.packets(), g.diagnostics()))
+    _assert_bitwise(out[0][0], out[1][0])
+    assert out[0][1]["reach"] == out[1][1]["reach"]
+    assert out[0][1]["eclamps"] == out[1][1]["eclamps"]
+
+
+def test_bgk_one_launch_cylinder_equals_two_kernels_fp32():
+    n = 256
+    args = ((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1), L.CIRCLE, 0.5,
+            0.5, 0.4)
+    out = []
+    for mr in (6, 4):
+        cfg = L.make_config(2, n, n, dt=1.0 / n, precision=L.F32, bc_x=P,
+                            bc_y=P, max_reach=mr)
+        with L.Bgk(cfg, 1.5) as g:
+            g.init_riemann(*args)
+            g.step(60)
+            out.append(g.packets())
+    _assert_bitwise(out[0], out[1])
+
+
+def test_bgk_one_launch_reach_limit():
+    """A reach beyond 4 on the one-launch path: LBM_EREACH, and the packets
+    are left as they were."""
+    nx = 40
+    f0 = random_packets(2, nx * nx, seed=12, spread=0.2)
+    f0[:, 1, :] += 3.0 * f0[:, 0, :]          # V_x about 3: reach 5 or more
+    with L.Bgk(_cfg(2, nx, nx, P, P, L.F64, max_reach=4), 1.5) as g:
+        g.set_packets(f0)
+        g.step(1)
+        d = g.diagnostics()
+        assert d["flags"] & 2
+        with pytest.raises(L.LbmError) as e:
+            g.synchronize()
+        assert e.value.status == L.EREACH
+
+
+def test_bgk_one_launch_restart_is_bitwise():
+    nx, ny, tau = 40, 24, 1.4
+    args = ((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1), L.CIRCLE, 0.5,
+            0.5, 0.3)
+    cfg = lambda: _cfg(2, nx, ny, T, R, L.F32, max_reach=4)
+    with L.Bgk(cfg(), tau) as g:
+        g.init_riemann(*args)
+        g.step(8)
+        whole = g.packets()
+    with L.Bgk(cfg(), tau) as g:
+        g.init_riemann(*args)
+        g.step(3)
+        mid = g.packets()
+    with L.Bgk(cfg(), tau) as g:
+        g.set_packets(mid)
+        g.step(5)
+        _assert_bitwise(g.packets(), whole)
