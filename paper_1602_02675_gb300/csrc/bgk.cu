@@ -131,6 +131,15 @@ __device__ __forceinline__ float rel_const<float>(double, float f) {
   return f;
 }
 
+// a * b + c: FP64 with two roundings, as the oracle evaluates it (this unit
+// is built without contraction); FP32 as one fused multiply-add.
+__device__ __forceinline__ double mad(double a, double b, double c) {
+  return a * b + c;
+}
+__device__ __forceinline__ float mad(float a, float b, float c) {
+  return __fmaf_rn(a, b, c);
+}
+
 // Equilibrium packet j of q as (mass, m_x, [m_y,] energy).
 template <typename T, int DIM>
 __device__ __forceinline__ void eq_packet(const Equil<T>& q, int j,
@@ -239,24 +248,49 @@ __device__ __forceinline__ void collide_one(const Args& a, const T* f,
   }
   long long w = s64_word(-1, 0, 0);
   if (q.emits && REGS) {
+    // the mirror image's slots: the node's, swapped across each reflecting
+    // wall (the two mirrors act on different slots and commute), normal
+    // momentum negated
+    if (flx) {
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        const int m = mirror_slot<DIM>(0, j);
+        if (m > j) {
+#pragma unroll
+          for (int c = 0; c < NF; ++c) {
+            const T t = fa[j][c];
+            fa[j][c] = fa[m][c];
+            fa[m][c] = t;
+          }
+        }
+        fa[j][1] = -fa[j][1];
+      }
+    }
+    if (DIM == 2 && fly) {
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        const int m = mirror_slot<DIM>(1, j);
+        if (m > j) {
+#pragma unroll
+          for (int c = 0; c < NF; ++c) {
+            const T t = fa[j][c];
+            fa[j][c] = fa[m][c];
+            fa[m][c] = t;
+          }
+        }
+        fa[j][2] = -fa[j][2];
+      }
+    }
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
-      // the node's slot this source's slot j mirrors (compile-time slots,
-      // chosen by the flips)
-      const int jx = mirror_slot<DIM>(0, j), jy = mirror_slot<DIM>(1, j);
-      const int jxy = mirror_slot<DIM>(1, jx);
       T fj[NF];
 #pragma unroll
-      for (int c = 0; c < NF; ++c)
-        fj[c] = flx ? (fly ? fa[jxy][c] : fa[jx][c])
-                    : (fly ? fa[jy][c] : fa[j][c]);
-      if (flx) fj[1] = -fj[1];
-      if (DIM == 2 && fly) fj[2] = -fj[2];
+      for (int c = 0; c < NF; ++c) fj[c] = fa[j][c];
       T feq[NF];
       eq_packet<T, DIM>(q, j, feq);
       // eqs 4-5 as the blend (1 - 1/tau) f + (1/tau) f_eq
 #pragma unroll
-      for (int c = 0; c < NF; ++c) r.fs(j, c, i) = keep * fj[c] + omega * feq[c];
+      for (int c = 0; c < NF; ++c) r.fs(j, c, i) = mad(keep, fj[c], omega * feq[c]);
     }
   } else if (q.emits) {
 #pragma unroll 1
@@ -274,7 +308,7 @@ __device__ __forceinline__ void collide_one(const Args& a, const T* f,
       eq_packet<T, DIM>(q, j, feq);
       // eqs 4-5 as the blend (1 - 1/tau) f + (1/tau) f_eq
 #pragma unroll
-      for (int c = 0; c < NF; ++c) r.fs(j, c, i) = keep * fj[c] + omega * feq[c];
+      for (int c = 0; c < NF; ++c) r.fs(j, c, i) = mad(keep, fj[c], omega * feq[c]);
     }
   }
   if (q.emits) {
@@ -357,7 +391,7 @@ __device__ __forceinline__ void gather_one(const RecView<T, DIM>& r, Idx idx,
                                 DIM == 2 ? dy - n1 - cy - (k >> 1) : 0);
         const T al = r.wt(k, i);
 #pragma unroll
-        for (int c = 0; c < NF; ++c) acc[c] = acc[c] + al * r.fs(j, c, i);
+        for (int c = 0; c < NF; ++c) acc[c] = mad(al, r.fs(j, c, i), acc[c]);
       }
       emit(j, acc);
     }
@@ -393,7 +427,7 @@ __device__ __forceinline__ void gather_one(const RecView<T, DIM>& r, Idx idx,
         if (DIM == 2 && (ky < 0 || ky > 1)) continue;
         const T al = r.wt(kx + 2 * ky, i);
 #pragma unroll
-        for (int c = 0; c < NF; ++c) acc[j][c] = acc[j][c] + al * r.fs(j, c, i);
+        for (int c = 0; c < NF; ++c) acc[j][c] = mad(al, r.fs(j, c, i), acc[j][c]);
       }
     }
   }
