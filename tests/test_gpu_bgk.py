@@ -362,3 +362,37 @@ def test_bgk_one_launch_restart_is_bitwise():
         g.set_packets(mid)
         g.step(5)
         _assert_bitwise(g.packets(), whole)
+
+
+def test_bgk_one_launch_fp64_bitwise_many_tiles():
+    """The one-launch step on a grid of 161 tiles with ragged right and
+    bottom rows of tiles, reflecting walls in y: the oracle's bits."""
+    nx, ny, tau, steps = 200, 184, 1.6, 4
+    cfg = _cfg(2, nx, ny, P, R, L.F64, max_reach=4)
+    args = ((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1), L.CIRCLE, 0.5,
+            0.45, 0.3)
+    with L.Bgk(cfg, tau) as g:
+        g.init_riemann(*args)
+        f0 = g.packets()
+        g.step(steps)
+        got = g.packets()
+        d = g.diagnostics()
+    ref, ec = O.bgk_run(_params(2, nx, ny, P, R), tau, f0, steps)
+    _assert_bitwise(got, ref)
+    assert d["eclamps"] == ec and d["flags"] == 0
+
+
+def test_bgk_one_launch_fp32_equals_two_kernels_many_tiles():
+    """416 x 600 (975 tiles), 40 steps of the cylinder: FP32 identical bit
+    for bit to the two-kernel step."""
+    nx, ny = 416, 600
+    args = ((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1), L.CIRCLE, 0.5,
+            0.7, 0.3)
+    out = []
+    for mr in (6, 4):
+        with L.Bgk(_cfg(2, nx, ny, P, P, L.F32, max_reach=mr), 1.5) as g:
+            g.init_riemann(*args)
+            g.step(40)
+            out.append((g.packets(), g.diagnostics()))
+    _assert_bitwise(out[0][0], out[1][0])
+    assert out[0][1]["reach"] == out[1][1]["reach"]
