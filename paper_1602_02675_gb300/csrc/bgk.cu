@@ -435,8 +435,9 @@ __device__ __forceinline__ void gather_one(const RecView<T, DIM>& r, Idx idx,
   for (int j = 0; j < NP; ++j) emit(j, acc[j]);
 }
 
-// Smallest and largest word key over a block (every thread gets them; one
-// barrier).
+// Smallest and largest word key over a block of NW warps (every thread
+// gets them; one barrier; red holds 2 NW words).
+template <int NW = 8>
 __device__ __forceinline__ void block_key_range(unsigned long long& lo,
                                                 unsigned long long& hi,
                                                 unsigned long long* red) {
@@ -449,15 +450,15 @@ __device__ __forceinline__ void block_key_range(unsigned long long& lo,
   }
   if ((threadIdx.x & 31) == 0) {
     red[threadIdx.x >> 5] = lo;
-    red[8 + (threadIdx.x >> 5)] = hi;
+    red[NW + (threadIdx.x >> 5)] = hi;
   }
   __syncthreads();
   lo = red[0];
-  hi = red[8];
+  hi = red[NW];
 #pragma unroll
-  for (int w = 1; w < 8; ++w) {
+  for (int w = 1; w < NW; ++w) {
     lo = red[w] < lo ? red[w] : lo;
-    hi = red[8 + w] > hi ? red[8 + w] : hi;
+    hi = red[NW + w] > hi ? red[NW + w] : hi;
   }
 }
 
@@ -520,8 +521,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
 // Shared memory of the one-launch step (step2d): the collided window of a
 // 32 x 8 tile at reach limit rc, (32 + 2 rc) x (8 + 2 rc) sources, each a
 // word, 32 packet fields and 4 corner weights.
+// Rows of the one-launch step's tile: 16 in FP32 (one 512-thread block per
+// multiprocessor: the window of 40 x 24 sources at R = 4 holds 1.9 sources
+// per destination), 8 in FP64 (its window's 296-byte sources).
+template <typename T>
+__host__ __device__ constexpr int step2d_rows() {
+  return sizeof(T) == 4 ? 16 : 8;
+}
 inline size_t step2d_smem(int rc, size_t es) {
-  return (size_t)(32 + 2 * rc) * (size_t)(8 + 2 * rc) * (8 + 36 * es);
+  const int ty = es == 4 ? step2d_rows<float>() : step2d_rows<double>();
+  return (size_t)(32 + 2 * rc) * (size_t)(ty + 2 * rc) * (8 + 36 * es);
 }
 // Largest reach limit the one-launch step takes (two blocks per
 // multiprocessor in FP32).
@@ -542,21 +551,23 @@ __global__ void __launch_bounds__(256) reach_pass(const Args a) {
   if ((threadIdx.x & 31) == 0 && rm) atomicMax(&a.rslot[a.rs], rm);
 }
 
-// One-launch square-lattice step: each block collides the sources of its
-// tile's window into shared memory (the same values collide() writes), then
+// One-launch square-lattice step: each block (a 32 x step2d_rows tile)
+// collides the sources of its tile's window into shared memory (the same
+// values collide() writes), then
 // gathers its destinations (the same sums, in the same order, as gather()),
 // and forms the new nodes' reach for the next step.  The reach rotates
 // through three slots: step s reads slot s % 3, max-reduces the next
 // state's reach into slot (s + 1) % 3 and clears slot (s + 2) % 3, which
 // the previous step read.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(32 * step2d_rows<T>(), 1)
     step2d(const Args a) {
   constexpr int NP = 8, NF = 4;
+  constexpr int TY = step2d_rows<T>(), NT = 32 * TY;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long red[16];
+  __shared__ unsigned long long red[2 * TY];
   const int rc = a.rc;
-  const int WM = (32 + 2 * rc) * (8 + 2 * rc);
+  const int WM = (32 + 2 * rc) * (TY + 2 * rc);
   RecView<T, 2> r;
   r.cap = WM;
   r.word = reinterpret_cast<long long*>(smem);
@@ -567,7 +578,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
   const int R = a.rslot[rs];
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
     a.rslot[(rs + 2) % 3] = 0;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY;
   const int dx = x0 + (threadIdx.x & 31), dy = y0 + (threadIdx.x >> 5);
   const bool valid = dx < a.nx && dy < a.ny;
   const long long d = (long long)dy * a.nx + dx;
@@ -578,14 +589,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
     return;
   }
   // the window, collided into shared memory
-  const int W = 32 + 2 * R, H = 8 + 2 * R;
+  const int W = 32 + 2 * R, H = TY + 2 * R;
   unsigned long long clamps = 0, lo = ~0ull, hi = 0ull;
   bool bad = false;
   int rdummy = 0;
-  for (int t = threadIdx.x; t < W * H; t += 256) {
+  for (int t = threadIdx.x; t < W * H; t += NT) {
     const int ly = t / W, lx = t - ly * W;
     const int sx = x0 - R + lx, sy = y0 - R + ly;
-    const bool owned = lx >= R && lx < R + 32 && ly >= R && ly < R + 8 &&
+    const bool owned = lx >= R && lx < R + 32 && ly >= R && ly < R + TY &&
                        sx < a.nx && sy < a.ny;
     collide_one<T, 2, true>(a, fin, sx, sy, owned, r, t, clamps, bad,
                             rdummy);
@@ -593,7 +604,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
     lo = k < lo ? k : lo;
     hi = k > hi ? k : hi;
   }
-  block_key_range(lo, hi, red);  // its barrier also publishes the window
+  block_key_range<TY>(lo, hi, red);  // its barrier also publishes the window
   int rm = 0;
   if (valid) {
     int c1, n0, n1;
@@ -788,11 +799,15 @@ cudaError_t launch_step_t(const bgk::Args& a, cudaStream_t s) {
 
 cudaError_t bgk_launch_step(const lbm_bgk* h, const bgk::Args& a) {
   if (h->one_launch) {
-    dim3 gg((unsigned)((a.nx + 31) / 32), (unsigned)((a.ny + 7) / 8));
+    constexpr int t32 = bgk::step2d_rows<float>(), t64 = bgk::step2d_rows<double>();
     if (h->f64)
-      bgk::step2d<double><<<gg, 256, h->smem, h->stream>>>(a);
+      bgk::step2d<double><<<dim3((unsigned)((a.nx + 31) / 32),
+                                 (unsigned)((a.ny + t64 - 1) / t64)),
+                            32 * t64, h->smem, h->stream>>>(a);
     else
-      bgk::step2d<float><<<gg, 256, h->smem, h->stream>>>(a);
+      bgk::step2d<float><<<dim3((unsigned)((a.nx + 31) / 32),
+                                (unsigned)((a.ny + t32 - 1) / t32)),
+                           32 * t32, h->smem, h->stream>>>(a);
     return cudaGetLastError();
   }
   if (h->f64)
