@@ -19,19 +19,22 @@
 // whose c' points the other way along the normal, normal momentum negated,
 // moments the node's with that component negated).
 //
-// Two kernels per step:
+// Square lattice with a reach limit up to 4: one kernel per step
+// (step2d), each block colliding its tile's window into shared memory and
+// gathering the tile from it.  Otherwise two kernels per step:
 //  * collide: one thread per source of the grid padded by the reach limit
 //    r_cap (additional points included): moments, equilibrium, post-collision
 //    packets, corner weights and a word (c1, n) into the source records;
 //    clamps, bad states and the step's reach of the grid's nodes are
 //    reduced on the device;
-//  * gather: one thread per destination of a 32 x 8 tile.  A tile whose
-//    source window holds one type (c1, n) reads each slot's four arriving
-//    corners directly; otherwise every source of the (2R + 1)^D window is
-//    tested once, all slots' sums in registers.  Either way in the order
-//    above.
+//  * gather: one thread per destination of a 32 x 8 tile.
+// In either gather a tile whose source window holds one type (c1, n) reads
+// each slot's four arriving corners directly; otherwise every source of the
+// (2R + 1)^D window is tested once, all slots' sums in registers.  Either
+// way in the order above, so both paths give the same bits.
 // This unit is built without floating-point contraction, so the FP64
-// instance reproduces a plain evaluation of the same formulas bit for bit.
+// instance reproduces a plain evaluation of the same formulas bit for bit;
+// FP32 multiply-adds are explicit fused multiply-adds (mad).
 #include <cmath>
 #include <cstring>
 #include <new>

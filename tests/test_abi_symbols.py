@@ -75,3 +75,16 @@ def test_bgk_create_checks_tau_before_any_cuda_call():
         assert not h.value
     lib.lbm_bgk_destroy(None)
     assert lib.lbm_bgk_last_error(None)
+
+
+def test_bgk_create_checks_the_grid_before_any_cuda_call():
+    from paper_1602_02675_gb300 import lbm as L
+    lib = L.load()
+    h = ctypes.c_void_p()
+    bad = [L.make_config(2, 64, 8 * 65535 + 1, bc_x=L.PERIODIC),  # launch rows
+           L.make_config(1, 16, bc_x=L.PERIODIC, dt=-1.0),          # dt <= 0
+           L.make_config(2, 64, 64, theta=0.5)]                     # 2-D theta
+    for cfg in bad:
+        assert lib.lbm_bgk_create(ctypes.byref(cfg), 1.5,
+                                  ctypes.byref(h)) == L.EINVAL
+        assert not h.value
