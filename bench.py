@@ -31,6 +31,7 @@ in FP32) is far larger than the 129 MB L2, so no flush is needed.
   sod2d      the 2-D shock tube (4096 x 512, transmissive x, reflecting y),
              L2 flushed before every timed step, with FP32 / FP64 errors
              against the oracle's stored row
+  bgk2d      the relaxation-time step (tau = 1.5) on the 2048^2 cylinder
   cpu_baseline  the FP64 oracle on this host's cores, bounded sample
 
 Other workloads (one JSON line each): --workload sod2d (the shock tube as
@@ -360,6 +361,16 @@ def run_cylinder(args, rank, world):
     if rank == 0 and not args.no_sod:
         line["sod2d"] = run_sod2d(args, L, torch, stream, world, rank,
                                   secondary=True)
+    if rank == 0 and not args.no_bgk:
+        b = run_bgk2d(args)
+        line["bgk2d"] = {k: b[k] for k in ("value", "unit", "ms_per_step",
+                                           "steps", "warmup", "roofline",
+                                           "gpu_launches",
+                                           "conservation_drift", "clocks")}
+        line["bgk2d"]["workload"] = b["config"]["workload"]
+        line["bgk2d"]["tau"] = b["config"]["tau"]
+        line["bgk2d"]["parity"] = ("FP64 bit-exact with the FP64 oracle, FP32 "
+                                   "within 1e-5 of each field's range (tests)")
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     return line
@@ -1028,6 +1039,8 @@ def main():
     ap.add_argument("--no-l1", action="store_true")
     ap.add_argument("--no-sod", action="store_true",
                     help="cylinder: skip the shock-tube sub-measurement")
+    ap.add_argument("--no-bgk", action="store_true",
+                    help="cylinder: skip the tau != 1 sub-measurement")
     ap.add_argument("--sod-steps", type=int, default=200)
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--precision-steps", type=int, default=100)
