@@ -78,22 +78,64 @@ __device__ __forceinline__ int* reach_slot(Scratch* scr, int rs) {
 // Source records over the padded grid (PX = nx + 2 rc, PY = ny + 2 rc in
 // 2-D, 1 in 1-D; cap = PX PY sources, source (x, y) at (y + rc) PX + x + rc
 // in 2-D, x + rc in 1-D): first one 64-bit word per source (c1, n_x, n_y as
-// 16-bit fields; c1 = -1: the source emits nothing), then NP * NF arrays of
-// the post-collision packets (slot j field c at array j * NF + c) and the
-// corner weights of eqs 28-29 (arrays NP * NF + k: 1-D k = 0, 1 for
-// (1 - f, f); 2-D k = kx + 2 ky for (1 - f_x or f_x) (1 - f_y or f_y)).
+// 16-bit fields; c1 = -1: the source emits nothing; rounded up to an even
+// count), then per slot j an array of cap groups of NF post-collision
+// fields (source i's at (j cap + i) NF), then the corner weights of eqs
+// 28-29 (arrays NP * NF + k of cap elements: 1-D k = 0, 1 for (1 - f, f);
+// 2-D k = kx + 2 ky for (1 - f_x or f_x) (1 - f_y or f_y)).
 template <typename T, int DIM>
 struct RecView {
+  static constexpr int NF = Shape<DIM>::NF;
   long long cap;
   long long* word;
   T* v;
-  __device__ __forceinline__ T& fs(int j, int c, long long i) const {
-    return v[(long long)(j * Shape<DIM>::NF + c) * cap + i];
+  // slot j's fields of source i are contiguous (one 16-byte access per
+  // slot in 2-D FP32, two in FP64)
+  __device__ __forceinline__ T* slot(int j, long long i) const {
+    return v + ((long long)j * cap + i) * NF;
+  }
+  __device__ __forceinline__ void ld(int j, long long i, T (&o)[NF]) const {
+    const T* p = slot(j, i);
+    if constexpr (NF == 4 && sizeof(T) == 4) {
+      const float4 q = *reinterpret_cast<const float4*>(p);
+      o[0] = q.x;
+      o[1] = q.y;
+      o[2] = q.z;
+      o[3] = q.w;
+    } else if constexpr (NF == 4 && sizeof(T) == 8) {
+      const double2 q0 = reinterpret_cast<const double2*>(p)[0];
+      const double2 q1 = reinterpret_cast<const double2*>(p)[1];
+      o[0] = q0.x;
+      o[1] = q0.y;
+      o[2] = q1.x;
+      o[3] = q1.y;
+    } else {
+#pragma unroll
+      for (int c = 0; c < NF; ++c) o[c] = p[c];
+    }
+  }
+  __device__ __forceinline__ void st(int j, long long i,
+                                     const T (&o)[NF]) const {
+    T* p = slot(j, i);
+    if constexpr (NF == 4 && sizeof(T) == 4) {
+      *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else if constexpr (NF == 4 && sizeof(T) == 8) {
+      reinterpret_cast<double2*>(p)[0] = make_double2(o[0], o[1]);
+      reinterpret_cast<double2*>(p)[1] = make_double2(o[2], o[3]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NF; ++c) p[c] = o[c];
+    }
   }
   __device__ __forceinline__ T& wt(int k, long long i) const {
-    return v[(long long)(Shape<DIM>::NP * Shape<DIM>::NF + k) * cap + i];
+    return v[(long long)(Shape<DIM>::NP * NF + k) * cap + i];
   }
 };
+// Words of a record view, rounded up to an even count so that the fields
+// after them start on a 16-byte boundary.
+__host__ __device__ inline long long rec_words(long long cap) {
+  return (cap + 1) & ~1LL;
+}
 template <typename T, int DIM>
 __device__ __forceinline__ RecView<T, DIM> rec_view(const Args& a) {
   const long long PX = (long long)a.nx + 2 * a.rc;
@@ -101,7 +143,7 @@ __device__ __forceinline__ RecView<T, DIM> rec_view(const Args& a) {
   RecView<T, DIM> r;
   r.cap = PX * PY;
   r.word = static_cast<long long*>(a.rec);
-  r.v = reinterpret_cast<T*>(r.word + r.cap);
+  r.v = reinterpret_cast<T*>(r.word + rec_words(r.cap));
   return r;
 }
 
@@ -110,7 +152,7 @@ inline size_t rec_bytes(int dim, int nx, int ny, int rc, size_t es) {
   const size_t PX = (size_t)nx + 2 * (size_t)rc;
   const size_t PY = dim == 2 ? (size_t)ny + 2 * (size_t)rc : 1;
   const int arrays = dim == 1 ? 5 * 3 + 2 : 8 * 4 + 4;
-  return PX * PY * (8 + arrays * es);
+  return (size_t)rec_words((long long)(PX * PY)) * 8 + PX * PY * arrays * es;
 }
 
 // Slot of the packet mirrored across a wall normal to `axis`.
@@ -292,8 +334,10 @@ __device__ __forceinline__ void collide_one(const Args& a, const T* f,
       T feq[NF];
       eq_packet<T, DIM>(q, j, feq);
       // eqs 4-5 as the blend (1 - 1/tau) f + (1/tau) f_eq
+      T o[NF];
 #pragma unroll
-      for (int c = 0; c < NF; ++c) r.fs(j, c, i) = mad(keep, fj[c], omega * feq[c]);
+      for (int c = 0; c < NF; ++c) o[c] = mad(keep, fj[c], omega * feq[c]);
+      r.st(j, i, o);
     }
   } else if (q.emits) {
 #pragma unroll 1
@@ -310,8 +354,10 @@ __device__ __forceinline__ void collide_one(const Args& a, const T* f,
       T feq[NF];
       eq_packet<T, DIM>(q, j, feq);
       // eqs 4-5 as the blend (1 - 1/tau) f + (1/tau) f_eq
+      T o[NF];
 #pragma unroll
-      for (int c = 0; c < NF; ++c) r.fs(j, c, i) = mad(keep, fj[c], omega * feq[c]);
+      for (int c = 0; c < NF; ++c) o[c] = mad(keep, fj[c], omega * feq[c]);
+      r.st(j, i, o);
     }
   }
   if (q.emits) {
@@ -393,8 +439,10 @@ __device__ __forceinline__ void gather_one(const RecView<T, DIM>& r, Idx idx,
         const long long i = idx(dx - n0 - cx - (k & 1),
                                 DIM == 2 ? dy - n1 - cy - (k >> 1) : 0);
         const T al = r.wt(k, i);
+        T fv[NF];
+        r.ld(j, i, fv);
 #pragma unroll
-        for (int c = 0; c < NF; ++c) acc[c] = mad(al, r.fs(j, c, i), acc[c]);
+        for (int c = 0; c < NF; ++c) acc[c] = mad(al, fv[c], acc[c]);
       }
       emit(j, acc);
     }
@@ -429,8 +477,10 @@ __device__ __forceinline__ void gather_one(const RecView<T, DIM>& r, Idx idx,
         if (kx < 0 || kx > 1) continue;
         if (DIM == 2 && (ky < 0 || ky > 1)) continue;
         const T al = r.wt(kx + 2 * ky, i);
+        T fv[NF];
+        r.ld(j, i, fv);
 #pragma unroll
-        for (int c = 0; c < NF; ++c) acc[j][c] = mad(al, r.fs(j, c, i), acc[j][c]);
+        for (int c = 0; c < NF; ++c) acc[j][c] = mad(al, fv[c], acc[j][c]);
       }
     }
   }
