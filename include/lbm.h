@@ -382,8 +382,9 @@ void lbm_pool_destroy(lbm_pool* p);
  * (NP * NF * n elements each), a moments buffer (4 fields), source records
  * over the grid padded by max_reach (8 bytes plus NP * NF + 2 elements per
  * padded node, rewritten every step), 5 n doubles of staging, scratch.
- * Both precisions; kahan and cons_every are ignored.  Conventions of
- * lbm_create otherwise (stream order, errors, not thread-safe). */
+ * Both precisions; kahan and cons_every are ignored (the configuration is
+ * checked as by lbm_create).  Conventions of lbm_create otherwise (stream
+ * order, errors, not thread-safe). */
 typedef struct lbm_bgk lbm_bgk;
 
 /* Validate cfg and tau (tau > 0.5, finite) and allocate.  tau < 1

@@ -158,24 +158,38 @@ extern "C" {
 
 int32_t lbm_abi_version(void) { return 1; }
 
+}  // extern "C"
+
+namespace lbm {
+
+bool config_ok(const lbm_config& c) {
+  if (c.dim != 1 && c.dim != 2) return false;
+  if (c.precision != LBM_F32 && c.precision != LBM_F64) return false;
+  if (c.nx < 1 || c.ny < 1 || (c.dim == 1 && c.ny != 1)) return false;
+  if (c.nx > INT32_MAX || c.ny > INT32_MAX ||
+      c.nx * c.ny > (int64_t)INT32_MAX)
+    return false;
+  if (c.bc_x < 0 || c.bc_x > 2 || (c.dim == 2 && (c.bc_y < 0 || c.bc_y > 2)))
+    return false;
+  if (!(c.x1 > c.x0) || !(c.gamma > 1.0) || !(c.dt > 0.0)) return false;
+  if (!std::isfinite(c.x0) || !std::isfinite(c.x1) || !std::isfinite(c.y0) ||
+      !std::isfinite(c.dt) || !std::isfinite(c.gamma))
+    return false;
+  if (c.dim == 1 && !(c.theta >= 0.0 && c.theta < 1.0)) return false;
+  if (c.dim == 2 && c.theta != 0.0) return false;
+  if (c.max_reach < 0 || c.cons_every < 0) return false;
+  return true;
+}
+
+}  // namespace lbm
+
+extern "C" {
+
 lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
   if (!cfg || !out) return LBM_EINVAL;
   *out = nullptr;
   const lbm_config& c = *cfg;
-  if (c.dim != 1 && c.dim != 2) return LBM_EINVAL;
-  if (c.precision != LBM_F32 && c.precision != LBM_F64) return LBM_EINVAL;
-  if (c.nx < 1 || c.ny < 1 || (c.dim == 1 && c.ny != 1)) return LBM_EINVAL;
-  if (c.nx * c.ny > (int64_t)INT32_MAX || c.nx > INT32_MAX || c.ny > INT32_MAX)
-    return LBM_EINVAL;
-  if (c.bc_x < 0 || c.bc_x > 2 || (c.dim == 2 && (c.bc_y < 0 || c.bc_y > 2)))
-    return LBM_EINVAL;
-  if (!(c.x1 > c.x0) || !(c.gamma > 1.0) || !(c.dt > 0.0)) return LBM_EINVAL;
-  if (!std::isfinite(c.x0) || !std::isfinite(c.x1) || !std::isfinite(c.y0) ||
-      !std::isfinite(c.dt) || !std::isfinite(c.gamma))
-    return LBM_EINVAL;
-  if (c.dim == 1 && !(c.theta >= 0.0 && c.theta < 1.0)) return LBM_EINVAL;
-  if (c.dim == 2 && c.theta != 0.0) return LBM_EINVAL;
-  if (c.max_reach < 0 || c.cons_every < 0) return LBM_EINVAL;
+  if (!config_ok(c)) return LBM_EINVAL;
 
   lbm_handle* h = new (std::nothrow) lbm_handle();
   if (!h) return LBM_ENOMEM;

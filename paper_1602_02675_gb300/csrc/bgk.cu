@@ -948,20 +948,7 @@ lbm_status lbm_bgk_create(const lbm_config* cfg, double tau, lbm_bgk** out) {
   if (!cfg || !out) return LBM_EINVAL;
   *out = nullptr;
   const lbm_config& c = *cfg;
-  if (c.dim != 1 && c.dim != 2) return LBM_EINVAL;
-  if (c.precision != LBM_F32 && c.precision != LBM_F64) return LBM_EINVAL;
-  if (c.nx < 1 || c.ny < 1 || (c.dim == 1 && c.ny != 1)) return LBM_EINVAL;
-  if (c.nx * c.ny > (int64_t)INT32_MAX || c.nx > INT32_MAX || c.ny > INT32_MAX)
-    return LBM_EINVAL;
-  if (c.bc_x < 0 || c.bc_x > 2 || (c.dim == 2 && (c.bc_y < 0 || c.bc_y > 2)))
-    return LBM_EINVAL;
-  if (!(c.x1 > c.x0) || !(c.gamma > 1.0) || !(c.dt > 0.0)) return LBM_EINVAL;
-  if (!std::isfinite(c.x0) || !std::isfinite(c.x1) || !std::isfinite(c.y0) ||
-      !std::isfinite(c.dt) || !std::isfinite(c.gamma))
-    return LBM_EINVAL;
-  if (c.dim == 1 && !(c.theta >= 0.0 && c.theta < 1.0)) return LBM_EINVAL;
-  if (c.dim == 2 && c.theta != 0.0) return LBM_EINVAL;
-  if (c.max_reach < 0 || c.max_reach > 1024) return LBM_EINVAL;
+  if (!config_ok(c) || c.max_reach > 1024) return LBM_EINVAL;
   // the 2-D gather launch takes 8 rows per block along grid y
   if (c.dim == 2 && (c.ny + 7) / 8 > 65535) return LBM_EINVAL;
   if (!(tau > 0.5) || !std::isfinite(tau)) return LBM_EINVAL;

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 struct lbm_handle;
+#include "lbm.h"
 
 namespace lbm {
 
@@ -74,6 +75,11 @@ struct StepArgs {
 inline size_t src_bytes(int nx, int ny, int r_cap, size_t esize) {
   return (size_t)(nx + 2 * r_cap) * (size_t)(ny + 2 * r_cap) * (30 * esize + 8);
 }
+
+// Checks of an lbm_config shared by the handle constructors (sizes,
+// boundary kinds, gas, extent, time step, rest share, reach limit); no CUDA
+// call.  True if the configuration is valid.
+bool config_ok(const lbm_config& c);
 
 // Multiprocessors of the current device (cached per device; 1 if the
 // query fails, which only makes grids smaller).

@@ -88,3 +88,51 @@ def test_bgk_create_checks_the_grid_before_any_cuda_call():
         assert lib.lbm_bgk_create(ctypes.byref(cfg), 1.5,
                                   ctypes.byref(h)) == L.EINVAL
         assert not h.value
+
+
+def test_create_calls_reject_the_same_bad_configs():
+    """lbm_create and lbm_bgk_create share one configuration check; every
+    rejection happens before any CUDA call, so it runs here without a GPU."""
+    from paper_1602_02675_gb300 import lbm as L
+    lib = L.load()
+    mk = L.make_config
+    bad = [mk(3, 16),                                       # dim
+           mk(1, 16, precision=7),                          # precision
+           mk(2, 16, 0),                                    # ny < 1
+           mk(1, 16, bc_x=5),                               # boundary kind
+           mk(2, 16, 16, bc_y=-1),
+           mk(1, 16, gamma=1.0),                            # gamma <= 1
+           mk(1, 16, x0=1.0, x1=0.5),                       # extent
+           mk(1, 16, dt=0.0),                               # dt
+           mk(1, 16, theta=1.0),                            # 1-D theta
+           mk(2, 16, 16, theta=0.5),                        # 2-D theta
+           mk(1, 16, max_reach=-1),
+           mk(2, 1 << 20, 1 << 12)]                         # nx ny > 2^31 - 1
+    for cfg in bad:
+        h = ctypes.c_void_p()
+        assert lib.lbm_create(ctypes.byref(cfg), ctypes.byref(h)) == L.EINVAL
+        assert not h.value
+        assert lib.lbm_bgk_create(ctypes.byref(cfg), 1.5,
+                                  ctypes.byref(h)) == L.EINVAL
+        assert not h.value
+
+
+def test_create_calls_accept_valid_configs():
+    """Valid configurations pass the shared check: without a GPU the call
+    then fails in CUDA (not LBM_EINVAL); with one it makes a handle."""
+    from paper_1602_02675_gb300 import lbm as L
+    lib = L.load()
+    good = [L.make_config(1, 1000, bc_x=L.TRANSMISSIVE),
+            L.make_config(2, 64, 48, precision=L.F32, bc_x=L.PERIODIC,
+                          bc_y=L.PERIODIC, max_reach=4),
+            L.make_config(2, 40, 24, bc_x=L.TRANSMISSIVE, bc_y=L.REFLECTING)]
+    for cfg in good:
+        h = ctypes.c_void_p()
+        st = lib.lbm_create(ctypes.byref(cfg), ctypes.byref(h))
+        assert st != L.EINVAL
+        if st == L.OK:
+            lib.lbm_destroy(h)
+        st = lib.lbm_bgk_create(ctypes.byref(cfg), 1.5, ctypes.byref(h))
+        assert st != L.EINVAL
+        if st == L.OK:
+            lib.lbm_bgk_destroy(h)
