@@ -1206,15 +1206,14 @@ lbm_status lbm_bgk_diagnostics(lbm_bgk* h, int64_t* steps, int64_t* eclamps,
                                int32_t* reach, uint32_t* flags) {
   if (!h) return LBM_EINVAL;
   Scratch s;
+  int rs[3] = {0, 0, 0};
   cudaError_t e = cudaMemcpyAsync(&s, h->scr, sizeof(Scratch),
                                   cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && h->one_launch)
+    e = cudaMemcpyAsync(rs, h->rslot, sizeof(rs), cudaMemcpyDeviceToHost,
+                        h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return bcuda(h, e, "diagnostics");
-  int rs[3] = {0, 0, 0};
-  if (h->one_launch) {
-    e = cudaMemcpy(rs, h->rslot, sizeof(rs), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return bcuda(h, e, "diagnostics");
-  }
   if (steps) *steps = h->steps;
   if (eclamps) *eclamps = (int64_t)s.eclamps;
   // the slot of the last step (0 before the first)
