@@ -254,3 +254,31 @@ def test_bgk_rejects_tau_at_or_below_one_half():
     f = O.bgk_equilibrium(P, s)
     with pytest.raises(O.OracleError):
         O.bgk_step(P, 0.5, f)
+
+
+def test_bgk_sod_converges_and_diffuses_more_with_tau():
+    """The Sod tube (Section V.C) at tau != 1 against the exact Riemann
+    solution (the paper's comparison): for each tau the L1 errors of rho and
+    p fall as the lattice is refined (the BGK step stays consistent with the
+    Euler equations, Section II), and at a fixed lattice they grow with tau
+    (the relaxation's diffusion grows with tau; tau = 1 sits between)."""
+    from oracle import riemann as RM
+    left, right = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    err = {}
+    for tau in (0.8, 1.0, 1.5, 3.0):
+        for N in (200, 400, 800):
+            n, lam = O.steps_and_lambda(0.2, 1.0 / N)
+            P = O.Params(dim=1, nx=N, bc_x=O.TRANSMISSIVE)
+            s = O.riemann_planar(P, 0.0, 1.0, 0.5, left, right, lam)
+            f, _ = O.bgk_run(P, tau, O.bgk_equilibrium(P, s), n)
+            ph = O.lattice_to_physical(1.4, lam, O.bgk_moments(P, f))
+            e = RM.l1_errors(O.node_x(N, 0.0, 1.0), 0.2, 0.5, left, right,
+                             ph["rho"], ph["u"], ph["p"])
+            err[tau, N] = (e["rho"], e["p"])
+    for tau in (0.8, 1.0, 1.5, 3.0):
+        for k in (0, 1):
+            assert err[tau, 200][k] > err[tau, 400][k] > err[tau, 800][k]
+    for N in (200, 400, 800):
+        for k in (0, 1):
+            assert (err[0.8, N][k] < err[1.0, N][k] < err[1.5, N][k]
+                    < err[3.0, N][k])
