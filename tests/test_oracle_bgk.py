@@ -8,7 +8,9 @@ state) against what the method fixes independently of it:
 * a single periodic node, where every packet comes back to its own slot and
   the distance from equilibrium decays by (1 - 1/tau) per step exactly;
 * conservation of mass, momentum and energy on periodic and closed boxes;
-* a uniform equilibrium state, which no tau may change.
+* a uniform equilibrium state, which no tau may change;
+* the Sod tube against the exact Riemann solution: convergence under
+  refinement, and more diffusion as tau grows.
 """
 import itertools
 from fractions import Fraction as F
