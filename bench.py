@@ -371,8 +371,9 @@ def run_cylinder(args, rank, world):
         line["bgk2d"]["tau"] = b["config"]["tau"]
         line["bgk2d"]["parity"] = ("FP64 bit-exact with the FP64 oracle, FP32 "
                                    "within 1e-5 of each field's range (tests)")
-    if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds,
+                                            cpu_procs(args.cpu_procs))
     return line
 
 
@@ -739,17 +740,51 @@ def _oracle_cylinder_rows(rows, nsteps=1):
     return time.perf_counter() - t0, n * rows * nsteps
 
 
-def cpu_baseline(seconds: float) -> dict:
-    # calibrate on one step of an 8192 x 4 strip, then size the sample
+def _oracle_rows_task(rows):
+    return _oracle_cylinder_rows(rows)
+
+
+def _oracle_on_cores(rows, procs, timeout=60.0):
+    """One oracle step of the strip in each of `procs` processes at once
+    (spawned, so that no process is forked from one that holds a GPU
+    context; a first round loads the library in each): (wall seconds of the
+    concurrent round, node updates of all processes), or None when the pool
+    fails or runs out of time (the caller then times one thread)."""
+    import multiprocessing as mp
+    try:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            pool.map_async(_oracle_rows_task, [1] * procs).get(timeout)
+            t0 = time.perf_counter()
+            res = pool.map_async(_oracle_rows_task, [rows] * procs).get(timeout)
+            wall = time.perf_counter() - t0
+    except Exception:
+        return None
+    return wall, sum(nu for _, nu in res)
+
+
+def cpu_procs(requested: int) -> int:
+    return max(1, requested if requested > 0 else (os.cpu_count() or 1))
+
+
+def cpu_baseline(seconds: float, procs: int = 1) -> dict:
+    # calibrate on one step of an 8192 x 4 strip, then size the sample:
+    # about `seconds` of CPU work over all processes together
     t, nu = _oracle_cylinder_rows(4)
     rate = nu / t
-    rows = max(4, min(CYL_N, int(seconds * rate / CYL_N)))
-    t, nu = _oracle_cylinder_rows(rows)
-    return {"value": nu / t, "unit": "node-updates/s", "cores": 1,
+    rows = max(4, min(CYL_N, int(seconds * rate / (procs * CYL_N))))
+    got = _oracle_on_cores(rows, procs) if procs > 1 else None
+    if got is None:
+        procs = 1
+        rows = max(4, min(CYL_N, int(seconds * rate / CYL_N)))
+        t, nu = _oracle_cylinder_rows(rows)
+    else:
+        t, nu = got
+    return {"value": nu / t, "unit": "node-updates/s", "cores": procs,
             "kind": "oracle", "host": host_info(),
             "sample": f"1 step of an 8192 x {rows} periodic strip through the "
-                      f"centre of the cylinder's initial state (FP64 oracle, "
-                      f"one thread), {t:.1f} s"}
+                      f"centre of the cylinder's initial state in each of "
+                      f"{procs} processes at once (FP64 oracle as it stands, "
+                      f"one thread each), {t:.1f} s"}
 
 
 def l1_vs_oracle(L) -> dict:
@@ -994,16 +1029,24 @@ def run_reference(args, rank, world):
     times, nus = [], []
     rows = args.ref_rows
     K = args.steps if args.steps > 0 else 5
+    procs = cpu_procs(args.cpu_procs)
+
+    def one():
+        got = _oracle_on_cores(rows, procs) if procs > 1 else None
+        return got if got is not None else _oracle_cylinder_rows(rows)
+
     for _ in range(args.warmup):
-        _oracle_cylinder_rows(rows)
+        one()
     for _ in range(K):
-        t, nu = _oracle_cylinder_rows(rows)
+        t, nu = one()
         times.append(t)
         nus.append(nu)
+    used = procs if nus[0] == CYL_N * rows * procs else 1
     value = sum(nus) / sum(times)
     sample = (f"each step: 1 lattice step of an 8192 x {rows} periodic strip "
-              "through the centre of the cylinder's initial state (FP64 "
-              "oracle, one thread)")
+              "through the centre of the cylinder's initial state in each of "
+              f"{used} processes at once (FP64 oracle as it stands, one thread "
+              "each)")
     return {
         "metric": METRIC, "value": value, "unit": "node-updates/s",
         "impl": "reference", "n_gpus": world, "steps": K,
@@ -1015,8 +1058,8 @@ def run_reference(args, rank, world):
         "config": {"workload": CYL_NAME, "nx": CYL_N, "ny": CYL_N,
                    "sample_rows": rows},
         "cpu_baseline": {"value": value, "unit": "node-updates/s",
-                         "cores": 1, "kind": "oracle", "host": host_info(),
-                         "sample": sample},
+                         "cores": used, "kind": "oracle",
+                         "host": host_info(), "sample": sample},
         "e2e": {"value": value, "unit": "node-updates/s",
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -1032,6 +1075,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-solves", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-procs", type=int, default=0,
+                    help="oracle timing: processes run at once (0 = one per "
+                         "host core)")
     ap.add_argument("--ref-rows", type=int, default=8)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per step-kernel launch, if measured")
@@ -1139,8 +1185,9 @@ def run_sod2d_main(args, rank, world):
             "roofline": sub["roofline"], "clocks": sub.get("clocks"),
             "gpu_launches": DS_LAUNCHES_PER_STEP * args.steps,
             "sod2d": sub}
-    if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds,
+                                            cpu_procs(args.cpu_procs))
     return line
 
 
