@@ -378,13 +378,20 @@ void lbm_pool_destroy(lbm_pool* p);
  * Packet arrays at the ABI: NP * NF arrays of n doubles, array j * NF + c
  * for slot j and field c, nodes x fastest (NP * NF * n doubles in all),
  * physical units (momentum = lattice momentum / lambda, energy = lattice
- * energy / lambda^2).  Device memory per handle: two packet sets
- * (NP * NF * n elements each), a moments buffer (4 fields), source records
- * over the grid padded by max_reach (8 bytes plus NP * NF + 2 elements per
- * padded node, rewritten every step), 5 n doubles of staging, scratch.
- * Both precisions; kahan and cons_every are ignored (the configuration is
- * checked as by lbm_create).  Conventions of lbm_create otherwise (stream
- * order, errors, not thread-safe). */
+ * energy / lambda^2).
+ *
+ * Step paths: on the square lattice with max_reach <= 4 one kernel launch
+ * per step (each tile's window collided in shared memory, then gathered);
+ * otherwise (1-D, or a larger reach limit) a collision pass into source
+ * records and a gather pass, two launches.  Both give the same bits.
+ * Device memory per handle: two packet sets (NP * NF * n elements each), a
+ * moments buffer (4 fields), 5 n doubles of staging, scratch; the
+ * two-launch path adds source records over the grid padded by max_reach
+ * (8 bytes plus NP * NF + 4 (2-D) or NP * NF + 2 (1-D) elements per padded
+ * node, rewritten every step).  Both precisions; kahan and cons_every are
+ * ignored (the configuration is checked as by lbm_create; max_reach at
+ * most 1024).  Conventions of lbm_create otherwise (stream order, errors,
+ * not thread-safe). */
 typedef struct lbm_bgk lbm_bgk;
 
 /* Validate cfg and tau (tau > 0.5, finite) and allocate.  tau < 1
