@@ -146,8 +146,40 @@ def write_sod2d_row(path):
             f.write(f"{float(r)!r} {float(m)!r} {float(e)!r}\n")
 
 
+BGK_TAUS = (0.8, 1.5, 3.0)
+BGK_NS = (200, 400, 800)
+
+
+def bgk_sod_l1(tau, N, t_end=0.2):
+    """L1 error against the exact solution of the 1-D Sod tube run with the
+    relaxation-time step (eqs 4-5) from equilibrium."""
+    P = O.Params(dim=1, nx=N, bc_x=O.TRANSMISSIVE)
+    n, lam = O.steps_and_lambda(t_end, 1.0 / N)
+    s = O.riemann_planar(P, 0, 1, 0.5, SOD_L, SOD_R, lam)
+    f, _ = O.bgk_run(P, tau, O.bgk_equilibrium(P, s), n)
+    ph = O.lattice_to_physical(1.4, lam, O.bgk_moments(P, f))
+    x = O.node_x(N, 0, 1)
+    return Rm.l1_errors(x, t_end, 0.5, SOD_L, SOD_R, ph["rho"], ph["u"],
+                        ph["p"])
+
+
+def write_bgk_sod_l1(path):
+    with open(path, "w") as f:
+        f.write("# L1 (mean absolute) error of the 1-D Sod tube run with the\n"
+                "# relaxation-time step (eqs 4-5, per-packet state) from\n"
+                "# equilibrium, against the exact Riemann solution at t = 0.2\n"
+                "# (Section V.C-D), theta = 0.5, lambda from n = ceil(t/dx),\n"
+                "# transmissive ends.  Written by tests/golden/make_golden.py\n"
+                "# from oracle/ only.  columns: tau N rho u p\n")
+        for tau in BGK_TAUS:
+            for N in BGK_NS:
+                e = bgk_sod_l1(tau, N)
+                f.write(f"{tau} {N} {e['rho']:.6e} {e['u']:.6e} {e['p']:.6e}\n")
+
+
 def main():
     here = os.path.dirname(os.path.abspath(__file__))
+    write_bgk_sod_l1(os.path.join(here, "bgk_sod_l1_errors.txt"))
     write_cylinder_floor(os.path.join(here, "cylinder_fp32_storage_floor.txt"))
     write_cylinder_hashes(os.path.join(here, "cylinder128_fp64_2000_sha256.txt"))
     write_sod2d_row(os.path.join(here, "sod2d_row_4096_t0.2.txt"))

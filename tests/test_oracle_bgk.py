@@ -284,3 +284,14 @@ def test_bgk_sod_converges_and_diffuses_more_with_tau():
         for k in (0, 1):
             assert (err[0.8, N][k] < err[1.0, N][k] < err[1.5, N][k]
                     < err[3.0, N][k])
+    # and they stay at the values frozen in tests/golden (written from the
+    # oracle alone; the run is deterministic FP64)
+    import os
+    here = os.path.join(os.path.dirname(__file__), "golden",
+                        "bgk_sod_l1_errors.txt")
+    rows = [l.split() for l in open(here) if l.strip() and l[0] != "#"]
+    assert len(rows) == 9
+    for tau, N, rho, _, p in rows:
+        got = err[float(tau), int(N)]
+        assert abs(got[0] - float(rho)) <= 1e-6 * float(rho)
+        assert abs(got[1] - float(p)) <= 1e-6 * float(p)
