@@ -763,7 +763,9 @@ def _oracle_on_cores(rows, procs, timeout=60.0):
 
 
 def cpu_procs(requested: int) -> int:
-    return max(1, requested if requested > 0 else (os.cpu_count() or 1))
+    """Processes of the oracle timing: as requested, else one per host core
+    (at most 64)."""
+    return max(1, requested if requested > 0 else min(64, os.cpu_count() or 1))
 
 
 def cpu_baseline(seconds: float, procs: int = 1) -> dict:
