@@ -10,7 +10,8 @@ state) against what the method fixes independently of it:
 * conservation of mass, momentum and energy on periodic and closed boxes;
 * a uniform equilibrium state, which no tau may change;
 * the Sod tube against the exact Riemann solution: convergence under
-  refinement, and more diffusion as tau grows.
+  refinement, and more diffusion as tau grows;
+* a shear wave, whose decay grows with tau.
 """
 import itertools
 from fractions import Fraction as F
@@ -295,3 +296,33 @@ def test_bgk_sod_converges_and_diffuses_more_with_tau():
         got = err[float(tau), int(N)]
         assert abs(got[0] - float(rho)) <= 1e-6 * float(rho)
         assert abs(got[1] - float(p)) <= 1e-6 * float(p)
+
+
+def _shear_decay_rate(tau, n=32, steps=50, amp=0.02):
+    """Per-step decay rate of a transverse shear wave v = amp sin(2 pi x) on a
+    periodic n x n gas at rest otherwise (rho = 1, p = 0.5), from the
+    amplitude of its Fourier mode after the first 10 steps."""
+    P = O.Params(dim=2, nx=n, ny=n, bc_x=O.PERIODIC, bc_y=O.PERIODIC)
+    x = (np.arange(n) + 0.5) / n
+    X, _ = np.meshgrid(x, x)
+    wave = np.sin(2 * np.pi * X).ravel()
+    s = O.prims_to_lattice(1.4, 1.0, np.ones(n * n), np.zeros(n * n),
+                           amp * wave, np.full(n * n, 0.5))
+    f = O.bgk_equilibrium(P, s)
+    a = []
+    for _ in range(steps):
+        m = O.bgk_moments(P, f)
+        a.append(2.0 * np.mean(m.my / m.rho * wave))
+        assert abs(np.sum(m.my)) <= 1e-12 * n * n   # y-momentum stays 0
+        f, _, _ = O.bgk_step(P, tau, f)
+    a = np.abs(np.array(a))
+    return -np.polyfit(np.arange(10, steps), np.log(a[10:]), 1)[0]
+
+
+def test_bgk_shear_wave_decays_faster_as_tau_grows():
+    """A shear wave on the square lattice decays (the step is stable for it)
+    and its decay, the transverse momentum's diffusion, grows with tau:
+    the relaxation's viscosity rises with tau as in BGK models (eqs 4-5)."""
+    rates = [_shear_decay_rate(t) for t in (0.7, 1.0, 1.5, 3.0)]
+    assert all(r > 0 for r in rates)
+    assert rates[0] < rates[1] < rates[2] < rates[3]
